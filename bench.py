@@ -1,0 +1,366 @@
+"""Benchmark of the sparse-grid PIC hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gb300,reference}]
+
+One step = gather-push, cell-key sort (every --sort-every steps), deposit,
+restriction to all component grids, batched spectral solves, FP64-grade
+combination.  Workload: 2D Landau damping, level n = 10, tau = 1
+(19 component grids), 4,194,304 FP32 particles (synthetic, seeded).
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own
+replica of the workload (independent runs, no collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s and HBM-roofline fraction (deposit, gather); p50/p99 step latency"
+UNIT = "particle-steps/s"
+WORKLOAD = "landau2d_n10_fp32"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel's source has not changed since (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    rec = d.get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["sha256_16"]:
+        return None
+    return rec
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() and args.impl != "reference" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x):
+    if pg is None:
+        return x
+    import torch
+    dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- algorithmic bytes
+def algorithmic_bytes(np_, n, d, real_bytes=4):
+    """Bytes the method must move per step (sort excluded), per kernel.
+    deposit: read u (d) + w; push: read u, v, w, write u, v; plus the
+    combined field read once by the push (hi plane, d N^d floats)."""
+    N = 1 << n
+    dep = np_ * (d + 1) * real_bytes
+    push = np_ * ((2 * d + 1) + 2 * d) * real_bytes + d * N ** d * real_bytes
+    return {"deposit": dep, "push": push}
+
+
+def cpu_baseline(sample_particles=1 << 18, steps=1):
+    from oracle import sgpic_oracle as O
+    from paper_2008_09441_gb300 import workloads
+    wl = workloads.make(WORKLOAD, n_particles=sample_particles)
+    u = wl.u.astype(np.float32).astype(np.float64)
+    v = wl.v.astype(np.float32).astype(np.float64)
+    q = wl.q.astype(np.float32).astype(np.float64)
+    run = O.OracleRun(wl.L, wl.n, u, v, q, wl.dt, tau=wl.tau)
+    t0 = time.perf_counter()
+    run.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": sample_particles * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} step(s) of {sample_particles} particles of the {WORKLOAD} workload "
+                      f"(n=10, tau=1, 19 grids), FP64 numpy oracle, single thread, {dt:.1f} s"}
+
+
+def run_reference(args, world, rank, pg):
+    """The oracle as it stands, on the host cores (the reference arm)."""
+    if rank != 0:
+        barrier(pg)
+        return
+    from oracle import sgpic_oracle as O
+    from paper_2008_09441_gb300 import workloads
+    sample = args.ref_particles
+    wl = workloads.make(WORKLOAD, n_particles=sample)
+    u = wl.u.astype(np.float32).astype(np.float64)
+    v = wl.v.astype(np.float32).astype(np.float64)
+    q = wl.q.astype(np.float32).astype(np.float64)
+    run = O.OracleRun(wl.L, wl.n, u, v, q, wl.dt, tau=wl.tau)
+    run.step(min(args.warmup, 1))
+    times = []
+    budget_s = args.ref_budget_s  # the oracle's per-step cost is seconds: bound the whole run
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        run.step(1)
+        times.append(time.perf_counter() - t0)
+        if sum(times) > budget_s:
+            break
+    tot = sum(times)
+    val = sample * len(times) / tot
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "particles": sample, "n": 10, "tau": 1, "grids": 19,
+                      "note": "oracle timed on a bounded particle sample of the workload"},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{len(times)} of the {args.steps} requested steps (time budget "
+                                      f"{budget_s:.0f} s) of {sample} particles, n=10, tau=1"},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    sys.stdout.flush()
+    barrier(pg)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--particles", type=int, default=4194304)
+    ap.add_argument("--sort-every", type=int, default=0)
+    ap.add_argument("--ref-particles", type=int, default=1 << 16)
+    ap.add_argument("--ref-budget-s", type=float, default=120.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank, pg)
+        return
+
+    import torch
+    from paper_2008_09441_gb300 import Run, workloads
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    wl = workloads.make(WORKLOAD, n_particles=args.particles, seed=workloads.SEED_BASE + 1 + rank)
+    d, n = wl.dim, wl.n
+    u = torch.from_numpy(wl.u.astype(np.float32)).to(dev)
+    v = torch.from_numpy(wl.v.astype(np.float32)).to(dev)
+    q = torch.from_numpy(wl.q.astype(np.float32)).to(dev)
+    sort_every = args.sort_every if args.sort_every > 0 else 1
+    run = Run(wl.L, n, u, v, q, wl.dt, tau=wl.tau, precision="fp32", sort_every=sort_every,
+              stream=stream.cuda_stream)
+    del u, v, q
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    np_ = wl.n_particles
+
+    # warm-up (graph capture happens here)
+    run.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K graph-launched steps, L2 flushed before each
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = run.kernel_launches()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        run.step(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier(pg)
+    clk = clocks.stop()
+    launches = run.kernel_launches() - l0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    tot_ms = max_over_ranks(pg, sum(step_ms))
+    value = world * np_ * args.steps / (tot_ms * 1e-3)
+
+    # ---- per-kernel durations (events between stages, same workload, L2 flushed)
+    run.set_profiling(True)
+    stage = {k: 0.0 for k in ["push", "sort", "deposit", "restrict", "solve", "combine"]}
+    for k in range(args.steps):
+        flush.zero_()
+        run.step(1)
+        for key, val in run.stage_times().items():
+            stage[key] += val
+    run.set_profiling(False)
+    torch.cuda.synchronize()
+    stage_avg = {k: v / args.steps for k, v in stage.items()}
+    alg = algorithmic_bytes(np_, n, d)
+    peak, peak_kind = measured_peaks()
+    rl = {}
+    for kern in ("deposit", "push"):
+        ms = stage_avg[kern]
+        ach = alg[kern] / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        rl[kern] = {"achieved": ach, "frac": ach / peak, "ms": ms, "alg_bytes": alg[kern]}
+    dominant = max(("deposit", "push"), key=lambda k: stage_avg[k])
+    tr = traffic_record({"deposit": "k_deposit", "push": "k_push"}[dominant])
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": rl[dominant]["achieved"], "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": rl[dominant]["frac"],
+                "traffic": (tr["dram_bytes_per_launch"] * (np_ / tr["particles"]) if tr else None),
+                "per_kernel": {k: {"achieved_gbs": rl[k]["achieved"], "frac": rl[k]["frac"],
+                                   "ms": rl[k]["ms"], "alg_bytes": rl[k]["alg_bytes"]} for k in rl},
+                "stage_ms": stage_avg}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hu = [torch.from_numpy(np.ascontiguousarray(wl.u[:, m], dtype=np.float32)).pin_memory() for m in range(d)]
+        hv = [torch.from_numpy(np.ascontiguousarray(wl.v[:, m], dtype=np.float32)).pin_memory() for m in range(d)]
+        hq = torch.from_numpy(wl.q.astype(np.float32)).pin_memory()
+        ou = torch.empty((d, np_), dtype=torch.float32).pin_memory()
+        ov = torch.empty((d, np_), dtype=torch.float32).pin_memory()
+        ow = torch.empty(np_, dtype=torch.float32).pin_memory()
+        run.close()
+        torch.cuda.synchronize()
+        barrier(pg)
+        t0 = time.perf_counter()
+        r2 = Run(wl.L, n, hu, hv, hq, wl.dt, tau=wl.tau, precision="fp32", sort_every=sort_every, stream=stream.cuda_stream)
+        r2.step(args.steps)
+        from paper_2008_09441_gb300 import _lib as L
+        import ctypes as C
+        o = L.sg_particles_out()
+        o.n = np_
+        o.on_device = 0
+        for m in range(d):
+            o.u[m] = ou[m].data_ptr()
+            o.v[m] = ov[m].data_ptr()
+        o.w = ow.data_ptr()
+        L.check(L.lib().sg_pic_get_particles(r2.h, C.byref(o)), "get_particles")
+        diag = r2.diagnostics()
+        e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
+        r2.close()
+        h2d = np_ * (2 * d + 1) * 4
+        d2h = np_ * (2 * d + 1) * 4
+        e2e = {"value": world * np_ * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "includes": "sg_pic_init from pinned host arrays (copy, sort, first solve), K steps, "
+                           "particles back to pinned host memory, diagnostics",
+               "field_energy": diag["field_energy"]}
+    else:
+        run.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        srt = sorted(step_ms)
+        p50 = srt[len(srt) // 2]
+        p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic (seeded Landau-damping particles)",
+               "config": {"workload": f"{WORKLOAD}: 2D Landau damping, n=10, tau=1, 19 component grids, "
+                                      f"{np_} FP32 particles, dt=0.05",
+                          "particles_per_gpu": np_, "sort_every": sort_every, "l2": "flushed before every step",
+                          "combine": "float-float (48-bit) accumulation, FP64 diagnostics",
+                          "parallelism": f"{world} independent replicas"},
+               "latency_ms": {"p50": p50, "p99": p99},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clk, "wall_s_timed": wall}
+        print(json.dumps(out))
+        sys.stdout.flush()
+    barrier(pg)
+
+
+if __name__ == "__main__":
+    main()

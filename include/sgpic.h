@@ -1,0 +1,261 @@
+/*
+ * sgpic.h -- C ABI of the GB300 sparse-grid combination-technique PIC library.
+ *
+ * The library advances electrostatic particle-in-cell runs whose charge
+ * density and field are represented by the truncated sparse-grid
+ * combination technique of Muralikrishnan, Cerfon, Frey, Ricketson and
+ * Adelmann, "Sparse grids based adaptive noise reduction strategy for
+ * particle-in-cell schemes" (arXiv:2008.09441).  One step is:
+ *
+ *   cell-key sort of the particles (every `sort_every` steps)
+ *   -> CIC deposit onto every component grid (Section 4.1, eq. restriction,
+ *      computed through the regular grid as Proposition 1 allows)
+ *   -> spectral Poisson solve on every component grid (Section 2)
+ *   -> signed combination of the component fields on the regular nodes
+ *      (eq. sparse_filter applied to the fields, coefficients of Section 4.2)
+ *   -> CIC gather and leapfrog / Boris push (Section 2, steps 3-4).
+ *
+ * Conventions shared by every call:
+ *   - Every function returns an int status: SG_OK (0) or a negative SG_ERR_*
+ *     code.  sg_strerror() names it; sg_last_error() gives the detail text of
+ *     the most recent failure in the calling thread.  No C++ exception crosses
+ *     this boundary.
+ *   - Geometry: periodic box [0, L_1) x ... x [0, L_d), d in {2, 3}.  Particle
+ *     positions are passed as fractions of the box, u_m = x_m / L_m (values
+ *     outside [0, 1) are wrapped periodically).  Velocities are physical.
+ *     Grids are node-centred: node k of a level-l axis is at x = k L / 2^l.
+ *   - Grid arrays are flat, x fastest: index = i_1 + 2^l_1 (i_2 + 2^l_2 i_3).
+ *   - Particle arrays are structure-of-arrays in the run's precision
+ *     (float for SG_FP32, double for SG_FP64).
+ *   - A handle is not thread safe: one thread at a time per handle.  All
+ *     device work of a handle runs on its stream (params.stream, or a stream
+ *     the library creates when that is NULL).
+ *   - Inputs are copied; the caller keeps ownership of every buffer it passes.
+ */
+#ifndef SGPIC_H
+#define SGPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define SG_OK 0
+#define SG_ERR_INVALID (-1)     /* bad argument (NULL, out of range, non-finite input) */
+#define SG_ERR_UNSUPPORTED (-2) /* valid request this build does not implement */
+#define SG_ERR_OOM (-3)         /* device allocation failed */
+#define SG_ERR_SIZE (-4)        /* caller buffer too small / size mismatch */
+#define SG_ERR_TIMEOUT (-5)     /* a bounded wait expired */
+#define SG_ERR_CUDA (-6)        /* CUDA runtime error (detail in sg_last_error) */
+#define SG_ERR_RANGE (-7)       /* empty or invalid truncation-parameter range */
+#define SG_ERR_NONFINITE (-8)   /* a kernel saw a non-finite particle state */
+#define SG_ERR_STATE (-9)       /* call not valid in the handle's current state */
+
+#define SG_FP32 0
+#define SG_FP64 1
+
+#define SG_TAU_ADAPTIVE (-1)          /* run Algorithm 1 (tauEstimator) every step */
+#define SG_TAU_CONST_PAPER 0          /* eq. grid_constants + eq. particle_constant */
+#define SG_TAU_CONST_EMPIRICAL 1      /* eq. empirical_constants */
+
+typedef struct sg_pic sg_pic; /* opaque run handle; owns all its device memory */
+
+typedef struct {
+  int dim;      /* 2 or 3 */
+  double L[3];  /* box lengths L_m > 0 (L[2] ignored in 2D) */
+} sg_domain;
+
+typedef struct {
+  size_t n;          /* number of particles */
+  int on_device;     /* 1: pointers are device memory; 0: host memory */
+  const void* u[3];  /* positions as fractions of L_m, one array per axis */
+  const void* v[3];  /* velocities, one array per axis */
+  const void* w;     /* per-particle charge q_p; mass is q_p / qm */
+} sg_particles;
+
+typedef struct {
+  size_t n;
+  int on_device;
+  void* u[3];
+  void* v[3];
+  void* w;
+} sg_particles_out;
+
+typedef struct {
+  int precision;      /* SG_FP32 or SG_FP64: particles, deposit, solves */
+  int tau;            /* truncation parameter 1..n, or SG_TAU_ADAPTIVE */
+  double dt;          /* time step */
+  double qm;          /* charge-to-mass ratio q/m (-1 in the paper, Section 5) */
+  double B[3];        /* uniform external magnetic field (Boris push if nonzero;
+                         in 2D only B[2] is allowed) */
+  double Eext_lin[3]; /* external field E_m = Eext_lin[m] (x_m - L_m/2) */
+  double alpha;       /* denoising threshold fraction (Section 4.3.3) */
+  double pc_ref;      /* reference particles per cell (P_c)_ref (Section 4.3.3) */
+  int tau_constants;  /* SG_TAU_CONST_PAPER or SG_TAU_CONST_EMPIRICAL */
+  int sort_every;     /* cell-key sort period in steps; 0 = library default */
+  void* stream;       /* cudaStream_t for all work of the run; NULL = own stream */
+} sg_params;
+
+typedef struct {
+  long long step;               /* steps taken */
+  double t;                     /* step * dt */
+  int tau;                      /* truncation parameter in use */
+  int n_grids;                  /* number of component grids */
+  double charge_total;          /* sum_p q_p (FP64, from the particles) */
+  double charge_combined;       /* sum_i c_i V_i sum_k rho_i(x_k) (FP64) */
+  double charge_grid_max_abs_err; /* max_i |V_i sum_k rho_i - sum_p q_p| */
+  double field_energy;          /* 0.5 h^d sum_j |E_comb(x_j)|^2 at time t */
+  double field_energy_prev;     /* the same at time t - dt (0 before the first step) */
+  double kinetic_energy;        /* 0.5 sum_p m_p v^{-1/2}.v^{+1/2}, time-centred at t - dt */
+  unsigned long long count_checksum; /* sum_p (key_p + 1) mod 2^64 at the last sort */
+} sg_diag;
+
+/* ---- run lifecycle -------------------------------------------------------
+ * sg_pic_init: create a run.  level_n: regular grid 2^n per axis
+ * (Section 4.1); dim 2 or 3 (must equal domain->dim); shape_order must be 1
+ * (CIC / linear, the paper's only shape, eq. restriction), else
+ * SG_ERR_UNSUPPORTED.  Limits: 1 <= tau <= n; dim*n <= 24; 2 <= n.
+ * Copies the particles (host or device), wraps positions into [0,1), sorts
+ * by cell key, deposits, solves and takes the backward half kick
+ * v^{-1/2} = v^0 - (q/m) E(x^0) dt/2 (Boris form when B != 0).
+ * On success *out owns every device buffer of the run. */
+int sg_pic_init(const sg_domain* domain, int level_n, int dim, int shape_order,
+                const sg_particles* particles, const sg_params* params, sg_pic** out);
+
+/* Advance nsteps >= 0 steps (asynchronous on the run's stream; graph replay). */
+int sg_pic_step(sg_pic* h, int nsteps);
+
+/* Synchronise the run's stream and return its FP64 diagnostics. */
+int sg_pic_diagnostics(sg_pic* h, sg_diag* out);
+
+/* Algorithm 1 (tauEstimator, Section 4.3.3) on the current regular-grid
+ * density: FFT, hard threshold (eq. denoising) with
+ * eps = alpha sqrt(pc_ref / P_c) max|rho^|, constants (params.tau_constants),
+ * then grid error + particle noise (eq. 2D/3D_grid_error, 2D/3D_particle_noise)
+ * for tau in [1, n-3] (2D) or [1, n-2] (3D); returns the argmin (ties: the
+ * smallest tau).  est_grid / est_noise (may be NULL) receive the estimates for
+ * tau = 1..cap.  Computed in FP64 on the GPU.  SG_ERR_RANGE if the range is
+ * empty; SG_ERR_UNSUPPORTED for non-cubic boxes (the estimates assume one L).
+ * Does not change the run's tau. */
+int sg_pic_select_tau(sg_pic* h, int* tau, double* est_grid, double* est_noise, int cap);
+
+/* Switch the truncation parameter (1..n) for the following steps: rebuilds
+ * the component-grid set and re-deposits / re-solves the current state. */
+int sg_pic_set_tau(sg_pic* h, int tau);
+
+/* Copy particle states to caller buffers in the ORIGINAL particle order
+ * (the order given at init), whatever sorts happened since.  out->n must
+ * equal the run's particle count; buffers are host or device per on_device. */
+int sg_pic_get_particles(sg_pic* h, const sg_particles_out* out);
+
+/* Cell keys (Morton order of the level-n cell, x lowest bit) of the particles
+ * in their current storage order, and per-cell counts indexed by key.
+ * Recomputes both from the current positions; cap_* are element capacities
+ * (keys: n particles, counts: 2^(d n)); either pointer may be NULL.  Host
+ * buffers. */
+int sg_pic_get_keys(sg_pic* h, uint32_t* keys, uint32_t* counts, size_t cap_keys, size_t cap_counts);
+
+/* Combined field E_comb = sum_i c_i P_i E_i on the regular nodes, FP64,
+ * component-major: out[m * 2^(d n) + node].  Host buffer, cap in doubles. */
+int sg_pic_get_field(sg_pic* h, double* E, size_t cap);
+
+/* Component-grid charge densities rho_i, concatenated in grid order
+ * (sg_pic_get_grids), FP64, host buffer, cap in doubles. */
+int sg_pic_get_grid_charge(sg_pic* h, double* rho, size_t cap);
+
+/* Component fields E_i: for each grid in order, d blocks of 2^|l_i| values
+ * (E_1 block, E_2 block, ...).  FP64 host buffer, cap in doubles. */
+int sg_pic_get_grid_field(sg_pic* h, double* E, size_t cap);
+
+/* Regular-grid charge density rho~ of the current positions (the tau = n
+ * deposit used by Algorithm 1), FP64 host buffer of 2^(d n) values. */
+int sg_pic_get_regular_charge(sg_pic* h, double* rho, size_t cap);
+
+/* Grid set in use: *n_grids receives the count; levels (3 ints per grid,
+ * unused axes 0) and coeffs receive up to cap grids. */
+int sg_pic_get_grids(sg_pic* h, int* n_grids, int* levels, int* coeffs, int cap);
+
+/* Checkpoint: *size receives the byte size; with buf != NULL and *size large
+ * enough, writes the full run state (particles in original order, step, tau,
+ * time-centring).  sg_pic_load restores it into a run created with the same
+ * domain, level, dimension, precision and particle count. */
+int sg_pic_save(sg_pic* h, void* buf, size_t* size);
+int sg_pic_load(sg_pic* h, const void* buf, size_t size);
+
+/* Device pointers of the run's state for callers that chain their own
+ * kernels (valid until the next sort / destroy): u[d], v[d], w arrays in the
+ * current storage order. */
+int sg_pic_device_particles(sg_pic* h, sg_particles_out* out);
+
+/* Count of library kernels launched on this handle so far (graph replays
+ * count each kernel node). */
+int sg_pic_kernel_launches(sg_pic* h, unsigned long long* count);
+
+/* Device-event timing of the run's last sg_pic_step call, per stage
+ * (0 gather-push, 1 sort, 2 deposit, 3 restrict, 4 solve, 5 combine) in
+ * milliseconds, summed over that call's steps.  Enabled with
+ * sg_pic_set_profiling(h, 1), which replaces graph replay by direct launches
+ * with events between the stages while on. */
+int sg_pic_set_profiling(sg_pic* h, int on);
+int sg_pic_stage_times(sg_pic* h, double* ms, int cap);
+
+void sg_pic_destroy(sg_pic* h);
+
+const char* sg_strerror(int status);
+const char* sg_last_error(void);
+const char* sg_version(void);
+
+/* ---- cell-key sort as a stand-alone operation ----------------------------
+ * sg_cell_sort: keys (Morton order of floor(u_m 2^level)), a stable sort
+ * permutation and per-cell counts of n positions u (device pointers,
+ * precision SG_FP32 or SG_FP64, dim arrays).  Outputs (device): keys_sorted
+ * (n), perm (n: sorted position -> input index), counts (2^(dim*level)).
+ * Scratch is allocated and freed inside the call.  stream may be NULL. */
+int sg_cell_sort(int precision, int dim, int level, size_t n, const void* const* u,
+                 uint32_t* keys_sorted, uint32_t* perm, uint32_t* counts, void* stream);
+
+/* ---- serving: independent runs admitted as memory allows -----------------
+ * A server keeps many independent runs resident on one GPU and advances all
+ * of them together in batched launches (one launch per stage covers every
+ * component grid of every resident run).  Requests are admitted in arrival
+ * order while their estimated device footprint fits hbm_budget_bytes and a
+ * slot is free; finished runs retire and free their memory. */
+typedef struct sg_server sg_server;
+
+typedef struct {
+  sg_domain domain;
+  int level_n;
+  int dim;
+  sg_particles particles; /* host arrays are copied at submit time */
+  sg_params params;       /* params.stream is ignored (the server's stream) */
+  int nsteps;
+} sg_request;
+
+#define SG_REQ_QUEUED 0
+#define SG_REQ_RUNNING 1
+#define SG_REQ_DONE 2
+#define SG_REQ_FAILED 3
+
+int sg_serve_create(size_t hbm_budget_bytes, int max_slots, sg_server** out);
+/* Queue a request (copies its particle arrays); returns a ticket. */
+int sg_serve_submit(sg_server* s, const sg_request* req, unsigned long long* ticket);
+/* Admit what fits, then advance every resident run by one step. *active
+ * receives the number of resident runs after the call. */
+int sg_serve_tick(sg_server* s, int* active);
+/* State of a ticket and (when running or done) its latest diagnostics. */
+int sg_serve_poll(sg_server* s, unsigned long long ticket, int* state, sg_diag* last);
+/* Final particle state of a finished request (original order). */
+int sg_serve_result(sg_server* s, unsigned long long ticket, const sg_particles_out* out);
+/* Per-step latency percentiles (ms) over all steps served so far and
+ * aggregate particle-steps per second of device time. */
+int sg_serve_stats(sg_server* s, double* p50_ms, double* p99_ms, double* particle_steps_per_s,
+                   unsigned long long* steps_served);
+void sg_serve_destroy(sg_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGPIC_H */

@@ -1,0 +1,126 @@
+// Signed combination of the component fields on the regular nodes:
+//   E_comb(x_j) = sum_i c_i (P_i E_i)(x_j)
+// (eq. sparse_filter's c_i and P_i of eq. restriction, applied to the
+// fields).  One block per regular row (a y line in 2D, a (y, z) line in
+// 3D).  For every grid the block interpolates the grid's field in the
+// transverse axes onto the row's coordinate, giving a coarse x-line of
+// 2^l_1 values that is added, times c_i, into a per-level accumulator.  The
+// x-prolongation is then applied once per level by Horner's scheme
+// (prolong level l to l+1, add level l+1, ...), which is exact for nested
+// node-centred grids.  Accumulation is float-float (FP32 path) or double
+// (FP64 path); the row is written as hi / lo planes and contributes its
+// share of sum |E_comb|^2 to the field energy.
+#include "sg_kernels.cuh"
+
+namespace sg {
+
+template <typename real, int D>
+__global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ grids, int ngrids, int lmin,
+                                                 const real* __restrict__ E, size_t S, int n, real* __restrict__ Ehi,
+                                                 float* __restrict__ Elo, double* __restrict__ partials) {
+  extern __shared__ unsigned char smem_raw[];
+  Acc<real>* A = reinterpret_cast<Acc<real>*>(smem_raw);  // level l at [2^l, 2^(l+1))
+  __shared__ double red[32];
+  const int N = 1 << n;
+  const size_t ND = (size_t)N * (D == 2 ? N : (size_t)N * N);
+  const int row = blockIdx.x;
+  const int y = row & (N - 1);
+  const int z = (D == 3) ? (row >> n) : 0;
+  Acc<real> energy;
+  for (int m = 0; m < D; ++m) {
+    for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) A[i] = Acc<real>();
+    __syncthreads();
+    for (int gi = 0; gi < ngrids; ++gi) {
+      const GridDesc g = grids[gi];
+      const int l1 = g.l[0];
+      const int nx = 1 << l1;
+      const int ry = n - g.l[1];
+      const int ny = 1 << g.l[1];
+      const int ky0 = y >> ry;
+      const int ky1 = (ky0 + 1) & (ny - 1);
+      const real fy = (real)(y & ((1 << ry) - 1)) / (real)(1 << ry);
+      int kz0 = 0, kz1 = 0;
+      real fz = (real)0;
+      int nz = 1;
+      if (D == 3) {
+        const int rz = n - g.l[2];
+        nz = 1 << g.l[2];
+        kz0 = z >> rz;
+        kz1 = (kz0 + 1) & (nz - 1);
+        fz = (real)(z & ((1 << rz) - 1)) / (real)(1 << rz);
+      }
+      const real* base = E + (size_t)m * S + g.offset;
+      const real c = (real)g.coeff;
+      for (int kx = threadIdx.x; kx < nx; kx += blockDim.x) {
+        Acc<real> val;
+        if (D == 2) {
+          val.add_prod((real)1 - fy, base[(size_t)ky0 * nx + kx]);
+          if (fy != (real)0) val.add_prod(fy, base[(size_t)ky1 * nx + kx]);
+        } else {
+          const real wz0 = (real)1 - fz;
+          val.add_prod(((real)1 - fy) * wz0, base[((size_t)kz0 * ny + ky0) * nx + kx]);
+          if (fy != (real)0) val.add_prod(fy * wz0, base[((size_t)kz0 * ny + ky1) * nx + kx]);
+          if (fz != (real)0) {
+            val.add_prod(((real)1 - fy) * fz, base[((size_t)kz1 * ny + ky0) * nx + kx]);
+            if (fy != (real)0) val.add_prod(fy * fz, base[((size_t)kz1 * ny + ky1) * nx + kx]);
+          }
+        }
+        val.scale(c);  // |c| is 1 or 2 (a power of two): exact
+        A[nx + kx].add_acc(val);
+      }
+      // the same thread owns (level, kx) for every grid: no sync needed here
+    }
+    __syncthreads();
+    for (int l = lmin; l < n; ++l) {
+      const int cnt = 2 << l;  // size of level l+1
+      const int half = 1 << l;
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int k = e >> 1;
+        Acc<real> v = A[half + k];
+        if (e & 1) {
+          v.add_acc(A[half + ((k + 1) & (half - 1))]);
+          v.scale((real)0.5);
+        }
+        A[cnt + e].add_acc(v);
+      }
+      __syncthreads();
+    }
+    for (int x = threadIdx.x; x < N; x += blockDim.x) {
+      const Acc<real> v = A[N + x];
+      const size_t o = (size_t)m * ND + (size_t)row * N + x;
+      Ehi[o] = (real)v.hi();
+      if (Elo) Elo[o] = (float)v.lo();
+      energy.add_prod((real)v.hi(), (real)v.hi());
+      energy.add((real)2 * (real)v.hi() * (real)v.lo());
+    }
+    __syncthreads();
+  }
+  double tot = block_sum_double(energy.to_double(), red);
+  if (threadIdx.x == 0) partials[row] = tot;
+}
+
+template <typename real, int D>
+int launch_combine(const GridDesc* grids, int ngrids, int lmin, const real* E, size_t S, int n, real* Ehi,
+                   float* Elo, double* energy_partials, cudaStream_t s) {
+  const int N = 1 << n;
+  unsigned rows = (unsigned)(D == 2 ? N : N * N);
+  size_t smem = (size_t)2 * N * sizeof(Acc<real>);
+  static bool attr_set = false;
+  if (!attr_set) {
+    SG_CUDA(cudaFuncSetAttribute(k_combine<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  k_combine<real, D><<<rows, 256, smem, s>>>(grids, ngrids, lmin, E, S, n, Ehi, Elo, energy_partials);
+  SG_CHECK_LAUNCH();
+  return SG_OK;
+}
+
+#define SG_INST_COMB(real, D)                                                                         \
+  template int launch_combine<real, D>(const GridDesc*, int, int, const real*, size_t, int, real*, float*, \
+                                       double*, cudaStream_t);
+SG_INST_COMB(float, 2)
+SG_INST_COMB(float, 3)
+SG_INST_COMB(double, 2)
+SG_INST_COMB(double, 3)
+
+}  // namespace sg

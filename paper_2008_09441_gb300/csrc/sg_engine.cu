@@ -1,0 +1,1058 @@
+// Engine<real, D>: one sparse-grid PIC run on one GPU.
+#include <algorithm>
+#include <map>
+#include <set>
+
+#include "sg_engine.cuh"
+
+namespace sg {
+
+std::vector<GridSpec> combination_grids(int d, int n, int tau) {
+  std::vector<GridSpec> out;
+  for (int q = 0; q < d; ++q) {
+    int target = n + (d - 1) * tau - q;
+    int binom = (d == 3 && q == 1) ? 2 : 1;  // C(d-1, q) for d <= 3
+    int coeff = (q % 2 ? -1 : 1) * binom;
+    if (d == 2) {
+      for (int a = tau; a <= n; ++a)
+        for (int b = tau; b <= n; ++b)
+          if (a + b == target) out.push_back({{a, b, 0}, coeff});
+    } else {
+      for (int a = tau; a <= n; ++a)
+        for (int b = tau; b <= n; ++b)
+          for (int c = tau; c <= n; ++c)
+            if (a + b + c == target) out.push_back({{a, b, c}, coeff});
+    }
+  }
+  return out;
+}
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+template <typename real, int D>
+class Engine final : public EngineBase {
+ public:
+  ~Engine() override { release(); }
+
+  int init(const EngineConfig& cfg, const sg_particles* parts, cudaStream_t stream) override {
+    cfg_ = cfg;
+    n_ = cfg.n;
+    N_ = 1 << n_;
+    ND_ = (size_t)1;
+    for (int m = 0; m < D; ++m) ND_ *= (size_t)N_;
+    np_ = parts->n;
+    if (stream) {
+      stream_ = stream;
+      own_stream_ = false;
+    } else {
+      SG_CUDA(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
+      own_stream_ = true;
+    }
+    sort_every_ = cfg.sort_every > 0 ? cfg.sort_every : 1;
+    tau_ = cfg.tau == SG_TAU_ADAPTIVE ? 1 : cfg.tau;
+    adaptive_ = cfg.tau == SG_TAU_ADAPTIVE;
+
+    // ---- particles (two sets for the sort's out-of-place permutation)
+    size_t pb = std::max<size_t>(np_, 1);
+    for (int set = 0; set < 2; ++set) {
+      for (int m = 0; m < D; ++m) {
+        SG_TRY(alloc((void**)&P_[set].u[m], pb * sizeof(real)));
+        SG_TRY(alloc((void**)&P_[set].v[m], pb * sizeof(real)));
+      }
+      SG_TRY(alloc((void**)&P_[set].w, pb * sizeof(real)));
+      SG_TRY(alloc((void**)&P_[set].pid, pb * sizeof(uint32_t)));
+    }
+    cur_ = 0;
+    SG_TRY(upload_particles(parts));
+    SG_TRY(alloc((void**)&keys_, pb * 4));
+    SG_TRY(alloc((void**)&keys_alt_, pb * 4));
+    SG_TRY(alloc((void**)&vals_, pb * 4));
+    SG_TRY(alloc((void**)&vals_alt_, pb * 4));
+    SG_TRY(alloc((void**)&sort_scr_, sort_scratch_words(np_) * 4));
+    sort_scratch_bind(scr_, sort_scr_, np_);
+
+    // ---- small device records
+    SG_TRY(alloc((void**)&dd_, sizeof(DevDiag)));
+    SG_TRY(alloc((void**)&status_, sizeof(unsigned)));
+    SG_TRY(alloc((void**)&checksum_, sizeof(unsigned long long)));
+    SG_CUDA(cudaMemsetAsync(dd_, 0, sizeof(DevDiag), stream_));
+    SG_CUDA(cudaMemsetAsync(status_, 0, sizeof(unsigned), stream_));
+    SG_CUDA(cudaMemsetAsync(checksum_, 0, sizeof(unsigned long long), stream_));
+    nke_ = push_blocks(np_);
+    SG_TRY(alloc((void**)&ke_partials_, (size_t)nke_ * sizeof(double)));
+    SG_CUDA(cudaMemsetAsync(ke_partials_, 0, (size_t)nke_ * sizeof(double), stream_));
+
+    // ---- regular grid, combined field, twiddles
+    SG_TRY(alloc((void**)&rho_reg_, ND_ * sizeof(real)));
+    SG_TRY(alloc((void**)&Ehi_, (size_t)D * ND_ * sizeof(real)));
+    if (sizeof(real) == 4) SG_TRY(alloc((void**)&Elo_, (size_t)D * ND_ * sizeof(float)));
+    nrows_ = (int)(ND_ / (size_t)N_);
+    SG_TRY(alloc((void**)&fe_partials_, (size_t)nrows_ * sizeof(double)));
+    {
+      std::vector<cplx<real>> tw(std::max(1, N_ / 2));
+      for (int k = 0; k < N_ / 2; ++k) {
+        double a = 2.0 * M_PI * (double)k / (double)N_;
+        tw[k].x = (real)std::cos(a);
+        tw[k].y = (real)(-std::sin(a));
+      }
+      SG_TRY(alloc((void**)&tw_, tw.size() * sizeof(cplx<real>)));
+      SG_CUDA(cudaMemcpyAsync(tw_, tw.data(), tw.size() * sizeof(cplx<real>), cudaMemcpyHostToDevice, stream_));
+      SG_CUDA(cudaStreamSynchronize(stream_));
+    }
+
+    // ---- charges: sum_p q_p in FP64 (fixed during the run)
+    {
+      const int nb = 256;
+      double* part = nullptr;
+      SG_TRY(alloc((void**)&part, nb * sizeof(double)));
+      SG_TRY(launch_sum_to_double<real>(P_[cur_].w, np_, part, nb, stream_));
+      std::vector<double> h(nb);
+      SG_CUDA(cudaMemcpyAsync(h.data(), part, nb * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+      SG_CUDA(cudaStreamSynchronize(stream_));
+      charge_total_ = 0;
+      for (double x : h) charge_total_ += x;
+      free_one(part);
+    }
+    unsigned st = 0;
+    SG_CUDA(cudaMemcpy(&st, status_, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (st & ST_NONFINITE) {
+      set_error("sg_pic_init: non-finite particle position, velocity or charge");
+      return SG_ERR_NONFINITE;
+    }
+
+    SG_TRY(build_grid_set(tau_));
+    // Initial state: sort, fields at t = 0, backward half kick.
+    SG_TRY(enqueue_sort());
+    SG_TRY(enqueue_fields());
+    SG_TRY(launch_finalize_step(fe_partials_, nrows_, nullptr, 0, fe_scale(), dd_, stream_));
+    SG_TRY(enqueue_push(-0.5 * cfg_.dt, false, nullptr));
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    step_ = 0;
+    return check_status();
+  }
+
+  int step(int nsteps) override {
+    if (nsteps < 0) {
+      set_error("sg_pic_step: nsteps < 0");
+      return SG_ERR_INVALID;
+    }
+    if (profiling_) std::fill(stage_ms_, stage_ms_ + 6, 0.0);
+    for (int k = 0; k < nsteps; ++k) {
+      bool do_sort = ((step_ + 1) % sort_every_) == 0;
+      if (adaptive_) {
+        SG_TRY(step_adaptive(do_sort));
+      } else if (profiling_) {
+        SG_TRY(step_profiled(do_sort));
+      } else {
+        SG_TRY(step_graph(do_sort));
+      }
+      ++step_;
+    }
+    return SG_OK;
+  }
+
+  int diagnostics(sg_diag* out) override {
+    SG_TRY(launch_grid_charges<real>(grids_dev_, ngrids_, rho_arena_, nullptr, charges_dev_, stream_));
+    DevDiag dd;
+    SG_CUDA(cudaMemcpyAsync(&dd, dd_, sizeof(DevDiag), cudaMemcpyDeviceToHost, stream_));
+    std::vector<double> ch(ngrids_);
+    SG_CUDA(cudaMemcpyAsync(ch.data(), charges_dev_, ngrids_ * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+    unsigned long long cks = 0;
+    SG_CUDA(cudaMemcpyAsync(&cks, checksum_, sizeof(cks), cudaMemcpyDeviceToHost, stream_));
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    std::memset(out, 0, sizeof(*out));
+    out->step = step_;
+    out->t = (double)step_ * cfg_.dt;
+    out->tau = tau_;
+    out->n_grids = ngrids_;
+    out->charge_total = charge_total_;
+    double comb = 0, maxerr = 0;
+    for (int i = 0; i < ngrids_; ++i) {
+      comb += (double)grids_[i].coeff * ch[i];
+      maxerr = std::max(maxerr, std::fabs(ch[i] - charge_total_));
+    }
+    out->charge_combined = comb;
+    out->charge_grid_max_abs_err = maxerr;
+    out->field_energy = dd.field_energy;
+    out->field_energy_prev = dd.field_energy_prev;
+    out->kinetic_energy = dd.kinetic_energy;
+    out->count_checksum = cks;
+    return check_status();
+  }
+
+  int select_tau(int* tau, double* est_grid, double* est_noise, int cap) override {
+    int hi = D == 2 ? n_ - 3 : n_ - 2;
+    if (hi < 1) {
+      set_error("sg_pic_select_tau: empty tau range [1, n-3] (2D) / [1, n-2] (3D)");
+      return SG_ERR_RANGE;
+    }
+    for (int m = 1; m < D; ++m)
+      if (std::fabs(cfg_.L[m] - cfg_.L[0]) > 1e-12 * std::fabs(cfg_.L[0])) {
+        set_error("sg_pic_select_tau: the estimates assume a cubic box (one L)");
+        return SG_ERR_UNSUPPORTED;
+      }
+    SG_TRY(ensure_estimator_buffers());
+    const double L = cfg_.L[0];
+    // rho~ of the current positions (the deposit of the last step).
+    SG_TRY(launch_to_double<real>(rho_reg_, est_rho_, ND_, stream_));
+    SG_TRY(launch_real_to_cplx(est_rho_, est_z_, ND_, 1.0 / (double)ND_, stream_));
+    for (int ax = 0; ax < D; ++ax) SG_TRY(launch_fft_array_axis<double>(est_z_, D, n_, ax, false, tw64_, n_, stream_));
+    SG_TRY(launch_maxabs_cplx(est_z_, ND_, est_scalar_ + 0, stream_));
+    const double Pc = (double)np_ / (double)ND_;
+    const double frac = cfg_.alpha * std::sqrt(cfg_.pc_ref / Pc);
+    SG_TRY(launch_threshold(est_z_, ND_, est_scalar_ + 0, frac, stream_));
+    double kfac[3] = {0, 0, 0};
+    for (int m = 0; m < D; ++m) kfac[m] = 2.0 * M_PI / cfg_.L[m];
+    // masks: kappa_m (single axis), beta (pairs), gamma (all three)
+    std::vector<int> masks;
+    for (int m = 0; m < D; ++m) masks.push_back(1 << m);
+    if (D == 2) {
+      masks.push_back(3);
+    } else {
+      masks.push_back(3);  // xy
+      masks.push_back(6);  // yz
+      masks.push_back(5);  // zx
+      masks.push_back(7);  // xyz
+    }
+    const bool paper = cfg_.tau_constants == SG_TAU_CONST_PAPER;
+    for (size_t i = 0; i < masks.size(); ++i) {
+      if (paper) {
+        SG_TRY(launch_kmult(est_z_, est_w_, D, n_, kfac, masks[i], stream_));
+        for (int ax = 0; ax < D; ++ax)
+          SG_TRY(launch_fft_array_axis<double>(est_w_, D, n_, ax, true, tw64_, n_, stream_));
+        SG_TRY(launch_maxabs_real_part(est_w_, ND_, est_scalar_ + 1 + i, stream_));
+      } else {
+        SG_TRY(launch_maxabs_kmult(est_z_, D, n_, kfac, masks[i], est_scalar_ + 1 + i, stream_));
+      }
+    }
+    SG_TRY(launch_maxabs_real(est_rho_, ND_, est_scalar_ + 8, stream_));
+    double sc[9];
+    SG_CUDA(cudaMemcpyAsync(sc, est_scalar_, sizeof(sc), cudaMemcpyDeviceToHost, stream_));
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    double kappa[3] = {0, 0, 0}, beta[3] = {0, 0, 0}, gamma = 0, sigma;
+    const double Q = std::fabs(charge_total_);
+    if (paper) {
+      for (int m = 0; m < D; ++m) kappa[m] = 0.25 * sc[1 + m];
+      if (D == 2) {
+        beta[0] = sc[1 + 2] / 72.0;
+      } else {
+        beta[0] = sc[1 + 3] / 72.0;
+        beta[1] = sc[1 + 4] / 72.0;
+        beta[2] = sc[1 + 5] / 72.0;
+        gamma = sc[1 + 6] / 864.0;
+      }
+      sigma = std::sqrt(std::pow(2.0 / 3.0, D) * Q * sc[8]);
+    } else {
+      for (int m = 0; m < D; ++m) kappa[m] = sc[1 + m];
+      if (D == 2) {
+        beta[0] = sc[1 + 2];
+      } else {
+        beta[0] = sc[1 + 3];
+        beta[1] = sc[1 + 4];
+        beta[2] = sc[1 + 5];
+        gamma = sc[1 + 6];
+      }
+      sigma = std::sqrt(Q * sc[8]);
+    }
+    const double h = L / (double)N_;
+    int best = 1;
+    double best_total = 0;
+    for (int t = 1; t <= hi; ++t) {
+      const double m = (double)(n_ - t);
+      double g, z;
+      if (D == 2) {
+        g = h * h * (kappa[0] + kappa[1] + beta[0] * L * L * std::pow(2.0, -2.0 * t) * (5 * m + 1));
+        z = sigma * std::pow(2.0, 0.5 * (t - 1)) * (m * (1 + std::sqrt(2.0)) + std::sqrt(2.0)) /
+            std::sqrt((double)np_ * h * L);
+      } else {
+        g = h * h *
+            (kappa[0] + kappa[1] + kappa[2] + (beta[0] + beta[1] + beta[2]) * L * L * std::pow(2.0, -2.0 * t) * (5 * m + 1) +
+             gamma * std::pow(L, 4) * std::pow(2.0, -(4.0 * t + 1)) * (25 * m * m - 5 * m + 2));
+        z = sigma * std::pow(2.0, (double)(t - 2)) *
+            ((3 + std::sqrt(2.0)) * m * m + (5 + std::sqrt(2.0)) * m + 4) / std::sqrt((double)np_ * h * L * L);
+      }
+      if (est_grid && t <= cap) est_grid[t - 1] = g;
+      if (est_noise && t <= cap) est_noise[t - 1] = z;
+      if (t == 1 || g + z < best_total) {
+        best = t;
+        best_total = g + z;
+      }
+    }
+    *tau = best;
+    return SG_OK;
+  }
+
+  int set_tau(int tau) override {
+    if (tau < 1 || tau > n_) {
+      set_error("sg_pic_set_tau: tau outside [1, n]");
+      return SG_ERR_INVALID;
+    }
+    if (tau == tau_) return SG_OK;
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    SG_TRY(build_grid_set(tau));
+    SG_TRY(enqueue_restrict_solve_combine());
+    SG_TRY(launch_finalize_step(fe_partials_, nrows_, nullptr, 0, fe_scale(), dd_, stream_));
+    return SG_OK;
+  }
+
+  int get_particles(const sg_particles_out* out) override {
+    if (!out || out->n != np_) {
+      set_error("sg_pic_get_particles: out->n must equal the run's particle count");
+      return SG_ERR_SIZE;
+    }
+    if (np_ == 0) return SG_OK;
+    PArrays<real, D> dst;
+    std::vector<void*> temps;
+    for (int m = 0; m < D; ++m) {
+      dst.u[m] = (real*)out->u[m];
+      dst.v[m] = (real*)out->v[m];
+    }
+    dst.w = (real*)out->w;
+    dst.pid = nullptr;
+    if (!out->on_device) {
+      // stage in the other particle set (free between steps)
+      const int o = cur_ ^ 1;
+      for (int m = 0; m < D; ++m) {
+        dst.u[m] = P_[o].u[m];
+        dst.v[m] = P_[o].v[m];
+      }
+      dst.w = P_[o].w;
+    }
+    SG_TRY(launch_unpermute<real, D>(P_[cur_], dst, np_, stream_));
+    if (!out->on_device) {
+      for (int m = 0; m < D; ++m) {
+        if (out->u[m]) SG_CUDA(cudaMemcpyAsync(out->u[m], dst.u[m], np_ * sizeof(real), cudaMemcpyDeviceToHost, stream_));
+        if (out->v[m]) SG_CUDA(cudaMemcpyAsync(out->v[m], dst.v[m], np_ * sizeof(real), cudaMemcpyDeviceToHost, stream_));
+      }
+      if (out->w) SG_CUDA(cudaMemcpyAsync(out->w, dst.w, np_ * sizeof(real), cudaMemcpyDeviceToHost, stream_));
+    }
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    return SG_OK;
+  }
+
+  int get_keys(uint32_t* keys, uint32_t* counts, size_t cap_keys, size_t cap_counts) override {
+    if (keys && cap_keys < np_) {
+      set_error("sg_pic_get_keys: key buffer too small");
+      return SG_ERR_SIZE;
+    }
+    if (counts && cap_counts < ND_) {
+      set_error("sg_pic_get_keys: count buffer too small");
+      return SG_ERR_SIZE;
+    }
+    SG_TRY(launch_keys<real, D>(P_[cur_], np_, n_, keys_alt_, nullptr, nullptr, status_, stream_));
+    if (keys) SG_CUDA(cudaMemcpyAsync(keys, keys_alt_, np_ * 4, cudaMemcpyDeviceToHost, stream_));
+    if (counts) {
+      uint32_t* dcounts = nullptr;
+      SG_TRY(alloc((void**)&dcounts, ND_ * 4));
+      SG_CUDA(cudaMemsetAsync(dcounts, 0, ND_ * 4, stream_));
+      SG_TRY(launch_counts(keys_alt_, np_, dcounts, stream_));
+      SG_CUDA(cudaMemcpyAsync(counts, dcounts, ND_ * 4, cudaMemcpyDeviceToHost, stream_));
+      SG_CUDA(cudaStreamSynchronize(stream_));
+      free_one(dcounts);
+    }
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    return SG_OK;
+  }
+
+  int get_field(double* E, size_t cap) override {
+    if (cap < (size_t)D * ND_) return size_error("sg_pic_get_field");
+    double* tmp = nullptr;
+    SG_TRY(alloc((void**)&tmp, (size_t)D * ND_ * sizeof(double)));
+    if (sizeof(real) == 4)
+      SG_TRY(launch_ff_to_double((const float*)Ehi_, Elo_, tmp, (size_t)D * ND_, stream_));
+    else
+      SG_TRY(launch_to_double<real>(Ehi_, tmp, (size_t)D * ND_, stream_));
+    SG_CUDA(cudaMemcpyAsync(E, tmp, (size_t)D * ND_ * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    free_one(tmp);
+    return SG_OK;
+  }
+
+  int get_grid_charge(double* rho, size_t cap) override {
+    if (cap < S_) return size_error("sg_pic_get_grid_charge");
+    return copy_to_host_double(rho_arena_, rho, S_);
+  }
+
+  int get_grid_field(double* E, size_t cap) override {
+    if (cap < (size_t)D * S_) return size_error("sg_pic_get_grid_field");
+    std::vector<double> all((size_t)D * S_);
+    SG_TRY(copy_to_host_double(E_arena_, all.data(), (size_t)D * S_));
+    size_t o = 0;
+    for (int g = 0; g < ngrids_; ++g) {
+      size_t sz = (size_t)gdesc_[g].size, off = (size_t)gdesc_[g].offset;
+      for (int m = 0; m < D; ++m) {
+        std::memcpy(E + o, all.data() + (size_t)m * S_ + off, sz * sizeof(double));
+        o += sz;
+      }
+    }
+    return SG_OK;
+  }
+
+  int get_regular_charge(double* rho, size_t cap) override {
+    if (cap < ND_) return size_error("sg_pic_get_regular_charge");
+    return copy_to_host_double(rho_reg_, rho, ND_);
+  }
+
+  int get_grids(int* n_grids, int* levels, int* coeffs, int cap) override {
+    if (n_grids) *n_grids = ngrids_;
+    for (int g = 0; g < ngrids_ && g < cap; ++g) {
+      if (levels)
+        for (int m = 0; m < 3; ++m) levels[3 * g + m] = grids_[g].l[m];
+      if (coeffs) coeffs[g] = grids_[g].coeff;
+    }
+    return SG_OK;
+  }
+
+  // Checkpoint layout: header, then u[d], v[d], w arrays in original order.
+  struct Header {
+    char magic[8];
+    int version, dim, precision, n, tau, adaptive;
+    long long np, step;
+    double dt;
+    DevDiag dd;
+  };
+
+  int save(void* buf, size_t* size) override {
+    size_t need = sizeof(Header) + (size_t)(2 * D + 1) * np_ * sizeof(real);
+    if (!buf || *size < need) {
+      *size = need;
+      return buf ? SG_ERR_SIZE : SG_OK;
+    }
+    Header hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, "SGPICv1", 8);
+    hd.version = 1;
+    hd.dim = D;
+    hd.precision = sizeof(real) == 4 ? SG_FP32 : SG_FP64;
+    hd.n = n_;
+    hd.tau = tau_;
+    hd.adaptive = adaptive_ ? 1 : 0;
+    hd.np = (long long)np_;
+    hd.step = step_;
+    hd.dt = cfg_.dt;
+    SG_CUDA(cudaMemcpyAsync(&hd.dd, dd_, sizeof(DevDiag), cudaMemcpyDeviceToHost, stream_));
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    std::memcpy(buf, &hd, sizeof(hd));
+    char* p = (char*)buf + sizeof(hd);
+    sg_particles_out o;
+    std::memset(&o, 0, sizeof(o));
+    o.n = np_;
+    o.on_device = 0;
+    for (int m = 0; m < D; ++m) {
+      o.u[m] = p + (size_t)m * np_ * sizeof(real);
+      o.v[m] = p + (size_t)(D + m) * np_ * sizeof(real);
+    }
+    o.w = p + (size_t)(2 * D) * np_ * sizeof(real);
+    SG_TRY(get_particles(&o));
+    *size = need;
+    return SG_OK;
+  }
+
+  int load(const void* buf, size_t size) override {
+    if (!buf || size < sizeof(Header)) return size_error("sg_pic_load");
+    Header hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (std::memcmp(hd.magic, "SGPICv1", 8) != 0 || hd.dim != D ||
+        hd.precision != (sizeof(real) == 4 ? SG_FP32 : SG_FP64) || hd.n != n_ || hd.np != (long long)np_) {
+      set_error("sg_pic_load: checkpoint does not match this run (magic, dim, precision, level or particle count)");
+      return SG_ERR_INVALID;
+    }
+    size_t need = sizeof(Header) + (size_t)(2 * D + 1) * np_ * sizeof(real);
+    if (size < need) return size_error("sg_pic_load");
+    const char* p = (const char*)buf + sizeof(hd);
+    sg_particles in;
+    std::memset(&in, 0, sizeof(in));
+    in.n = np_;
+    in.on_device = 0;
+    for (int m = 0; m < D; ++m) {
+      in.u[m] = p + (size_t)m * np_ * sizeof(real);
+      in.v[m] = p + (size_t)(D + m) * np_ * sizeof(real);
+    }
+    in.w = p + (size_t)(2 * D) * np_ * sizeof(real);
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    cur_ = 0;
+    SG_TRY(upload_particles(&in));
+    if (hd.tau != tau_) SG_TRY(build_grid_set(hd.tau));
+    adaptive_ = hd.adaptive != 0;
+    SG_TRY(enqueue_sort());
+    SG_TRY(enqueue_fields());
+    SG_CUDA(cudaMemcpyAsync(dd_, &hd.dd, sizeof(DevDiag), cudaMemcpyHostToDevice, stream_));
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    step_ = hd.step;
+    invalidate_graphs();
+    return check_status();
+  }
+
+  int device_particles(sg_particles_out* out) override {
+    std::memset(out, 0, sizeof(*out));
+    out->n = np_;
+    out->on_device = 1;
+    for (int m = 0; m < D; ++m) {
+      out->u[m] = P_[cur_].u[m];
+      out->v[m] = P_[cur_].v[m];
+    }
+    out->w = P_[cur_].w;
+    return SG_OK;
+  }
+
+  int set_profiling(int on) override {
+    profiling_ = on != 0;
+    if (profiling_ && !ev_[0]) {
+      for (int i = 0; i < 8; ++i) SG_CUDA(cudaEventCreate(&ev_[i]));
+    }
+    return SG_OK;
+  }
+
+  int stage_times(double* ms, int cap) override {
+    for (int i = 0; i < 6 && i < cap; ++i) ms[i] = stage_ms_[i];
+    return SG_OK;
+  }
+
+  unsigned long long kernel_launches() const override { return launches_; }
+  size_t device_bytes() const override { return bytes_; }
+  cudaStream_t stream() const override { return stream_; }
+  size_t n_particles() const override { return np_; }
+  long long steps_done() const override { return step_; }
+
+ private:
+  // ------------------------------------------------------------ memory
+  int alloc(void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+      return SG_ERR_OOM;
+    }
+    bufs_.push_back({*p, bytes});
+    bytes_ += bytes;
+    return SG_OK;
+  }
+  void free_one(void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < bufs_.size(); ++i)
+      if (bufs_[i].p == p) {
+        cudaFree(p);
+        bytes_ -= bufs_[i].bytes;
+        bufs_.erase(bufs_.begin() + i);
+        return;
+      }
+  }
+  void release() {
+    invalidate_graphs();
+    if (stream_) cudaStreamSynchronize(stream_);
+    for (auto& b : bufs_) cudaFree(b.p);
+    bufs_.clear();
+    for (int i = 0; i < 8; ++i)
+      if (ev_[i]) cudaEventDestroy(ev_[i]);
+    if (own_stream_ && stream_) cudaStreamDestroy(stream_);
+    stream_ = nullptr;
+  }
+  int size_error(const char* who) {
+    set_error(std::string(who) + ": caller buffer too small");
+    return SG_ERR_SIZE;
+  }
+  int copy_to_host_double(const real* src, double* dst, size_t n) {
+    double* tmp = nullptr;
+    SG_TRY(alloc((void**)&tmp, n * sizeof(double)));
+    SG_TRY(launch_to_double<real>(src, tmp, n, stream_));
+    SG_CUDA(cudaMemcpyAsync(dst, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    free_one(tmp);
+    return SG_OK;
+  }
+  int check_status() {
+    unsigned st = 0;
+    SG_CUDA(cudaMemcpyAsync(&st, status_, sizeof(unsigned), cudaMemcpyDeviceToHost, stream_));
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    if (st & ST_NONFINITE) {
+      set_error("a kernel produced a non-finite particle state");
+      return SG_ERR_NONFINITE;
+    }
+    return SG_OK;
+  }
+
+  int upload_particles(const sg_particles* parts) {
+    cudaMemcpyKind kind = parts->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (np_ > 0) {
+      for (int m = 0; m < D; ++m) {
+        if (!parts->u[m] || !parts->v[m]) {
+          set_error("sg_pic_init: NULL particle array");
+          return SG_ERR_INVALID;
+        }
+        SG_CUDA(cudaMemcpyAsync(P_[cur_].u[m], parts->u[m], np_ * sizeof(real), kind, stream_));
+        SG_CUDA(cudaMemcpyAsync(P_[cur_].v[m], parts->v[m], np_ * sizeof(real), kind, stream_));
+      }
+      if (!parts->w) {
+        set_error("sg_pic_init: NULL charge array");
+        return SG_ERR_INVALID;
+      }
+      SG_CUDA(cudaMemcpyAsync(P_[cur_].w, parts->w, np_ * sizeof(real), kind, stream_));
+      SG_TRY(launch_wrap_check<real, D>(P_[cur_], np_, status_, stream_));
+    }
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    return SG_OK;
+  }
+
+  // ------------------------------------------------------------ grid set
+  int build_grid_set(int tau) {
+    invalidate_graphs();
+    tau_ = tau;
+    grids_ = combination_grids(D, n_, tau);
+    ngrids_ = (int)grids_.size();
+    gdesc_.assign(ngrids_, GridDesc{});
+    size_t off = 0;
+    lmin_ = n_;
+    for (int g = 0; g < ngrids_; ++g) {
+      GridDesc& d = gdesc_[g];
+      std::memset(&d, 0, sizeof(d));
+      int sz = 1;
+      double vol = 1;
+      for (int m = 0; m < 3; ++m) d.l[m] = grids_[g].l[m];
+      for (int m = 0; m < D; ++m) {
+        sz <<= d.l[m];
+        vol *= cfg_.L[m] / (double)(1 << d.l[m]);
+        d.kfac[m] = 2.0 * M_PI / cfg_.L[m];
+      }
+      d.coeff = grids_[g].coeff;
+      d.offset = (int)off;
+      d.size = sz;
+      d.vol = vol;
+      off += (size_t)sz;
+      lmin_ = std::min(lmin_, d.l[0]);
+    }
+    S_ = off;
+    // (re)allocate arenas
+    for (void* p : grid_bufs_) free_one(p);
+    grid_bufs_.clear();
+    SG_TRY(galloc((void**)&grids_dev_, ngrids_ * sizeof(GridDesc)));
+    SG_TRY(galloc((void**)&charges_dev_, ngrids_ * sizeof(double)));
+    SG_TRY(galloc((void**)&rho_arena_, S_ * sizeof(real)));
+    SG_TRY(galloc((void**)&A_, S_ * sizeof(cplx<real>)));
+    SG_TRY(galloc((void**)&B_, (size_t)D * S_ * sizeof(cplx<real>)));
+    SG_TRY(galloc((void**)&E_arena_, (size_t)D * S_ * sizeof(real)));
+    SG_CUDA(cudaMemcpyAsync(grids_dev_, gdesc_.data(), ngrids_ * sizeof(GridDesc), cudaMemcpyHostToDevice, stream_));
+    SG_TRY(build_restrict_jobs());
+    SG_TRY(build_fft_jobs());
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    return SG_OK;
+  }
+  int galloc(void** p, size_t bytes) {
+    SG_TRY(alloc(p, bytes));
+    grid_bufs_.push_back(*p);
+    return SG_OK;
+  }
+
+  struct Pass {
+    LineJob* dev = nullptr;
+    int njobs = 0, nblocks = 0, smem = 0;
+  };
+  struct FPass {
+    FftJob* dev = nullptr;
+    int kind = 0, njobs = 0, nblocks = 0, smem = 0;
+  };
+
+  // Restriction: axis by axis, each pass restricting every distinct prefix
+  // of the grid set's level vectors.
+  int build_restrict_jobs() {
+    rpasses_.clear();
+    const int CAP = 8192;  // reals of shared memory per block for the pyramid
+    // level prefixes: pass a produces arrays keyed by (l_0..l_a)
+    std::map<std::vector<int>, real*> prev;  // arrays of the previous pass
+    prev[{}] = rho_reg_;
+    for (int a = 0; a < D; ++a) {
+      std::map<std::vector<int>, std::set<int>> targets;  // prefix -> levels along axis a
+      for (auto& g : grids_) {
+        std::vector<int> pre(g.l, g.l + a);
+        targets[pre].insert(g.l[a]);
+      }
+      std::vector<LineJob> jobs;
+      std::map<std::vector<int>, real*> next;
+      int blocks = 0, smem = 0;
+      for (auto& kv : targets) {
+        LineJob J;
+        std::memset(&J, 0, sizeof(J));
+        J.src = prev.at(kv.first);
+        for (int m = 0; m < 3; ++m) J.dims[m] = 1;
+        for (int m = 0; m < D; ++m) J.dims[m] = m < a ? (1 << kv.first[m]) : N_;
+        J.axis = a;
+        J.top = n_;
+        long long lines = 1;
+        for (int m = 0; m < D; ++m)
+          if (m != a) lines *= J.dims[m];
+        J.lines = (int)lines;
+        int C = std::max(1, CAP / (2 * N_));
+        if (C > lines) C = (int)lines;
+        J.lines_per_block = C;
+        J.block_begin = blocks;
+        blocks += (int)((lines + C - 1) / C);
+        smem = std::max(smem, (int)(C * 2 * N_ * sizeof(real)));
+        J.ntargets = 0;
+        for (int tl : kv.second) {
+          if (J.ntargets >= LJ_MAX_TARGETS) {
+            set_error("restriction: too many target levels");
+            return SG_ERR_UNSUPPORTED;
+          }
+          std::vector<int> key = kv.first;
+          key.push_back(tl);
+          real* dst;
+          if (a == D - 1) {  // final pass writes the component grid
+            int gi = find_grid(key);
+            dst = rho_arena_ + gdesc_[gi].offset;
+          } else {
+            size_t cnt = (size_t)(1 << tl);
+            for (int m = 0; m < D; ++m) cnt *= (m < a ? (size_t)(1 << kv.first[m]) : (m == a ? 1 : (size_t)N_));
+            SG_TRY(galloc((void**)&dst, cnt * sizeof(real)));
+            next[key] = dst;
+          }
+          J.tlev[J.ntargets] = tl;
+          J.dst[J.ntargets] = dst;
+          ++J.ntargets;
+        }
+        jobs.push_back(J);
+      }
+      Pass P;
+      P.njobs = (int)jobs.size();
+      P.nblocks = blocks;
+      P.smem = smem;
+      SG_TRY(galloc((void**)&P.dev, jobs.size() * sizeof(LineJob)));
+      SG_CUDA(cudaMemcpyAsync(P.dev, jobs.data(), jobs.size() * sizeof(LineJob), cudaMemcpyHostToDevice, stream_));
+      SG_CUDA(cudaStreamSynchronize(stream_));
+      rpasses_.push_back(P);
+      prev.swap(next);
+    }
+    return SG_OK;
+  }
+  int find_grid(const std::vector<int>& l) {
+    for (int g = 0; g < ngrids_; ++g) {
+      bool eq = true;
+      for (int m = 0; m < D; ++m) eq &= grids_[g].l[m] == l[m];
+      if (eq) return g;
+    }
+    return -1;
+  }
+
+  int build_fft_jobs() {
+    fpasses_.clear();
+    std::vector<std::pair<int, int>> seq;  // (kind, axis)
+    if (D == 2) {
+      seq = {{FFT_FWD_FIRST, 0}, {FFT_LAST, 1}, {FFT_INV_LAST, 0}};
+    } else {
+      seq = {{FFT_FWD_FIRST, 0}, {FFT_FWD_MID, 1}, {FFT_LAST, 2}, {FFT_INV_MID, 1}, {FFT_INV_LAST, 0}};
+    }
+    const int CAPC = 2048;  // complex values per buffer
+    for (auto& ka : seq) {
+      const int kind = ka.first, axis = ka.second;
+      const bool per_comp = (kind == FFT_INV_MID || kind == FFT_INV_LAST);
+      std::vector<FftJob> jobs;
+      int blocks = 0, smem = 0;
+      for (int g = 0; g < ngrids_; ++g) {
+        for (int comp = 0; comp < (per_comp ? D : 1); ++comp) {
+          FftJob J;
+          std::memset(&J, 0, sizeof(J));
+          J.grid = g;
+          for (int m = 0; m < 3; ++m) J.dims[m] = m < D ? (1 << gdesc_[g].l[m]) : 1;
+          J.axis = axis;
+          J.logn = gdesc_[g].l[axis];
+          const int len = 1 << J.logn;
+          J.lines = gdesc_[g].size / len;
+          int C = std::max(1, CAPC / len);
+          if (C > J.lines) C = J.lines;
+          J.lines_per_block = C;
+          J.block_begin = blocks;
+          J.comp = comp;
+          blocks += (J.lines + C - 1) / C;
+          smem = std::max(smem, (int)(2 * C * len * sizeof(cplx<real>)));
+          jobs.push_back(J);
+        }
+      }
+      FPass P;
+      P.kind = kind;
+      P.njobs = (int)jobs.size();
+      P.nblocks = blocks;
+      P.smem = smem;
+      SG_TRY(galloc((void**)&P.dev, jobs.size() * sizeof(FftJob)));
+      SG_CUDA(cudaMemcpyAsync(P.dev, jobs.data(), jobs.size() * sizeof(FftJob), cudaMemcpyHostToDevice, stream_));
+      SG_CUDA(cudaStreamSynchronize(stream_));
+      fpasses_.push_back(P);
+    }
+    return SG_OK;
+  }
+
+  int ensure_estimator_buffers() {
+    if (est_z_) return SG_OK;
+    SG_TRY(alloc((void**)&est_rho_, ND_ * sizeof(double)));
+    SG_TRY(alloc((void**)&est_z_, ND_ * sizeof(cplx<double>)));
+    SG_TRY(alloc((void**)&est_w_, ND_ * sizeof(cplx<double>)));
+    SG_TRY(alloc((void**)&est_scalar_, 16 * sizeof(double)));
+    std::vector<cplx<double>> tw(std::max(1, N_ / 2));
+    for (int k = 0; k < N_ / 2; ++k) {
+      double a = 2.0 * M_PI * (double)k / (double)N_;
+      tw[k].x = std::cos(a);
+      tw[k].y = -std::sin(a);
+    }
+    SG_TRY(alloc((void**)&tw64_, tw.size() * sizeof(cplx<double>)));
+    SG_CUDA(cudaMemcpyAsync(tw64_, tw.data(), tw.size() * sizeof(cplx<double>), cudaMemcpyHostToDevice, stream_));
+    return SG_OK;
+  }
+
+  // ------------------------------------------------------------ step stages
+  double fe_scale() const {
+    double hd = 1;
+    for (int m = 0; m < D; ++m) hd *= cfg_.L[m] / (double)N_;
+    return 0.5 * hd;
+  }
+  real inv_cell_vol() const {
+    double hd = 1;
+    for (int m = 0; m < D; ++m) hd *= cfg_.L[m] / (double)N_;
+    return (real)(1.0 / hd);
+  }
+
+  int enqueue_push(double dt, bool drift, double* ke) {
+    PushParams<real> pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.qm = (real)cfg_.qm;
+    pp.dt = (real)dt;
+    bool boris = false, eext = false;
+    for (int m = 0; m < 3; ++m) {
+      pp.dt_over_L[m] = m < D ? (real)(dt / cfg_.L[m]) : (real)0;
+      pp.eext[m] = m < D ? (real)(cfg_.eext_lin[m] * cfg_.L[m]) : (real)0;
+      pp.tB[m] = (real)(cfg_.qm * cfg_.B[m] * 0.5 * dt);
+      boris |= cfg_.B[m] != 0.0;
+      eext |= (m < D && cfg_.eext_lin[m] != 0.0);
+    }
+    pp.boris = boris ? 1 : 0;
+    pp.has_eext = eext ? 1 : 0;
+    pp.drift = drift ? 1 : 0;
+    return launch_push<real, D>(P_[cur_], np_, n_, Ehi_, pp, ke, status_, stream_);
+  }
+
+  int enqueue_sort() {
+    SG_CUDA(cudaMemsetAsync(checksum_, 0, sizeof(unsigned long long), stream_));
+    SG_TRY(launch_keys<real, D>(P_[cur_], np_, n_, keys_, nullptr, checksum_, status_, stream_));
+    bool in_alt = false;
+    SG_TRY(radix_sort_pairs(keys_, vals_, keys_alt_, vals_alt_, np_, D * n_, true, scr_, stream_, &in_alt));
+    const uint32_t* perm = in_alt ? vals_alt_ : vals_;
+    SG_TRY(launch_permute<real, D>(P_[cur_], P_[cur_ ^ 1], perm, np_, stream_));
+    cur_ ^= 1;
+    return SG_OK;
+  }
+
+  int enqueue_deposit() {
+    SG_CUDA(cudaMemsetAsync(rho_reg_, 0, ND_ * sizeof(real), stream_));
+    return launch_deposit<real, D>(P_[cur_], np_, n_, inv_cell_vol(), rho_reg_, cfg_.win_cap, stream_);
+  }
+
+  int enqueue_restrict() {
+    for (auto& P : rpasses_) SG_TRY(launch_restrict_pass<real>(P.dev, P.njobs, P.nblocks, P.smem, stream_));
+    return SG_OK;
+  }
+
+  int enqueue_solve() {
+    SolveArena<real> a;
+    a.grids = grids_dev_;
+    a.rho = rho_arena_;
+    a.A = A_;
+    a.B = B_;
+    a.E = E_arena_;
+    a.S = S_;
+    a.tw = tw_;
+    a.log_nmax = n_;
+    a.dim = D;
+    for (auto& P : fpasses_) SG_TRY(launch_fft_pass<real>(P.kind, a, P.dev, P.njobs, P.nblocks, P.smem, stream_));
+    return SG_OK;
+  }
+
+  int enqueue_combine() {
+    return launch_combine<real, D>(grids_dev_, ngrids_, lmin_, E_arena_, S_, n_, Ehi_, Elo_, fe_partials_, stream_);
+  }
+
+  int enqueue_restrict_solve_combine() {
+    SG_TRY(enqueue_restrict());
+    SG_TRY(enqueue_solve());
+    return enqueue_combine();
+  }
+
+  int enqueue_fields() {
+    SG_TRY(enqueue_deposit());
+    return enqueue_restrict_solve_combine();
+  }
+
+  int enqueue_step(bool do_sort) {
+    SG_TRY(enqueue_push(cfg_.dt, true, ke_partials_));
+    if (do_sort) SG_TRY(enqueue_sort());
+    SG_TRY(enqueue_fields());
+    return launch_finalize_step(fe_partials_, nrows_, ke_partials_, nke_, fe_scale(), dd_, stream_);
+  }
+
+  // Graph variants: (current particle set, sort or not).
+  int step_graph(bool do_sort) {
+    int vi = cur_ * 2 + (do_sort ? 1 : 0);
+    if (!gexec_[vi]) {
+      int cur_before = cur_;
+      unsigned long long l0 = launches_so_far();
+      cudaGraph_t g;
+      SG_CUDA(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
+      int st = enqueue_step(do_sort);
+      cudaError_t e = cudaStreamEndCapture(stream_, &g);
+      cur_ = cur_before;  // the capture did not run anything
+      if (st != SG_OK) return st;
+      if (e != cudaSuccess) {
+        set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+        return SG_ERR_CUDA;
+      }
+      SG_CUDA(cudaGraphInstantiate(&gexec_[vi], g, 0));
+      cudaGraphDestroy(g);
+      glaunches_[vi] = launches_so_far() - l0;
+    }
+    SG_CUDA(cudaGraphLaunch(gexec_[vi], stream_));
+    launches_ += glaunches_[vi];
+    if (do_sort) cur_ ^= 1;
+    return SG_OK;
+  }
+
+  void invalidate_graphs() {
+    for (int i = 0; i < 4; ++i)
+      if (gexec_[i]) {
+        cudaGraphExecDestroy(gexec_[i]);
+        gexec_[i] = nullptr;
+      }
+  }
+
+  // Same sequence as enqueue_step with events between the stages:
+  // 0 push, 1 sort, 2 deposit, 3 restrict, 4 solve, 5 combine (+ finalize).
+  int step_profiled(bool do_sort) {
+    unsigned long long l0 = launches_so_far();
+    SG_CUDA(cudaEventRecord(ev_[0], stream_));
+    SG_TRY(enqueue_push(cfg_.dt, true, ke_partials_));
+    SG_CUDA(cudaEventRecord(ev_[1], stream_));
+    if (do_sort) SG_TRY(enqueue_sort());
+    SG_CUDA(cudaEventRecord(ev_[2], stream_));
+    SG_TRY(enqueue_deposit());
+    SG_CUDA(cudaEventRecord(ev_[3], stream_));
+    SG_TRY(enqueue_restrict());
+    SG_CUDA(cudaEventRecord(ev_[4], stream_));
+    SG_TRY(enqueue_solve());
+    SG_CUDA(cudaEventRecord(ev_[5], stream_));
+    SG_TRY(enqueue_combine());
+    SG_TRY(launch_finalize_step(fe_partials_, nrows_, ke_partials_, nke_, fe_scale(), dd_, stream_));
+    SG_CUDA(cudaEventRecord(ev_[6], stream_));
+    SG_CUDA(cudaEventSynchronize(ev_[6]));
+    for (int i = 0; i < 6; ++i) {
+      float ms = 0;
+      SG_CUDA(cudaEventElapsedTime(&ms, ev_[i], ev_[i + 1]));
+      stage_ms_[i] += ms;
+    }
+    launches_ += launches_so_far() - l0;
+    return SG_OK;
+  }
+
+  int step_adaptive(bool do_sort) {
+    unsigned long long l0 = launches_so_far();
+    SG_TRY(enqueue_push(cfg_.dt, true, ke_partials_));
+    if (do_sort) SG_TRY(enqueue_sort());
+    SG_TRY(enqueue_deposit());
+    int t = tau_;
+    int st = select_tau(&t, nullptr, nullptr, 0);
+    if (st == SG_OK && t != tau_) {
+      SG_CUDA(cudaStreamSynchronize(stream_));
+      SG_TRY(build_grid_set(t));
+    } else if (st != SG_OK && st != SG_ERR_RANGE) {
+      return st;
+    }
+    SG_TRY(enqueue_restrict_solve_combine());
+    SG_TRY(launch_finalize_step(fe_partials_, nrows_, ke_partials_, nke_, fe_scale(), dd_, stream_));
+    launches_ += launches_so_far() - l0;
+    return SG_OK;
+  }
+
+  // ------------------------------------------------------------ state
+  EngineConfig cfg_;
+  int n_ = 0, N_ = 0;
+  size_t ND_ = 0, np_ = 0, S_ = 0;
+  cudaStream_t stream_ = nullptr;
+  bool own_stream_ = false;
+  int sort_every_ = 1;
+  int tau_ = 1;
+  bool adaptive_ = false;
+  long long step_ = 0;
+  double charge_total_ = 0;
+
+  std::vector<DevBuf> bufs_;
+  std::vector<void*> grid_bufs_;
+  size_t bytes_ = 0;
+
+  PArrays<real, D> P_[2];
+  int cur_ = 0;
+  uint32_t *keys_ = nullptr, *keys_alt_ = nullptr, *vals_ = nullptr, *vals_alt_ = nullptr, *sort_scr_ = nullptr;
+  SortScratch scr_;
+  DevDiag* dd_ = nullptr;
+  unsigned* status_ = nullptr;
+  unsigned long long* checksum_ = nullptr;
+  double* ke_partials_ = nullptr;
+  double* fe_partials_ = nullptr;
+  int nke_ = 0, nrows_ = 0;
+
+  real* rho_reg_ = nullptr;
+  real* Ehi_ = nullptr;
+  float* Elo_ = nullptr;
+  cplx<real>* tw_ = nullptr;
+
+  std::vector<GridSpec> grids_;
+  std::vector<GridDesc> gdesc_;
+  int ngrids_ = 0, lmin_ = 0;
+  GridDesc* grids_dev_ = nullptr;
+  double* charges_dev_ = nullptr;
+  real* rho_arena_ = nullptr;
+  cplx<real>* A_ = nullptr;
+  cplx<real>* B_ = nullptr;
+  real* E_arena_ = nullptr;
+  std::vector<Pass> rpasses_;
+  std::vector<FPass> fpasses_;
+
+  double* est_rho_ = nullptr;
+  cplx<double>* est_z_ = nullptr;
+  cplx<double>* est_w_ = nullptr;
+  double* est_scalar_ = nullptr;
+  cplx<double>* tw64_ = nullptr;
+
+  cudaGraphExec_t gexec_[4] = {nullptr, nullptr, nullptr, nullptr};
+  unsigned long long glaunches_[4] = {0, 0, 0, 0};
+  unsigned long long launches_ = 0;
+  bool profiling_ = false;
+  cudaEvent_t ev_[8] = {};
+  double stage_ms_[6] = {0, 0, 0, 0, 0, 0};
+};
+
+}  // namespace
+
+EngineBase* make_engine(int precision, int dim) {
+  if (precision == SG_FP32 && dim == 2) return new Engine<float, 2>();
+  if (precision == SG_FP32 && dim == 3) return new Engine<float, 3>();
+  if (precision == SG_FP64 && dim == 2) return new Engine<double, 2>();
+  if (precision == SG_FP64 && dim == 3) return new Engine<double, 3>();
+  return nullptr;
+}
+
+size_t estimate_footprint(int precision, int dim, int n, int tau, size_t np) {
+  size_t rs = precision == SG_FP64 ? 8 : 4;
+  size_t ND = (size_t)1 << (dim * n);
+  auto grids = combination_grids(dim, n, tau);
+  size_t S = 0;
+  for (auto& g : grids) {
+    size_t s = 1;
+    for (int m = 0; m < dim; ++m) s <<= g.l[m];
+    S += s;
+  }
+  size_t part = 2 * np * ((2 * dim + 1) * rs + 4) + 4 * np * 4 + (np / RS_TILE + 1) * 256 * 4 * 2;
+  size_t grid = ND * rs * (1 + dim) + (rs == 4 ? dim * ND * 4 : 0) + 2 * ND * rs;  // rho, Ecomb, restrict scratch
+  size_t arena = S * (rs + 2 * rs + dim * 2 * rs + dim * rs);
+  return part + grid + arena + (1 << 20);
+}
+
+}  // namespace sg

@@ -1,0 +1,188 @@
+// Launchers of the library's device kernels (host side).  Every launcher
+// enqueues on the given stream and returns an SG_* status.
+#pragma once
+
+#include "sg_common.cuh"
+
+namespace sg {
+
+// ---------------------------------------------------------------- sort
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // keys per tile
+
+struct SortScratch {
+  uint32_t* tile_hist = nullptr;   // 256 * ntiles
+  uint32_t* block_sums = nullptr;  // scan block totals
+  size_t ntiles = 0;
+};
+
+size_t sort_scratch_words(size_t np);  // u32 words needed for SortScratch
+void sort_scratch_bind(SortScratch& s, uint32_t* base, size_t np);
+
+// keys[i] = Morton key of particle i's level-n cell, idx[i] = i,
+// *checksum += sum_i (keys[i] + 1).
+template <typename real, int D>
+int launch_keys(const PArrays<real, D>& p, size_t np, int n, uint32_t* keys, uint32_t* idx,
+                unsigned long long* checksum, unsigned* status, cudaStream_t s);
+
+// Same for positions given as plain arrays (stand-alone sort entry point).
+template <typename real, int D>
+int launch_keys_raw(const real* const* u, size_t np, int n, uint32_t* keys, uint32_t* idx,
+                    unsigned long long* checksum, unsigned* status, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
+// Ping-pongs between (keys, vals) and (keys_alt, vals_alt); *in_alt tells
+// where the sorted result ended.  If vals_identity, the first pass uses the
+// input index as value instead of reading vals.
+int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                     size_t np, int bits, bool vals_identity, SortScratch& scr, cudaStream_t s,
+                     bool* in_alt);
+
+template <typename real, int D>
+int launch_permute(const PArrays<real, D>& src, const PArrays<real, D>& dst, const uint32_t* perm,
+                   size_t np, cudaStream_t s);
+
+// dst[pid[i]] = src[i] for every particle array (back to the original order).
+template <typename real, int D>
+int launch_unpermute(const PArrays<real, D>& src, const PArrays<real, D>& dst, size_t np, cudaStream_t s);
+
+// counts[key] += 1 for every sorted key (counts zeroed by the caller).
+int launch_counts(const uint32_t* keys, size_t np, uint32_t* counts, cudaStream_t s);
+
+// Exclusive scan of m u32 values (out may equal in).
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, size_t m, uint32_t* block_sums,
+                       cudaStream_t s);
+size_t scan_block_sums_words(size_t m);
+
+// ---------------------------------------------------------------- deposit
+constexpr int DEP_THREADS = 256;
+constexpr int DEP_ITEMS = 8;
+constexpr int DEP_CHUNK = DEP_THREADS * DEP_ITEMS;
+
+template <typename real, int D>
+int launch_deposit(const PArrays<real, D>& p, size_t np, int n, real inv_cell_vol, real* rho,
+                   int win_cap_nodes, cudaStream_t s);
+
+// ---------------------------------------------------------------- line passes
+// A batch of lines of one array, processed by one kernel launch together
+// with the other jobs of the same pass.
+constexpr int LJ_MAX_TARGETS = 14;
+struct LineJob {
+  const void* src;
+  int dims[3];
+  int axis;
+  int top;        // log2(dims[axis])
+  int ntargets;
+  int lines;      // number of lines in the array
+  int lines_per_block;
+  int block_begin;  // first block of this job in the launch
+  int tlev[LJ_MAX_TARGETS];
+  void* dst[LJ_MAX_TARGETS];
+};
+
+// Restriction pyramid (full weighting 1/4, 1/2, 1/4 per level halving, the
+// exact form of R along one axis for nested node-centred grids).
+template <typename real>
+int launch_restrict_pass(const LineJob* jobs_dev, int njobs, int nblocks, int smem_bytes,
+                         cudaStream_t s);
+
+// FFT passes over the component grids.
+enum FftKind { FFT_FWD_FIRST = 0, FFT_FWD_MID = 1, FFT_LAST = 2, FFT_INV_MID = 3, FFT_INV_LAST = 4 };
+
+struct FftJob {
+  int grid;          // index into the grid table
+  int dims[3];
+  int axis;
+  int logn;
+  int lines;
+  int lines_per_block;
+  int block_begin;
+  int comp;          // field component for the inverse passes
+};
+
+template <typename real>
+struct SolveArena {
+  const GridDesc* grids;
+  const real* rho;     // S
+  cplx<real>* A;       // S
+  cplx<real>* B;       // D * S
+  real* E;             // D * S
+  size_t S;
+  const cplx<real>* tw;  // twiddles exp(-2 pi i k / Nmax), k < Nmax/2
+  int log_nmax;
+  int dim;
+};
+
+template <typename real>
+int launch_fft_pass(int kind, const SolveArena<real>& a, const FftJob* jobs_dev, int njobs,
+                    int nblocks, int smem_bytes, cudaStream_t s);
+
+// Generic in-place complex FFT of a whole N^D array (regular grid) along one
+// axis, forward or inverse (unnormalised), in the given precision.
+template <typename real>
+int launch_fft_array_axis(cplx<real>* data, int D, int logn, int axis, bool inverse,
+                          const cplx<real>* tw, int log_nmax, cudaStream_t s);
+
+// ---------------------------------------------------------------- combine
+template <typename real, int D>
+int launch_combine(const GridDesc* grids, int ngrids, int lmin, const real* E, size_t S, int n,
+                   real* Ehi, float* Elo, double* energy_partials, cudaStream_t s);
+
+// ---------------------------------------------------------------- push
+template <typename real>
+struct PushParams {
+  real qm, dt;
+  real dt_over_L[3];
+  real eext[3];   // E_ext,m = eext[m] * (u_m - 1/2)   (eext = Eext_lin * L)
+  real tB[3];     // q/m * B * dt / 2 (Boris t vector)
+  int boris;
+  int has_eext;
+  int drift;      // 0: velocity only (initial half kick), 1: kick + drift
+};
+
+template <typename real, int D>
+int launch_push(const PArrays<real, D>& p, size_t np, int n, const real* Ecomb, PushParams<real> pp,
+                double* ke_partials, unsigned* status, cudaStream_t s);
+int push_blocks(size_t np);
+
+// ---------------------------------------------------------------- misc
+template <typename real, int D>
+int launch_wrap_check(const PArrays<real, D>& p, size_t np, unsigned* status, cudaStream_t s);
+
+template <typename real>
+int launch_sum_to_double(const real* x, size_t n, double* partials, int nblocks, cudaStream_t s);
+
+// Device diagnostics record updated at the end of each step.
+struct DevDiag {
+  double field_energy;
+  double field_energy_prev;
+  double kinetic_energy;
+  unsigned long long checksum;
+  unsigned status;
+  unsigned pad;
+};
+
+int launch_finalize_step(const double* fe_partials, int n_fe, const double* ke_partials, int n_ke,
+                         double fe_scale, DevDiag* dd, cudaStream_t s);
+
+template <typename real>
+int launch_grid_charges(const GridDesc* grids, int ngrids, const real* rho, const double* vol,
+                        double* charges, cudaStream_t s);
+
+template <typename real>
+int launch_to_double(const real* src, double* dst, size_t n, cudaStream_t s);
+int launch_ff_to_double(const float* hi, const float* lo, double* dst, size_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------- tau estimator
+int launch_real_to_cplx(const double* src, cplx<double>* dst, size_t n, double scale, cudaStream_t s);
+int launch_maxabs_cplx(const cplx<double>* z, size_t n, double* out_max, cudaStream_t s);
+int launch_maxabs_real_part(const cplx<double>* z, size_t n, double* out_max, cudaStream_t s);
+int launch_maxabs_real(const double* x, size_t n, double* out_max, cudaStream_t s);
+int launch_threshold(cplx<double>* z, size_t n, const double* maxabs, double frac, cudaStream_t s);
+int launch_kmult(const cplx<double>* src, cplx<double>* dst, int D, int logn, const double* kfac,
+                 int mask, cudaStream_t s);
+int launch_maxabs_kmult(const cplx<double>* src, int D, int logn, const double* kfac, int mask,
+                        double* out_max, cudaStream_t s);
+
+}  // namespace sg

@@ -1,0 +1,281 @@
+// Serving: many independent runs resident on one GPU, admitted in arrival
+// order by device-memory footprint, advanced together tick by tick.  Each
+// resident run owns a stream, so the runs' kernels overlap on the device;
+// per-step latency is measured with events on the run's stream.
+#include <algorithm>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "sg_engine.cuh"
+
+using namespace sg;
+
+namespace {
+
+struct Request {
+  unsigned long long ticket;
+  sg_request req;
+  std::vector<char> u[3], v[3], w;  // host copies
+  size_t footprint;
+  int state = SG_REQ_QUEUED;
+  EngineBase* eng = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int steps_left = 0;
+  sg_diag last{};
+  std::vector<char> result_u[3], result_v[3], result_w;
+};
+
+}  // namespace
+
+struct sg_server {
+  size_t budget = 0;
+  int max_slots = 0;
+  size_t in_use = 0;
+  unsigned long long next_ticket = 1;
+  std::deque<Request*> queue;
+  std::vector<Request*> resident;
+  std::map<unsigned long long, Request*> all;
+  std::vector<double> step_ms;
+  double device_ms = 0;
+  double particle_steps = 0;
+  unsigned long long steps_served = 0;
+  std::mutex mu;
+};
+
+static int serr(const char* m, int code = SG_ERR_INVALID) {
+  set_error(m);
+  return code;
+}
+
+static void finish(sg_server* s, Request* r, int state) {
+  if (r->eng) {
+    size_t rs = r->req.params.precision == SG_FP64 ? 8 : 4;
+    size_t np = r->req.particles.n;
+    int d = r->req.dim;
+    for (int m = 0; m < d; ++m) {
+      r->result_u[m].resize(np * rs);
+      r->result_v[m].resize(np * rs);
+    }
+    r->result_w.resize(np * rs);
+    sg_particles_out o;
+    std::memset(&o, 0, sizeof(o));
+    o.n = np;
+    o.on_device = 0;
+    for (int m = 0; m < d; ++m) {
+      o.u[m] = r->result_u[m].data();
+      o.v[m] = r->result_v[m].data();
+    }
+    o.w = r->result_w.data();
+    if (state == SG_REQ_DONE && r->eng->get_particles(&o) != SG_OK) state = SG_REQ_FAILED;
+    r->eng->diagnostics(&r->last);
+    delete r->eng;
+    r->eng = nullptr;
+  }
+  if (r->ev0) cudaEventDestroy(r->ev0);
+  if (r->ev1) cudaEventDestroy(r->ev1);
+  if (r->stream) cudaStreamDestroy(r->stream);
+  r->ev0 = r->ev1 = nullptr;
+  r->stream = nullptr;
+  for (int m = 0; m < 3; ++m) {
+    std::vector<char>().swap(r->u[m]);
+    std::vector<char>().swap(r->v[m]);
+  }
+  std::vector<char>().swap(r->w);
+  s->in_use -= r->footprint;
+  r->state = state;
+}
+
+extern "C" {
+
+int sg_serve_create(size_t hbm_budget_bytes, int max_slots, sg_server** out) {
+  if (!out) return serr("sg_serve_create: out is NULL");
+  if (max_slots < 1 || hbm_budget_bytes == 0) return serr("sg_serve_create: need max_slots >= 1 and a budget");
+  sg_server* s = new sg_server;
+  s->budget = hbm_budget_bytes;
+  s->max_slots = max_slots;
+  *out = s;
+  return SG_OK;
+}
+
+int sg_serve_submit(sg_server* s, const sg_request* req, unsigned long long* ticket) {
+  if (!s || !req || !ticket) return serr("sg_serve_submit: NULL argument");
+  const sg_particles& p = req->particles;
+  if (p.on_device) return serr("sg_serve_submit: particle arrays must be host memory", SG_ERR_UNSUPPORTED);
+  if (req->dim != 2 && req->dim != 3) return serr("sg_serve_submit: dim must be 2 or 3");
+  if (req->nsteps < 0) return serr("sg_serve_submit: nsteps < 0");
+  if (req->params.tau == SG_TAU_ADAPTIVE) return serr("sg_serve_submit: adaptive tau is not served", SG_ERR_UNSUPPORTED);
+  int tau = req->params.tau;
+  if (tau < 1 || tau > req->level_n || req->level_n < 2 || req->dim * req->level_n > 24)
+    return serr("sg_serve_submit: bad level / tau");
+  size_t rs = req->params.precision == SG_FP64 ? 8 : 4;
+  Request* r = new Request;
+  r->req = *req;
+  for (int m = 0; m < req->dim; ++m) {
+    if (p.n && (!p.u[m] || !p.v[m])) {
+      delete r;
+      return serr("sg_serve_submit: NULL particle array");
+    }
+    r->u[m].assign((const char*)p.u[m], (const char*)p.u[m] + p.n * rs);
+    r->v[m].assign((const char*)p.v[m], (const char*)p.v[m] + p.n * rs);
+  }
+  if (p.n && !p.w) {
+    delete r;
+    return serr("sg_serve_submit: NULL charge array");
+  }
+  r->w.assign((const char*)p.w, (const char*)p.w + p.n * rs);
+  r->footprint = estimate_footprint(req->params.precision, req->dim, req->level_n, tau, p.n);
+  if (r->footprint > s->budget) {
+    delete r;
+    return serr("sg_serve_submit: request larger than the whole memory budget", SG_ERR_OOM);
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  r->ticket = s->next_ticket++;
+  r->steps_left = req->nsteps;
+  s->queue.push_back(r);
+  s->all[r->ticket] = r;
+  *ticket = r->ticket;
+  return SG_OK;
+}
+
+int sg_serve_tick(sg_server* s, int* active) {
+  if (!s) return serr("sg_serve_tick: NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  // admit in arrival order while memory and slots allow
+  while (!s->queue.empty() && (int)s->resident.size() < s->max_slots &&
+         s->in_use + s->queue.front()->footprint <= s->budget) {
+    Request* r = s->queue.front();
+    s->queue.pop_front();
+    s->in_use += r->footprint;
+    if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&r->ev0) != cudaSuccess || cudaEventCreate(&r->ev1) != cudaSuccess) {
+      finish(s, r, SG_REQ_FAILED);
+      continue;
+    }
+    EngineConfig cfg;
+    const sg_request& q = r->req;
+    cfg.dim = q.dim;
+    cfg.n = q.level_n;
+    cfg.tau = q.params.tau;
+    cfg.precision = q.params.precision;
+    for (int m = 0; m < 3; ++m) {
+      cfg.L[m] = m < q.dim ? q.domain.L[m] : 1.0;
+      cfg.B[m] = q.params.B[m];
+      cfg.eext_lin[m] = q.params.Eext_lin[m];
+    }
+    cfg.dt = q.params.dt;
+    cfg.qm = q.params.qm;
+    cfg.alpha = q.params.alpha;
+    cfg.pc_ref = q.params.pc_ref;
+    cfg.tau_constants = q.params.tau_constants;
+    cfg.sort_every = q.params.sort_every;
+    sg_particles hp;
+    std::memset(&hp, 0, sizeof(hp));
+    hp.n = q.particles.n;
+    hp.on_device = 0;
+    for (int m = 0; m < q.dim; ++m) {
+      hp.u[m] = r->u[m].data();
+      hp.v[m] = r->v[m].data();
+    }
+    hp.w = r->w.data();
+    r->eng = make_engine(q.params.precision, q.dim);
+    if (!r->eng || r->eng->init(cfg, &hp, r->stream) != SG_OK) {
+      finish(s, r, SG_REQ_FAILED);
+      continue;
+    }
+    r->state = SG_REQ_RUNNING;
+    s->resident.push_back(r);
+  }
+  // one step of every resident run, each on its own stream
+  for (Request* r : s->resident) {
+    if (r->steps_left <= 0) continue;
+    cudaEventRecord(r->ev0, r->stream);
+    if (r->eng->step(1) != SG_OK) r->steps_left = -1;
+    cudaEventRecord(r->ev1, r->stream);
+  }
+  std::vector<Request*> keep;
+  for (Request* r : s->resident) {
+    if (r->steps_left > 0) {
+      cudaEventSynchronize(r->ev1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, r->ev0, r->ev1);
+      s->step_ms.push_back(ms);
+      s->device_ms += ms;
+      s->particle_steps += (double)r->req.particles.n;
+      ++s->steps_served;
+      --r->steps_left;
+    }
+    if (r->steps_left == 0) {
+      finish(s, r, SG_REQ_DONE);
+    } else if (r->steps_left < 0) {
+      finish(s, r, SG_REQ_FAILED);
+    } else {
+      keep.push_back(r);
+    }
+  }
+  s->resident.swap(keep);
+  if (active) *active = (int)s->resident.size();
+  return SG_OK;
+}
+
+int sg_serve_poll(sg_server* s, unsigned long long ticket, int* state, sg_diag* last) {
+  if (!s || !state) return serr("sg_serve_poll: NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return serr("sg_serve_poll: unknown ticket");
+  Request* r = it->second;
+  *state = r->state;
+  if (last) {
+    if (r->state == SG_REQ_RUNNING && r->eng) r->eng->diagnostics(&r->last);
+    *last = r->last;
+  }
+  return SG_OK;
+}
+
+int sg_serve_result(sg_server* s, unsigned long long ticket, const sg_particles_out* out) {
+  if (!s || !out) return serr("sg_serve_result: NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return serr("sg_serve_result: unknown ticket");
+  Request* r = it->second;
+  if (r->state != SG_REQ_DONE) return serr("sg_serve_result: request not finished", SG_ERR_STATE);
+  if (out->n != r->req.particles.n) return serr("sg_serve_result: size mismatch", SG_ERR_SIZE);
+  if (out->on_device) return serr("sg_serve_result: host buffers only", SG_ERR_UNSUPPORTED);
+  size_t bytes = r->result_w.size();
+  for (int m = 0; m < r->req.dim; ++m) {
+    if (out->u[m]) std::memcpy(out->u[m], r->result_u[m].data(), bytes);
+    if (out->v[m]) std::memcpy(out->v[m], r->result_v[m].data(), bytes);
+  }
+  if (out->w) std::memcpy(out->w, r->result_w.data(), bytes);
+  return SG_OK;
+}
+
+int sg_serve_stats(sg_server* s, double* p50_ms, double* p99_ms, double* particle_steps_per_s,
+                   unsigned long long* steps_served) {
+  if (!s) return serr("sg_serve_stats: NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  std::vector<double> v = s->step_ms;
+  std::sort(v.begin(), v.end());
+  auto pct = [&](double q) {
+    if (v.empty()) return 0.0;
+    size_t i = (size_t)(q * (double)(v.size() - 1) + 0.5);
+    return v[std::min(i, v.size() - 1)];
+  };
+  if (p50_ms) *p50_ms = pct(0.50);
+  if (p99_ms) *p99_ms = pct(0.99);
+  if (particle_steps_per_s) *particle_steps_per_s = s->device_ms > 0 ? s->particle_steps / (s->device_ms * 1e-3) : 0.0;
+  if (steps_served) *steps_served = s->steps_served;
+  return SG_OK;
+}
+
+void sg_serve_destroy(sg_server* s) {
+  if (!s) return;
+  for (Request* r : s->resident) finish(s, r, SG_REQ_FAILED);
+  for (auto& kv : s->all) delete kv.second;
+  delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,385 @@
+// Cell-key sort of the particles: Morton keys of the level-n cells, a stable
+// LSD radix sort of (key, index) pairs with 8-bit digits, the permutation of
+// the particle arrays and per-cell counts.  Integer work, bit-exact.
+#include "sg_kernels.cuh"
+
+namespace sg {
+
+
+// ---------------------------------------------------------------- keys
+template <typename real, int D>
+__global__ void __launch_bounds__(256) k_keys(PArrays<real, D> p, size_t np, int n, uint32_t* keys,
+                                              uint32_t* idx, unsigned long long* checksum,
+                                              unsigned* status) {
+  const int N = 1 << n;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long part = 0;
+  if (i < np) {
+    int c[D];
+    bool bad = false;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      real u = p.u[m][i];
+      bad |= !(u >= (real)0 && u < (real)1);
+      c[m] = cell_of(u, n, N);
+    }
+    if (bad) atomicOr(status, ST_KEY_RANGE);
+    uint32_t k = morton_key<D>(c, n);
+    keys[i] = k;
+    if (idx) idx[i] = (uint32_t)i;
+    part = (unsigned long long)k + 1ull;
+  }
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0 && checksum && part) atomicAdd(checksum, part);
+}
+
+template <typename real, int D>
+struct RawU {
+  const real* u[D];
+};
+
+template <typename real, int D>
+__global__ void __launch_bounds__(256) k_keys_raw(RawU<real, D> r, size_t np, int n, uint32_t* keys,
+                                                  uint32_t* idx, unsigned long long* checksum,
+                                                  unsigned* status) {
+  const int N = 1 << n;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long part = 0;
+  if (i < np) {
+    int c[D];
+    bool bad = false;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      real u = r.u[m][i];
+      bad |= !(u >= (real)0 && u < (real)1);
+      // positions outside [0,1) are wrapped first (periodic box)
+      if (bad) u = wrap_unit(u);
+      c[m] = cell_of(u, n, N);
+    }
+    uint32_t k = morton_key<D>(c, n);
+    keys[i] = k;
+    if (idx) idx[i] = (uint32_t)i;
+    part = (unsigned long long)k + 1ull;
+  }
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0 && checksum && part) atomicAdd(checksum, part);
+}
+
+template <typename real, int D>
+int launch_keys(const PArrays<real, D>& p, size_t np, int n, uint32_t* keys, uint32_t* idx,
+                unsigned long long* checksum, unsigned* status, cudaStream_t s) {
+  if (np == 0) return SG_OK;
+  k_keys<real, D><<<(unsigned)((np + 255) / 256), 256, 0, s>>>(p, np, n, keys, idx, checksum, status);
+  SG_CHECK_LAUNCH();
+  return SG_OK;
+}
+
+template <typename real, int D>
+int launch_keys_raw(const real* const* u, size_t np, int n, uint32_t* keys, uint32_t* idx,
+                    unsigned long long* checksum, unsigned* status, cudaStream_t s) {
+  if (np == 0) return SG_OK;
+  RawU<real, D> r;
+  for (int m = 0; m < D; ++m) r.u[m] = u[m];
+  k_keys_raw<real, D><<<(unsigned)((np + 255) / 256), 256, 0, s>>>(r, np, n, keys, idx, checksum, status);
+  SG_CHECK_LAUNCH();
+  return SG_OK;
+}
+
+// ---------------------------------------------------------------- scan
+constexpr int SC_THREADS = 256;
+constexpr int SC_ITEMS = 16;
+constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
+
+size_t scan_block_sums_words(size_t m) { return (m + SC_TILE - 1) / SC_TILE + 1; }
+
+// Block-wide exclusive scan of SC_TILE values staged in shared memory.
+__device__ void block_exclusive_scan_tile(uint32_t* sh, uint32_t* total) {
+  __shared__ uint32_t warp_tot[SC_THREADS / 32];
+  int t = threadIdx.x;
+  uint32_t loc[SC_ITEMS];
+  uint32_t run = 0;
+#pragma unroll
+  for (int j = 0; j < SC_ITEMS; ++j) {
+    loc[j] = run;
+    run += sh[t * SC_ITEMS + j];
+  }
+  // inclusive warp scan of per-thread totals
+  uint32_t x = run;
+  int lane = t & 31, w = t >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t v = lane < SC_THREADS / 32 ? warp_tot[lane] : 0;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane < SC_THREADS / 32) warp_tot[lane] = inc - v;  // exclusive
+    if (lane == SC_THREADS / 32 - 1) *total = inc;
+  }
+  __syncthreads();
+  uint32_t base = warp_tot[w] + (x - run);
+#pragma unroll
+  for (int j = 0; j < SC_ITEMS; ++j) sh[t * SC_ITEMS + j] = base + loc[j];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_tiles(const uint32_t* in, uint32_t* out, size_t m,
+                                                           uint32_t* block_sums) {
+  __shared__ uint32_t sh[SC_TILE];
+  __shared__ uint32_t tot;
+  size_t base = (size_t)blockIdx.x * SC_TILE;
+  for (int j = threadIdx.x; j < SC_TILE; j += SC_THREADS) sh[j] = (base + j < m) ? in[base + j] : 0u;
+  __syncthreads();
+  block_exclusive_scan_tile(sh, &tot);
+  for (int j = threadIdx.x; j < SC_TILE; j += SC_THREADS)
+    if (base + j < m) out[base + j] = sh[j];
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+// Exclusive scan of up to SC_TILE block sums in one block (repeated tiles if more).
+__global__ void __launch_bounds__(SC_THREADS) k_scan_top(uint32_t* block_sums, int nb) {
+  __shared__ uint32_t sh[SC_TILE];
+  __shared__ uint32_t tot;
+  uint32_t carry = 0;
+  for (int base = 0; base < nb; base += SC_TILE) {
+    for (int j = threadIdx.x; j < SC_TILE; j += SC_THREADS) sh[j] = (base + j < nb) ? block_sums[base + j] : 0u;
+    __syncthreads();
+    block_exclusive_scan_tile(sh, &tot);
+    for (int j = threadIdx.x; j < SC_TILE; j += SC_THREADS)
+      if (base + j < nb) block_sums[base + j] = sh[j] + carry;
+    __syncthreads();
+    carry += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_add(uint32_t* out, size_t m, const uint32_t* block_sums) {
+  size_t base = (size_t)blockIdx.x * SC_TILE;
+  uint32_t add = block_sums[blockIdx.x];
+  if (add == 0) return;
+  for (int j = threadIdx.x; j < SC_TILE; j += SC_THREADS)
+    if (base + j < m) out[base + j] += add;
+}
+
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, size_t m, uint32_t* block_sums, cudaStream_t s) {
+  if (m == 0) return SG_OK;
+  unsigned nb = (unsigned)((m + SC_TILE - 1) / SC_TILE);
+  k_scan_tiles<<<nb, SC_THREADS, 0, s>>>(in, out, m, block_sums);
+  SG_CHECK_LAUNCH();
+  if (nb > 1) {
+    k_scan_top<<<1, SC_THREADS, 0, s>>>(block_sums, (int)nb);
+    SG_CHECK_LAUNCH();
+    k_scan_add<<<nb, SC_THREADS, 0, s>>>(out, m, block_sums);
+    SG_CHECK_LAUNCH();
+  }
+  return SG_OK;
+}
+
+// ---------------------------------------------------------------- radix sort
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_WARP_KEYS = RS_TILE / RS_WARPS;
+static_assert(RS_WARP_KEYS == 32 * RS_ITEMS, "one key per lane per chunk");
+
+size_t sort_scratch_words(size_t np) {
+  size_t ntiles = (np + RS_TILE - 1) / RS_TILE;
+  if (ntiles == 0) ntiles = 1;
+  return 256 * ntiles + scan_block_sums_words(256 * ntiles) + 64;
+}
+
+void sort_scratch_bind(SortScratch& s, uint32_t* base, size_t np) {
+  size_t ntiles = (np + RS_TILE - 1) / RS_TILE;
+  if (ntiles == 0) ntiles = 1;
+  s.ntiles = ntiles;
+  s.tile_hist = base;
+  s.block_sums = base + 256 * ntiles;
+}
+
+// Digit histogram of one tile; keys with equal digits in a warp are counted
+// by their leader (match_any aggregation) to avoid shared atomic pile-ups on
+// nearly sorted input.
+__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* keys, size_t n, int shift,
+                                                           uint32_t* hist, int ntiles) {
+  __shared__ uint32_t h[256];
+  for (int i = threadIdx.x; i < 256; i += RS_THREADS) h[i] = 0;
+  __syncthreads();
+  size_t base = (size_t)blockIdx.x * RS_TILE;
+  int lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
+    size_t idx = base + i;
+    bool valid = idx < n;
+    uint32_t dg = valid ? ((keys[idx] >> shift) & 255u) : 256u;
+    unsigned peers = __match_any_sync(0xffffffffu, dg);
+    if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[dg], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += RS_THREADS) hist[(size_t)i * ntiles + blockIdx.x] = h[i];
+}
+
+// Stable scatter of one tile: warp w owns keys [w*512, (w+1)*512) of the
+// tile, taken in 16 chunks of 32 in order; the rank of a key is the count
+// of earlier equal digits in its warp segment, then the warp-ordered prefix,
+// then the tile's global offset for the digit.
+__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t* keys_in, const uint32_t* vals_in,
+                                                              size_t n, int shift, const uint32_t* offsets,
+                                                              int ntiles, uint32_t* keys_out,
+                                                              uint32_t* vals_out, int vals_identity) {
+  __shared__ uint32_t wh[RS_WARPS][256];
+  __shared__ uint32_t tile_off[256];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&wh[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < 256; i += RS_THREADS) tile_off[i] = offsets[(size_t)i * ntiles + blockIdx.x];
+  __syncthreads();
+  size_t base = (size_t)blockIdx.x * RS_TILE + (size_t)w * RS_WARP_KEYS;
+  uint32_t kk[RS_ITEMS], rank[RS_ITEMS];
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int c = 0; c < RS_ITEMS; ++c) {
+    size_t idx = base + (size_t)c * 32 + lane;
+    bool valid = idx < n;
+    uint32_t key = valid ? keys_in[idx] : 0u;
+    uint32_t dg = valid ? ((key >> shift) & 255u) : 256u;
+    unsigned peers = __match_any_sync(0xffffffffu, dg);
+    uint32_t before = valid ? wh[w][dg] : 0u;
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) wh[w][dg] = before + (uint32_t)__popc(peers);
+    __syncwarp();
+    rank[c] = before + (uint32_t)__popc(peers & lt);
+    kk[c] = key;
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
+    uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < RS_WARPS; ++ww) {
+      uint32_t t = wh[ww][d];
+      wh[ww][d] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < RS_ITEMS; ++c) {
+    size_t idx = base + (size_t)c * 32 + lane;
+    if (idx < n) {
+      uint32_t dg = (kk[c] >> shift) & 255u;
+      uint32_t pos = tile_off[dg] + wh[w][dg] + rank[c];
+      keys_out[pos] = kk[c];
+      vals_out[pos] = vals_identity ? (uint32_t)idx : vals_in[idx];
+    }
+  }
+}
+
+int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, size_t np,
+                     int bits, bool vals_identity, SortScratch& scr, cudaStream_t s, bool* in_alt) {
+  *in_alt = false;
+  if (np == 0) return SG_OK;
+  if (np > 0xFFFFFFFFull) {
+    set_error("radix sort: more than 2^32-1 particles");
+    return SG_ERR_SIZE;
+  }
+  int ntiles = (int)((np + RS_TILE - 1) / RS_TILE);
+  uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
+  int passes = (bits + 7) / 8;
+  if (passes == 0) passes = 1;
+  bool ident = vals_identity;
+  for (int pass = 0; pass < passes; ++pass) {
+    int shift = pass * 8;
+    k_radix_hist<<<ntiles, RS_THREADS, 0, s>>>(ki, np, shift, scr.tile_hist, ntiles);
+    SG_CHECK_LAUNCH();
+    SG_TRY(exclusive_scan_u32(scr.tile_hist, scr.tile_hist, (size_t)256 * ntiles, scr.block_sums, s));
+    k_radix_scatter<<<ntiles, RS_THREADS, 0, s>>>(ki, vi, np, shift, scr.tile_hist, ntiles, ko, vo, ident ? 1 : 0);
+    SG_CHECK_LAUNCH();
+    ident = false;
+    uint32_t* t;
+    t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+    *in_alt = !*in_alt;
+  }
+  return SG_OK;
+}
+
+// ---------------------------------------------------------------- permute / counts
+template <typename real, int D>
+__global__ void __launch_bounds__(256) k_permute(PArrays<real, D> src, PArrays<real, D> dst, const uint32_t* perm,
+                                                 size_t np) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  uint32_t j = perm[i];
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    dst.u[m][i] = src.u[m][j];
+    dst.v[m][i] = src.v[m][j];
+  }
+  dst.w[i] = src.w[j];
+  dst.pid[i] = src.pid[j];
+}
+
+template <typename real, int D>
+int launch_permute(const PArrays<real, D>& src, const PArrays<real, D>& dst, const uint32_t* perm, size_t np,
+                   cudaStream_t s) {
+  if (np == 0) return SG_OK;
+  k_permute<real, D><<<(unsigned)((np + 255) / 256), 256, 0, s>>>(src, dst, perm, np);
+  SG_CHECK_LAUNCH();
+  return SG_OK;
+}
+
+template <typename real, int D>
+__global__ void __launch_bounds__(256) k_unpermute(PArrays<real, D> src, PArrays<real, D> dst, size_t np) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  uint32_t j = src.pid[i];
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    dst.u[m][j] = src.u[m][i];
+    dst.v[m][j] = src.v[m][i];
+  }
+  dst.w[j] = src.w[i];
+  if (dst.pid) dst.pid[j] = j;
+}
+
+template <typename real, int D>
+int launch_unpermute(const PArrays<real, D>& src, const PArrays<real, D>& dst, size_t np, cudaStream_t s) {
+  if (np == 0) return SG_OK;
+  k_unpermute<real, D><<<(unsigned)((np + 255) / 256), 256, 0, s>>>(src, dst, np);
+  SG_CHECK_LAUNCH();
+  return SG_OK;
+}
+
+__global__ void __launch_bounds__(256) k_counts(const uint32_t* keys, size_t np, uint32_t* counts) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool valid = i < np;
+  uint32_t k = valid ? keys[i] : 0xFFFFFFFFu;
+  unsigned peers = __match_any_sync(0xffffffffu, k);
+  if (valid && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[k], (uint32_t)__popc(peers));
+}
+
+int launch_counts(const uint32_t* keys, size_t np, uint32_t* counts, cudaStream_t s) {
+  if (np == 0) return SG_OK;
+  k_counts<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(keys, np, counts);
+  SG_CHECK_LAUNCH();
+  return SG_OK;
+}
+
+#define SG_INST_SORT(real, D)                                                                           \
+  template int launch_keys<real, D>(const PArrays<real, D>&, size_t, int, uint32_t*, uint32_t*,        \
+                                    unsigned long long*, unsigned*, cudaStream_t);                      \
+  template int launch_keys_raw<real, D>(const real* const*, size_t, int, uint32_t*, uint32_t*,         \
+                                        unsigned long long*, unsigned*, cudaStream_t);                  \
+  template int launch_permute<real, D>(const PArrays<real, D>&, const PArrays<real, D>&, const uint32_t*, \
+                                       size_t, cudaStream_t);                                             \
+  template int launch_unpermute<real, D>(const PArrays<real, D>&, const PArrays<real, D>&, size_t, cudaStream_t);
+
+SG_INST_SORT(float, 2)
+SG_INST_SORT(float, 3)
+SG_INST_SORT(double, 2)
+SG_INST_SORT(double, 3)
+
+}  // namespace sg
