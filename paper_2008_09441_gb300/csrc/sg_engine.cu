@@ -67,6 +67,14 @@ class Engine final : public EngineBase {
       SG_TRY(alloc((void**)&P_[set].w, pb * sizeof(real)));
       SG_TRY(alloc((void**)&P_[set].pid, pb * sizeof(uint32_t)));
     }
+    // ---- small device records (the status word is written by the upload check)
+    SG_TRY(alloc((void**)&dd_, sizeof(DevDiag)));
+    SG_TRY(alloc((void**)&status_, sizeof(unsigned)));
+    SG_TRY(alloc((void**)&checksum_, sizeof(unsigned long long)));
+    SG_CUDA(cudaMemsetAsync(dd_, 0, sizeof(DevDiag), stream_));
+    SG_CUDA(cudaMemsetAsync(status_, 0, sizeof(unsigned), stream_));
+    SG_CUDA(cudaMemsetAsync(checksum_, 0, sizeof(unsigned long long), stream_));
+
     cur_ = 0;
     SG_TRY(upload_particles(parts));
     SG_TRY(alloc((void**)&keys_, pb * 4));
@@ -75,14 +83,6 @@ class Engine final : public EngineBase {
     SG_TRY(alloc((void**)&vals_alt_, pb * 4));
     SG_TRY(alloc((void**)&sort_scr_, sort_scratch_words(np_) * 4));
     sort_scratch_bind(scr_, sort_scr_, np_);
-
-    // ---- small device records
-    SG_TRY(alloc((void**)&dd_, sizeof(DevDiag)));
-    SG_TRY(alloc((void**)&status_, sizeof(unsigned)));
-    SG_TRY(alloc((void**)&checksum_, sizeof(unsigned long long)));
-    SG_CUDA(cudaMemsetAsync(dd_, 0, sizeof(DevDiag), stream_));
-    SG_CUDA(cudaMemsetAsync(status_, 0, sizeof(unsigned), stream_));
-    SG_CUDA(cudaMemsetAsync(checksum_, 0, sizeof(unsigned long long), stream_));
     nke_ = push_blocks(np_);
     SG_TRY(alloc((void**)&ke_partials_, (size_t)nke_ * sizeof(double)));
     SG_CUDA(cudaMemsetAsync(ke_partials_, 0, (size_t)nke_ * sizeof(double), stream_));
