@@ -232,7 +232,11 @@ def main():
     from paper_2008_09441_gb300 import Run, workloads
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    # A dedicated stream (torch's default stream has handle 0, which the
+    # library reads as "create your own"): the library, the L2 flush and the
+    # timing events all run on it.
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     wl = workloads.make(WORKLOAD, n_particles=args.particles, seed=workloads.SEED_BASE + 1 + rank)
     d, n = wl.dim, wl.n
     u = torch.from_numpy(wl.u.astype(np.float32)).to(dev)

@@ -2,46 +2,46 @@
 //   E_comb(x_j) = sum_i c_i (P_i E_i)(x_j)
 // (eq. sparse_filter's c_i and P_i of eq. restriction, applied to the
 // fields).  One block per regular row (a y line in 2D, a (y, z) line in
-// 3D).  For every grid the block interpolates the grid's field in the
-// transverse axes onto the row's coordinate, giving a coarse x-line of
-// 2^l_1 values that is added, times c_i, into a per-level accumulator.  The
-// x-prolongation is then applied once per level by Horner's scheme
-// (prolong level l to l+1, add level l+1, ...), which is exact for nested
+// 3D).  Every (level l, coarse x index k) pair of the row is an independent
+// work item: it interpolates, in the transverse axes, every grid whose x level
+// is l at the row's coordinate and adds c_i times the result (grids in a fixed
+// order).  The x-prolongation is then applied once per level by Horner's
+// scheme (prolong level l to l+1, add level l+1, ...), exact for nested
 // node-centred grids.  Accumulation is float-float (FP32 path) or double
-// (FP64 path); the row is written as hi / lo planes and contributes its
-// share of sum |E_comb|^2 to the field energy.
+// (FP64 path); the row is written as hi / lo planes and contributes its share
+// of sum |E_comb|^2 to the field energy.
 #include "sg_kernels.cuh"
 
 namespace sg {
 
 template <typename real, int D>
-__global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ grids, int ngrids, int lmin,
+__global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ grids, LevelLists ll, int lmin,
                                                  const real* __restrict__ E, size_t S, int n, real* __restrict__ Ehi,
                                                  float* __restrict__ Elo, double* __restrict__ partials) {
   extern __shared__ unsigned char smem_raw[];
-  Acc<real>* A = reinterpret_cast<Acc<real>*>(smem_raw);  // level l at [2^l, 2^(l+1))
+  Acc<real>* A = reinterpret_cast<Acc<real>*>(smem_raw);  // [D][2N], level l of comp m at m*2N + [2^l, 2^(l+1))
   __shared__ double red[32];
   const int N = 1 << n;
   const size_t ND = (size_t)N * (D == 2 ? N : (size_t)N * N);
   const int row = blockIdx.x;
   const int y = row & (N - 1);
   const int z = (D == 3) ? (row >> n) : 0;
-  Acc<real> energy;
-  for (int m = 0; m < D; ++m) {
-    for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) A[i] = Acc<real>();
-    __syncthreads();
-    for (int gi = 0; gi < ngrids; ++gi) {
-      const GridDesc g = grids[gi];
-      const int l1 = g.l[0];
-      const int nx = 1 << l1;
+
+  // zero the levels below lmin that Horner reads (none) and fill the rest
+  for (int e = threadIdx.x + (1 << lmin); e < 2 * N; e += blockDim.x) {
+    const int l = 31 - __clz(e);
+    const int kx = e - (1 << l);
+    Acc<real> acc[D];
+    for (int gi = ll.start[l]; gi < ll.start[l + 1]; ++gi) {
+      const GridDesc g = grids[ll.grid[gi]];
+      const int nx = 1 << l;
       const int ry = n - g.l[1];
       const int ny = 1 << g.l[1];
       const int ky0 = y >> ry;
       const int ky1 = (ky0 + 1) & (ny - 1);
       const real fy = (real)(y & ((1 << ry) - 1)) / (real)(1 << ry);
-      int kz0 = 0, kz1 = 0;
+      int kz0 = 0, kz1 = 0, nz = 1;
       real fz = (real)0;
-      int nz = 1;
       if (D == 3) {
         const int rz = n - g.l[2];
         nz = 1 << g.l[2];
@@ -49,9 +49,10 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
         kz1 = (kz0 + 1) & (nz - 1);
         fz = (real)(z & ((1 << rz) - 1)) / (real)(1 << rz);
       }
-      const real* base = E + (size_t)m * S + g.offset;
       const real c = (real)g.coeff;
-      for (int kx = threadIdx.x; kx < nx; kx += blockDim.x) {
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        const real* base = E + (size_t)m * S + g.offset;
         Acc<real> val;
         if (D == 2) {
           val.add_prod((real)1 - fy, base[(size_t)ky0 * nx + kx]);
@@ -66,58 +67,62 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
           }
         }
         val.scale(c);  // |c| is 1 or 2 (a power of two): exact
-        A[nx + kx].add_acc(val);
+        acc[m].add_acc(val);
       }
-      // the same thread owns (level, kx) for every grid: no sync needed here
+    }
+#pragma unroll
+    for (int m = 0; m < D; ++m) A[m * 2 * N + e] = acc[m];
+  }
+  __syncthreads();
+  for (int l = lmin; l < n; ++l) {
+    const int cnt = 2 << l;  // size of level l+1
+    const int half = 1 << l;
+    for (int e2 = threadIdx.x; e2 < D * cnt; e2 += blockDim.x) {
+      const int m = e2 / cnt, e = e2 - m * cnt;
+      Acc<real>* Am = A + m * 2 * N;
+      const int k = e >> 1;
+      Acc<real> v = Am[half + k];
+      if (e & 1) {
+        v.add_acc(Am[half + ((k + 1) & (half - 1))]);
+        v.scale((real)0.5);
+      }
+      Am[cnt + e].add_acc(v);
     }
     __syncthreads();
-    for (int l = lmin; l < n; ++l) {
-      const int cnt = 2 << l;  // size of level l+1
-      const int half = 1 << l;
-      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int k = e >> 1;
-        Acc<real> v = A[half + k];
-        if (e & 1) {
-          v.add_acc(A[half + ((k + 1) & (half - 1))]);
-          v.scale((real)0.5);
-        }
-        A[cnt + e].add_acc(v);
-      }
-      __syncthreads();
-    }
-    for (int x = threadIdx.x; x < N; x += blockDim.x) {
-      const Acc<real> v = A[N + x];
-      const size_t o = (size_t)m * ND + (size_t)row * N + x;
-      Ehi[o] = (real)v.hi();
-      if (Elo) Elo[o] = (float)v.lo();
-      energy.add_prod((real)v.hi(), (real)v.hi());
-      energy.add((real)2 * (real)v.hi() * (real)v.lo());
-    }
-    __syncthreads();
+  }
+  Acc<real> energy;
+  for (int e2 = threadIdx.x; e2 < D * N; e2 += blockDim.x) {
+    const int m = e2 / N, x = e2 - m * N;
+    const Acc<real> v = A[m * 2 * N + N + x];
+    const size_t o = (size_t)m * ND + (size_t)row * N + x;
+    Ehi[o] = (real)v.hi();
+    if (Elo) Elo[o] = (float)v.lo();
+    energy.add_prod((real)v.hi(), (real)v.hi());
+    energy.add((real)2 * (real)v.hi() * (real)v.lo());
   }
   double tot = block_sum_double(energy.to_double(), red);
   if (threadIdx.x == 0) partials[row] = tot;
 }
 
 template <typename real, int D>
-int launch_combine(const GridDesc* grids, int ngrids, int lmin, const real* E, size_t S, int n, real* Ehi,
+int launch_combine(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n, real* Ehi,
                    float* Elo, double* energy_partials, cudaStream_t s) {
   const int N = 1 << n;
   unsigned rows = (unsigned)(D == 2 ? N : N * N);
-  size_t smem = (size_t)2 * N * sizeof(Acc<real>);
+  size_t smem = (size_t)D * 2 * N * sizeof(Acc<real>);
   static bool attr_set = false;
   if (!attr_set) {
     SG_CUDA(cudaFuncSetAttribute(k_combine<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  k_combine<real, D><<<rows, 256, smem, s>>>(grids, ngrids, lmin, E, S, n, Ehi, Elo, energy_partials);
+  k_combine<real, D><<<rows, 256, smem, s>>>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
 
-#define SG_INST_COMB(real, D)                                                                         \
-  template int launch_combine<real, D>(const GridDesc*, int, int, const real*, size_t, int, real*, float*, \
-                                       double*, cudaStream_t);
+#define SG_INST_COMB(real, D)                                                                                   \
+  template int launch_combine<real, D>(const GridDesc*, const LevelLists&, int, const real*, size_t, int, real*, \
+                                       float*, double*, cudaStream_t);
 SG_INST_COMB(float, 2)
 SG_INST_COMB(float, 3)
 SG_INST_COMB(double, 2)

@@ -185,6 +185,30 @@ struct Acc<double> {
   __device__ __forceinline__ double lo() const { return 0.0; }
 };
 
+// Four consecutive values with 16-byte vector loads / stores (the arrays
+// come from cudaMalloc and every vector index is a multiple of 4).
+template <typename real>
+struct V4 {
+  real x[4];
+};
+
+__device__ __forceinline__ V4<float> ld4(const float* p) {
+  float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  return {{t.x, t.y, t.z, t.w}};
+}
+__device__ __forceinline__ V4<double> ld4(const double* p) {
+  double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return {{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float* p, const V4<float>& v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v.x[0], v.x[1], v.x[2], v.x[3]);
+}
+__device__ __forceinline__ void st4(double* p, const V4<double>& v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v.x[0], v.x[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v.x[2], v.x[3]);
+}
+
 // Complex value in the run's precision.
 template <typename real>
 struct cplx {

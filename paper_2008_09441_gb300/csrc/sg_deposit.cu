@@ -54,13 +54,39 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
     dmin[m] = INT_MAX;
     dmax[m] = INT_MIN;
   }
+  // Items: DEP_ITEMS / 4 vectors of four consecutive particles per thread
+  // (16-byte loads); the ragged end of the last chunk is read element-wise.
+  real ub[DEP_ITEMS][D], wb[DEP_ITEMS];
+#pragma unroll
+  for (int j = 0; j < DEP_ITEMS / 4; ++j) {
+    const size_t i0 = chunk + ((size_t)j * DEP_THREADS + threadIdx.x) * 4;
+    if (i0 + 4 <= np) {
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        V4<real> t = ld4(p.u[m] + i0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ub[4 * j + k][m] = t.x[k];
+      }
+      V4<real> t = ld4(p.w + i0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) wb[4 * j + k] = t.x[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool ok = i0 + k < np;
+#pragma unroll
+        for (int m = 0; m < D; ++m) ub[4 * j + k][m] = ok ? p.u[m][i0 + k] : (real)0;
+        wb[4 * j + k] = ok ? p.w[i0 + k] : (real)0;
+      }
+    }
+  }
 #pragma unroll
   for (int it = 0; it < DEP_ITEMS; ++it) {
-    size_t i = chunk + (size_t)it * DEP_THREADS + threadIdx.x;
+    const size_t i = chunk + ((size_t)(it >> 2) * DEP_THREADS + threadIdx.x) * 4 + (it & 3);
     if (i < np) {
 #pragma unroll
       for (int m = 0; m < D; ++m) {
-        real s = p.u[m][i] * (real)N;
+        real s = ub[it][m] * (real)N;
         int ci = (int)s;
         ci = ci < 0 ? 0 : (ci > mask ? mask : ci);
         c[it][m] = ci;
@@ -69,7 +95,7 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
         dmin[m] = min(dmin[m], dd);
         dmax[m] = max(dmax[m], dd);
       }
-      q[it] = p.w[i] * inv_cell_vol;
+      q[it] = wb[it] * inv_cell_vol;
     } else {
       q[it] = (real)0;
 #pragma unroll
@@ -205,8 +231,7 @@ __global__ void __launch_bounds__(256) k_restrict_lines(const LineJob* __restric
   extern __shared__ unsigned char smem_raw[];
   real* buf = reinterpret_cast<real*>(smem_raw);
   int b = blockIdx.x;
-  int j = 0;
-  while (j + 1 < njobs && jobs[j + 1].block_begin <= b) ++j;
+  const int j = find_job(jobs, njobs);
   const LineJob& J = jobs[j];
   const int top = J.top;
   const int len = 1 << top;

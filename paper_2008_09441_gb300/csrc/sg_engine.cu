@@ -79,10 +79,11 @@ class Engine final : public EngineBase {
     SG_TRY(upload_particles(parts));
     SG_TRY(alloc((void**)&keys_, pb * 4));
     SG_TRY(alloc((void**)&keys_alt_, pb * 4));
-    SG_TRY(alloc((void**)&vals_, pb * 4));
-    SG_TRY(alloc((void**)&vals_alt_, pb * 4));
-    SG_TRY(alloc((void**)&sort_scr_, sort_scratch_words(np_) * 4));
-    sort_scratch_bind(scr_, sort_scr_, np_);
+    tile_shift_ = std::max(0, n_ - 12 / D);
+    ntiles_ = (size_t)1 << (D * (n_ - tile_shift_));
+    SG_TRY(alloc((void**)&tile_count_, ntiles_ * 4));
+    SG_TRY(alloc((void**)&cursor_, ntiles_ * 4));
+    SG_TRY(alloc((void**)&scan_sums_, scan_block_sums_words(ntiles_) * 4));
     nke_ = push_blocks(np_);
     SG_TRY(alloc((void**)&ke_partials_, (size_t)nke_ * sizeof(double)));
     SG_CUDA(cudaMemsetAsync(ke_partials_, 0, (size_t)nke_ * sizeof(double), stream_));
@@ -632,6 +633,20 @@ class Engine final : public EngineBase {
     grid_bufs_.clear();
     SG_TRY(galloc((void**)&grids_dev_, ngrids_ * sizeof(GridDesc)));
     SG_TRY(galloc((void**)&charges_dev_, ngrids_ * sizeof(double)));
+    {  // grids grouped by x level for the combination
+      std::vector<int> order;
+      std::memset(&levels_, 0, sizeof(levels_));
+      for (int l = 0; l <= n_; ++l) {
+        levels_.start[l] = (int)order.size();
+        for (int g = 0; g < ngrids_; ++g)
+          if (gdesc_[g].l[0] == l) order.push_back(g);
+      }
+      levels_.start[n_ + 1] = (int)order.size();
+      int* dev = nullptr;
+      SG_TRY(galloc((void**)&dev, order.size() * sizeof(int)));
+      SG_CUDA(cudaMemcpyAsync(dev, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, stream_));
+      levels_.grid = dev;
+    }
     SG_TRY(galloc((void**)&rho_arena_, S_ * sizeof(real)));
     SG_TRY(galloc((void**)&A_, S_ * sizeof(cplx<real>)));
     SG_TRY(galloc((void**)&B_, (size_t)D * S_ * sizeof(cplx<real>)));
@@ -813,7 +828,7 @@ class Engine final : public EngineBase {
     return (real)(1.0 / hd);
   }
 
-  int enqueue_push(double dt, bool drift, double* ke) {
+  int enqueue_push(double dt, bool drift, double* ke, bool fuse_sort = false) {
     PushParams<real> pp;
     std::memset(&pp, 0, sizeof(pp));
     pp.qm = (real)cfg_.qm;
@@ -829,18 +844,41 @@ class Engine final : public EngineBase {
     pp.boris = boris ? 1 : 0;
     pp.has_eext = eext ? 1 : 0;
     pp.drift = drift ? 1 : 0;
-    return launch_push<real, D>(P_[cur_], np_, n_, Ehi_, pp, ke, status_, stream_);
+    SortFuse sf;
+    if (fuse_sort) {
+      SG_TRY(sort_reset());
+      sf = sort_fuse();
+    }
+    return launch_push<real, D>(P_[cur_], np_, n_, Ehi_, pp, ke, status_, sf, stream_);
   }
 
-  int enqueue_sort() {
+  // Step sort: counting sort of the particles by tile key (the Morton key of
+  // the level-(n - tile_shift) cell), in two halves: keys + tile counts
+  // (emitted by the push on sort steps, or by k_tile_keys), then the scan of
+  // the counts and one scatter pass of the particle payload.
+  SortFuse sort_fuse() const {
+    SortFuse sf;
+    sf.keys = keys_;
+    sf.tile_count = tile_count_;
+    sf.checksum = checksum_;
+    sf.tile_shift = tile_shift_;
+    return sf;
+  }
+  int sort_reset() {
     SG_CUDA(cudaMemsetAsync(checksum_, 0, sizeof(unsigned long long), stream_));
-    SG_TRY(launch_keys<real, D>(P_[cur_], np_, n_, keys_, nullptr, checksum_, status_, stream_));
-    bool in_alt = false;
-    SG_TRY(radix_sort_pairs(keys_, vals_, keys_alt_, vals_alt_, np_, D * n_, true, scr_, stream_, &in_alt));
-    const uint32_t* perm = in_alt ? vals_alt_ : vals_;
-    SG_TRY(launch_permute<real, D>(P_[cur_], P_[cur_ ^ 1], perm, np_, stream_));
+    SG_CUDA(cudaMemsetAsync(tile_count_, 0, ntiles_ * sizeof(uint32_t), stream_));
+    return SG_OK;
+  }
+  int sort_finish() {
+    SG_TRY(exclusive_scan_u32(tile_count_, cursor_, ntiles_, scan_sums_, stream_));
+    SG_TRY(launch_tile_scatter<real, D>(P_[cur_], P_[cur_ ^ 1], keys_, cursor_, np_, stream_));
     cur_ ^= 1;
     return SG_OK;
+  }
+  int enqueue_sort() {  // from the current positions (init, load)
+    SG_TRY(sort_reset());
+    SG_TRY(launch_tile_keys<real, D>(P_[cur_], np_, n_, sort_fuse(), status_, stream_));
+    return sort_finish();
   }
 
   int enqueue_deposit() {
@@ -864,12 +902,15 @@ class Engine final : public EngineBase {
     a.tw = tw_;
     a.log_nmax = n_;
     a.dim = D;
+    int maxsize = 0;
+    for (auto& g : gdesc_) maxsize = std::max(maxsize, g.size);
+    if (maxsize <= small_solve_max<real>()) return launch_solve_small<real>(a, ngrids_, maxsize, stream_);
     for (auto& P : fpasses_) SG_TRY(launch_fft_pass<real>(P.kind, a, P.dev, P.njobs, P.nblocks, P.smem, stream_));
     return SG_OK;
   }
 
   int enqueue_combine() {
-    return launch_combine<real, D>(grids_dev_, ngrids_, lmin_, E_arena_, S_, n_, Ehi_, Elo_, fe_partials_, stream_);
+    return launch_combine<real, D>(grids_dev_, levels_, lmin_, E_arena_, S_, n_, Ehi_, Elo_, fe_partials_, stream_);
   }
 
   int enqueue_restrict_solve_combine() {
@@ -884,8 +925,8 @@ class Engine final : public EngineBase {
   }
 
   int enqueue_step(bool do_sort) {
-    SG_TRY(enqueue_push(cfg_.dt, true, ke_partials_));
-    if (do_sort) SG_TRY(enqueue_sort());
+    SG_TRY(enqueue_push(cfg_.dt, true, ke_partials_, do_sort));
+    if (do_sort) SG_TRY(sort_finish());
     SG_TRY(enqueue_fields());
     return launch_finalize_step(fe_partials_, nrows_, ke_partials_, nke_, fe_scale(), dd_, stream_);
   }
@@ -929,9 +970,9 @@ class Engine final : public EngineBase {
   int step_profiled(bool do_sort) {
     unsigned long long l0 = launches_so_far();
     SG_CUDA(cudaEventRecord(ev_[0], stream_));
-    SG_TRY(enqueue_push(cfg_.dt, true, ke_partials_));
+    SG_TRY(enqueue_push(cfg_.dt, true, ke_partials_, do_sort));
     SG_CUDA(cudaEventRecord(ev_[1], stream_));
-    if (do_sort) SG_TRY(enqueue_sort());
+    if (do_sort) SG_TRY(sort_finish());
     SG_CUDA(cudaEventRecord(ev_[2], stream_));
     SG_TRY(enqueue_deposit());
     SG_CUDA(cudaEventRecord(ev_[3], stream_));
@@ -954,8 +995,8 @@ class Engine final : public EngineBase {
 
   int step_adaptive(bool do_sort) {
     unsigned long long l0 = launches_so_far();
-    SG_TRY(enqueue_push(cfg_.dt, true, ke_partials_));
-    if (do_sort) SG_TRY(enqueue_sort());
+    SG_TRY(enqueue_push(cfg_.dt, true, ke_partials_, do_sort));
+    if (do_sort) SG_TRY(sort_finish());
     SG_TRY(enqueue_deposit());
     int t = tau_;
     int st = select_tau(&t, nullptr, nullptr, 0);
@@ -989,8 +1030,10 @@ class Engine final : public EngineBase {
 
   PArrays<real, D> P_[2];
   int cur_ = 0;
-  uint32_t *keys_ = nullptr, *keys_alt_ = nullptr, *vals_ = nullptr, *vals_alt_ = nullptr, *sort_scr_ = nullptr;
-  SortScratch scr_;
+  uint32_t *keys_ = nullptr, *keys_alt_ = nullptr;
+  uint32_t *tile_count_ = nullptr, *cursor_ = nullptr, *scan_sums_ = nullptr;
+  int tile_shift_ = 0;
+  size_t ntiles_ = 1;
   DevDiag* dd_ = nullptr;
   unsigned* status_ = nullptr;
   unsigned long long* checksum_ = nullptr;
@@ -1006,6 +1049,7 @@ class Engine final : public EngineBase {
   std::vector<GridSpec> grids_;
   std::vector<GridDesc> gdesc_;
   int ngrids_ = 0, lmin_ = 0;
+  LevelLists levels_{};
   GridDesc* grids_dev_ = nullptr;
   double* charges_dev_ = nullptr;
   real* rho_arena_ = nullptr;

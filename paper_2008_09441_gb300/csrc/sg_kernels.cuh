@@ -81,6 +81,27 @@ struct LineJob {
   void* dst[LJ_MAX_TARGETS];
 };
 
+// Block -> job of a pass: the last job whose block_begin <= blockIdx.x.  The
+// first warp reads 32 job headers at a time (no chain of dependent loads).
+template <typename Job>
+__device__ __forceinline__ int find_job(const Job* __restrict__ jobs, int njobs) {
+  __shared__ int s_job;
+  const int b = blockIdx.x;
+  if (threadIdx.x < 32) {
+    int best = 0;
+    for (int base = 0; base < njobs; base += 32) {
+      const int idx = base + (int)threadIdx.x;
+      const bool le = idx < njobs && jobs[idx].block_begin <= b;
+      const unsigned m = __ballot_sync(0xffffffffu, le);
+      if (m) best = base + 31 - __clz(m);
+      if (m != 0xffffffffu) break;
+    }
+    if (threadIdx.x == 0) s_job = best;
+  }
+  __syncthreads();
+  return s_job;
+}
+
 // Restriction pyramid (full weighting 1/4, 1/2, 1/4 per level halving, the
 // exact form of R along one axis for nested node-centred grids).
 template <typename real>
@@ -118,6 +139,13 @@ template <typename real>
 int launch_fft_pass(int kind, const SolveArena<real>& a, const FftJob* jobs_dev, int njobs,
                     int nblocks, int smem_bytes, cudaStream_t s);
 
+// All component grids in one launch, one block per grid, whole grid in shared
+// memory (used when every grid has at most SMALL_SOLVE_MAX<real> points).
+template <typename real>
+int launch_solve_small(const SolveArena<real>& a, int ngrids, int max_size, cudaStream_t s);
+template <typename real>
+constexpr int small_solve_max() { return sizeof(real) == 4 ? 4096 : 2048; }
+
 // Generic in-place complex FFT of a whole N^D array (regular grid) along one
 // axis, forward or inverse (unnormalised), in the given precision.
 template <typename real>
@@ -125,8 +153,14 @@ int launch_fft_array_axis(cplx<real>* data, int D, int logn, int axis, bool inve
                           const cplx<real>* tw, int log_nmax, cudaStream_t s);
 
 // ---------------------------------------------------------------- combine
+// Grids grouped by their x level: grid[start[l] .. start[l+1]) have l_1 = l.
+struct LevelLists {
+  int start[18];
+  const int* grid;
+};
+
 template <typename real, int D>
-int launch_combine(const GridDesc* grids, int ngrids, int lmin, const real* E, size_t S, int n,
+int launch_combine(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n,
                    real* Ehi, float* Elo, double* energy_partials, cudaStream_t s);
 
 // ---------------------------------------------------------------- push
@@ -141,10 +175,30 @@ struct PushParams {
   int drift;      // 0: velocity only (initial half kick), 1: kick + drift
 };
 
+// Sort work fused into the push on sort steps (keys == nullptr: none).
+struct SortFuse {
+  uint32_t* keys = nullptr;        // tile key per particle (storage order)
+  uint32_t* tile_count = nullptr;  // per-tile counts (zeroed by the caller)
+  unsigned long long* checksum = nullptr;
+  int tile_shift = 0;              // tile = level-n Morton key >> (D * tile_shift)
+};
+
 template <typename real, int D>
 int launch_push(const PArrays<real, D>& p, size_t np, int n, const real* Ecomb, PushParams<real> pp,
-                double* ke_partials, unsigned* status, cudaStream_t s);
+                double* ke_partials, unsigned* status, const SortFuse& sf, cudaStream_t s);
 int push_blocks(size_t np);
+
+// ---------------------------------------------------------------- step sort (tile counting sort)
+// Tile keys and counts of the current positions (the push emits them on sort
+// steps; this kernel serves init and checkpoint load).
+template <typename real, int D>
+int launch_tile_keys(const PArrays<real, D>& p, size_t np, int n, const SortFuse& sf, unsigned* status,
+                     cudaStream_t s);
+// Scatter every particle to its tile's next free slot (cursor = exclusive
+// scan of the tile counts): one pass, reads key + payload, writes payload.
+template <typename real, int D>
+int launch_tile_scatter(const PArrays<real, D>& src, const PArrays<real, D>& dst, const uint32_t* keys,
+                        uint32_t* cursor, size_t np, cudaStream_t s);
 
 // ---------------------------------------------------------------- misc
 template <typename real, int D>

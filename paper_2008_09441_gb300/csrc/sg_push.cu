@@ -3,6 +3,11 @@
 // leapfrog kick (Boris rotation when B != 0) and the drift
 // x^{n+1} = x^n + v^{n+1/2} dt, wrapped into the periodic box.  Each thread
 // also adds 0.5 m_p v^{n-1/2}.v^{n+1/2} to the time-centred kinetic energy.
+//
+// Each thread advances four consecutive particles per iteration with 16-byte
+// vector loads and stores.  On a sort step the kernel also emits the tile key
+// of every new position and the per-tile counts (the first half of the
+// counting sort), and adds sum (cell key + 1) to the checksum.
 #include "sg_kernels.cuh"
 
 namespace sg {
@@ -11,119 +16,211 @@ static __device__ __forceinline__ bool finite_r(float x) { return isfinite(x); }
 static __device__ __forceinline__ bool finite_r(double x) { return isfinite(x); }
 
 int push_blocks(size_t np) {
-  size_t b = (np + 255) / 256;
-  const size_t cap = 152 * 16;
+  size_t b = (np / 4 + 255) / 256;
+  const size_t cap = 152 * 8;
   if (b > cap) b = cap;
   if (b == 0) b = 1;
   return (int)b;
 }
 
+// Advance one particle in registers.
+template <typename real, int D>
+__device__ __forceinline__ void push_one(real (&u)[D], real (&v)[D], real w, int n, const real* __restrict__ Ec,
+                                         size_t ND, const PushParams<real>& pp, Acc<real>& ke, bool& bad) {
+  const int N = 1 << n;
+  const int mask = N - 1;
+  const real half = (real)0.5;
+  int c[D];
+  real f[D], E[D];
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    real s = u[m] * (real)N;
+    int ci = (int)s;
+    ci = ci < 0 ? 0 : (ci > mask ? mask : ci);
+    c[m] = ci;
+    f[m] = s - (real)ci;
+    E[m] = (real)0;
+  }
+#pragma unroll
+  for (int corner = 0; corner < (1 << D); ++corner) {
+    real wgt = (real)1;
+    size_t node = 0, gs = 1;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      int b = (corner >> m) & 1;
+      wgt *= b ? f[m] : ((real)1 - f[m]);
+      node += (size_t)((c[m] + b) & mask) * gs;
+      gs *= (size_t)N;
+    }
+#pragma unroll
+    for (int m = 0; m < D; ++m) E[m] += wgt * __ldg(Ec + (size_t)m * ND + node);
+  }
+  if (pp.has_eext) {
+#pragma unroll
+    for (int m = 0; m < D; ++m) E[m] += pp.eext[m] * (u[m] - half);
+  }
+  real vm[D];
+  const real hk = pp.qm * pp.dt * half;
+#pragma unroll
+  for (int m = 0; m < D; ++m) vm[m] = v[m] + hk * E[m];
+  if (pp.boris) {
+    if (D == 2) {
+      const real tz = pp.tB[2];
+      const real sz = (real)2 * tz / ((real)1 + tz * tz);
+      const real px = vm[0] + vm[1] * tz;
+      const real py = vm[1] - vm[0] * tz;
+      vm[0] = vm[0] + py * sz;
+      vm[1] = vm[1] - px * sz;
+    } else {
+      const real t0 = pp.tB[0], t1 = pp.tB[1], t2 = pp.tB[2];
+      const real tt = t0 * t0 + t1 * t1 + t2 * t2;
+      const real s0 = (real)2 * t0 / ((real)1 + tt), s1 = (real)2 * t1 / ((real)1 + tt),
+                 s2 = (real)2 * t2 / ((real)1 + tt);
+      const real a0 = vm[0], a1 = vm[1], a2 = vm[D - 1];
+      const real p0 = a0 + (a1 * t2 - a2 * t1);
+      const real p1 = a1 + (a2 * t0 - a0 * t2);
+      const real p2 = a2 + (a0 * t1 - a1 * t0);
+      vm[0] = a0 + (p1 * s2 - p2 * s1);
+      vm[1] = a1 + (p2 * s0 - p0 * s2);
+      vm[D - 1] = a2 + (p0 * s1 - p1 * s0);
+    }
+  }
+  real dot = (real)0;
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    real vn = vm[m] + hk * E[m];
+    dot += v[m] * vn;
+    bad |= !finite_r(vn);
+    v[m] = vn;
+  }
+  ke.add(half * (w / pp.qm) * dot);
+  if (pp.drift) {
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      real un = wrap_unit(u[m] + v[m] * pp.dt_over_L[m]);
+      bad |= !finite_r(un);
+      u[m] = un;
+    }
+  }
+}
+
+// Tile key (Morton key of the level-(n - shift) cell) of a wrapped position;
+// also returns the level-n key for the checksum.
+template <typename real, int D>
+__device__ __forceinline__ uint32_t tile_key(const real (&u)[D], int n, int shift, uint32_t* full) {
+  const int N = 1 << n;
+  int c[D];
+#pragma unroll
+  for (int m = 0; m < D; ++m) c[m] = cell_of(u[m], n, N);
+  uint32_t k = morton_key<D>(c, n);
+  *full = k;
+  return k >> (D * shift);
+}
+
+// Warp-aggregated count of equal tile keys among the active lanes.
+__device__ __forceinline__ void count_tile(uint32_t* tile_count, uint32_t t, bool valid) {
+  const unsigned act = __activemask();
+  const uint32_t key = valid ? t : 0xFFFFFFFFu;
+  const unsigned peers = __match_any_sync(act, key);
+  if (valid && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&tile_count[t], (uint32_t)__popc(peers));
+}
+
 template <typename real, int D>
 __global__ void __launch_bounds__(256) k_push(PArrays<real, D> p, size_t np, int n, const real* __restrict__ Ec,
                                               PushParams<real> pp, double* __restrict__ ke_partials,
-                                              unsigned* status) {
+                                              unsigned* status, SortFuse sf) {
   __shared__ double red[32];
   const int N = 1 << n;
-  const int mask = N - 1;
   const size_t ND = (size_t)N * (D == 2 ? N : (size_t)N * N);
-  const real half = (real)0.5;
   Acc<real> ke;
   bool bad = false;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += (size_t)gridDim.x * blockDim.x) {
-    real u[D], v[D], E[D];
-    int c[D];
-    real f[D];
+  unsigned long long cks = 0;
+  const size_t nvec = np >> 2;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t iv = (size_t)blockIdx.x * blockDim.x + threadIdx.x; iv < nvec; iv += stride) {
+    const size_t i0 = iv << 2;
+    V4<real> U[D], Vv[D];
 #pragma unroll
     for (int m = 0; m < D; ++m) {
-      u[m] = p.u[m][i];
-      v[m] = p.v[m][i];
-      real s = u[m] * (real)N;
-      int ci = (int)s;
-      ci = ci < 0 ? 0 : (ci > mask ? mask : ci);
-      c[m] = ci;
-      f[m] = s - (real)ci;
-      E[m] = (real)0;
+      U[m] = ld4(p.u[m] + i0);
+      Vv[m] = ld4(p.v[m] + i0);
     }
-    const real w = p.w[i];
+    const V4<real> W = ld4(p.w + i0);
 #pragma unroll
-    for (int corner = 0; corner < (1 << D); ++corner) {
-      real wgt = (real)1;
-      size_t node = 0, gs = 1;
+    for (int j = 0; j < 4; ++j) {
+      real u[D], v[D];
 #pragma unroll
       for (int m = 0; m < D; ++m) {
-        int b = (corner >> m) & 1;
-        wgt *= b ? f[m] : ((real)1 - f[m]);
-        node += (size_t)((c[m] + b) & mask) * gs;
-        gs *= (size_t)N;
+        u[m] = U[m].x[j];
+        v[m] = Vv[m].x[j];
       }
+      push_one<real, D>(u, v, W.x[j], n, Ec, ND, pp, ke, bad);
 #pragma unroll
-      for (int m = 0; m < D; ++m) E[m] += wgt * __ldg(Ec + (size_t)m * ND + node);
-    }
-    if (pp.has_eext) {
-#pragma unroll
-      for (int m = 0; m < D; ++m) E[m] += pp.eext[m] * (u[m] - half);
-    }
-    real vm[D], vn[D];
-    const real hk = pp.qm * pp.dt * half;
-#pragma unroll
-    for (int m = 0; m < D; ++m) vm[m] = v[m] + hk * E[m];
-    if (pp.boris) {
-      if (D == 2) {
-        const real tz = pp.tB[2];
-        const real sz = (real)2 * tz / ((real)1 + tz * tz);
-        const real px = vm[0] + vm[1] * tz;
-        const real py = vm[1] - vm[0] * tz;
-        vm[0] = vm[0] + py * sz;
-        vm[1] = vm[1] - px * sz;
-      } else {
-        const real t0 = pp.tB[0], t1 = pp.tB[1], t2 = pp.tB[2];
-        const real tt = t0 * t0 + t1 * t1 + t2 * t2;
-        const real s0 = (real)2 * t0 / ((real)1 + tt), s1 = (real)2 * t1 / ((real)1 + tt),
-                   s2 = (real)2 * t2 / ((real)1 + tt);
-        const real a0 = vm[D > 1 ? 0 : 0], a1 = vm[1], a2 = vm[D - 1];
-        const real p0 = a0 + (a1 * t2 - a2 * t1);
-        const real p1 = a1 + (a2 * t0 - a0 * t2);
-        const real p2 = a2 + (a0 * t1 - a1 * t0);
-        vm[0] = a0 + (p1 * s2 - p2 * s1);
-        vm[1] = a1 + (p2 * s0 - p0 * s2);
-        vm[D - 1] = a2 + (p0 * s1 - p1 * s0);
+      for (int m = 0; m < D; ++m) {
+        U[m].x[j] = u[m];
+        Vv[m].x[j] = v[m];
+      }
+      if (sf.keys) {
+        uint32_t full;
+        uint32_t t = tile_key<real, D>(u, n, sf.tile_shift, &full);
+        sf.keys[i0 + j] = t;
+        cks += (unsigned long long)full + 1ull;
+        count_tile(sf.tile_count, t, true);
       }
     }
-    real dot = (real)0;
 #pragma unroll
     for (int m = 0; m < D; ++m) {
-      vn[m] = vm[m] + hk * E[m];
-      dot += v[m] * vn[m];
-      bad |= !finite_r(vn[m]);
-      p.v[m][i] = vn[m];
+      if (pp.drift) st4(p.u[m] + i0, U[m]);
+      st4(p.v[m] + i0, Vv[m]);
     }
-    ke.add(half * (w / pp.qm) * dot);
-    if (pp.drift) {
+  }
+  // ragged tail (np not a multiple of 4): block 0 takes it particle by particle
+  if (blockIdx.x == 0) {
+    const size_t i = (nvec << 2) + threadIdx.x;
+    const bool valid = i < np;
+    if (valid) {
+      real u[D], v[D];
 #pragma unroll
       for (int m = 0; m < D; ++m) {
-        real un = wrap_unit(u[m] + vn[m] * pp.dt_over_L[m]);
-        bad |= !finite_r(un);
-        p.u[m][i] = un;
+        u[m] = p.u[m][i];
+        v[m] = p.v[m][i];
+      }
+      push_one<real, D>(u, v, p.w[i], n, Ec, ND, pp, ke, bad);
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        if (pp.drift) p.u[m][i] = u[m];
+        p.v[m][i] = v[m];
+      }
+      if (sf.keys) {
+        uint32_t full;
+        uint32_t t = tile_key<real, D>(u, n, sf.tile_shift, &full);
+        sf.keys[i] = t;
+        cks += (unsigned long long)full + 1ull;
+        atomicAdd(&sf.tile_count[t], 1u);
       }
     }
   }
   if (bad) atomicOr(status, ST_NONFINITE);
+  if (sf.checksum) {
+    cks = warp_sum(cks);
+    if ((threadIdx.x & 31) == 0 && cks) atomicAdd(sf.checksum, cks);
+  }
   double tot = block_sum_double(ke.to_double(), red);
   if (threadIdx.x == 0 && ke_partials) ke_partials[blockIdx.x] = tot;
 }
 
 template <typename real, int D>
 int launch_push(const PArrays<real, D>& p, size_t np, int n, const real* Ecomb, PushParams<real> pp,
-                double* ke_partials, unsigned* status, cudaStream_t s) {
+                double* ke_partials, unsigned* status, const SortFuse& sf, cudaStream_t s) {
   int blocks = push_blocks(np);
-  k_push<real, D><<<blocks, 256, 0, s>>>(p, np, n, Ecomb, pp, ke_partials, status);
+  k_push<real, D><<<blocks, 256, 0, s>>>(p, np, n, Ecomb, pp, ke_partials, status, sf);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
 
 #define SG_INST_PUSH(real, D)                                                                           \
   template int launch_push<real, D>(const PArrays<real, D>&, size_t, int, const real*, PushParams<real>, \
-                                    double*, unsigned*, cudaStream_t);
+                                    double*, unsigned*, const SortFuse&, cudaStream_t);
 SG_INST_PUSH(float, 2)
 SG_INST_PUSH(float, 3)
 SG_INST_PUSH(double, 2)

@@ -57,8 +57,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(int kind, SolveArena<real> a, 
                                                   int njobs) {
   extern __shared__ unsigned char smem_raw[];
   int b = blockIdx.x;
-  int j = 0;
-  while (j + 1 < njobs && jobs[j + 1].block_begin <= b) ++j;
+  const int j = find_job(jobs, njobs);
   const FftJob& J = jobs[j];
   const GridDesc g = a.grids[J.grid];
   const int logn = J.logn;
@@ -171,6 +170,121 @@ int launch_fft_pass(int kind, const SolveArena<real>& a, const FftJob* jobs_dev,
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
+
+// ---------------------------------------------------------------- one block per grid
+//
+// When every component grid fits in shared memory (twice: spectrum and one
+// field component), one launch solves all of them: a block loads its grid,
+// transforms it along every axis in place (bit-reversal swap, then the
+// butterfly stages), forms each E^_m and transforms it back.
+template <typename real>
+__device__ void fft_axis_inplace(cplx<real>* buf, const int* dims, const int* logs, int S, int ax, bool inverse,
+                                 const cplx<real>* __restrict__ tw, int log_nmax) {
+  const int len = dims[ax], logn = logs[ax];
+  int stride = 1;
+  for (int m = 0; m < ax; ++m) stride *= dims[m];
+  for (int e = threadIdx.x; e < S; e += blockDim.x) {
+    const int t = (e / stride) & (len - 1);
+    const int r = bitrev(t, logn);
+    if (r > t) {
+      const int e2 = e + (r - t) * stride;
+      cplx<real> x = buf[e];
+      buf[e] = buf[e2];
+      buf[e2] = x;
+    }
+  }
+  __syncthreads();
+  const int halfN = len >> 1;
+  for (int s = 1; s <= logn; ++s) {
+    const int half = 1 << (s - 1);
+    const int tshift = log_nmax - s;
+    for (int j = threadIdx.x; j < (S >> 1); j += blockDim.x) {
+      const int L = j >> (logn - 1);
+      const int jj = j & (halfN - 1);
+      const int pos = jj & (half - 1);
+      const int grp = jj >> (s - 1);
+      const int t0 = grp * 2 * half + pos;
+      const int low = L % stride, high = L / stride;
+      const int i0 = low + stride * (t0 + len * high);
+      const int i1 = i0 + half * stride;
+      cplx<real> w = tw[pos << tshift];
+      if (inverse) w.y = -w.y;
+      cplx<real> x0 = buf[i0], x1 = buf[i1];
+      real bx = x1.x * w.x - x1.y * w.y;
+      real by = x1.x * w.y + x1.y * w.x;
+      buf[i0] = {x0.x + bx, x0.y + by};
+      buf[i1] = {x0.x - bx, x0.y - by};
+    }
+    __syncthreads();
+  }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(1024) k_solve_small(SolveArena<real> a) {
+  extern __shared__ unsigned char smem_raw[];
+  const GridDesc g = a.grids[blockIdx.x];
+  const int D = a.dim;
+  int dims[3] = {1, 1, 1}, logs[3] = {0, 0, 0};
+  for (int m = 0; m < D; ++m) {
+    logs[m] = g.l[m];
+    dims[m] = 1 << g.l[m];
+  }
+  const int S = g.size;
+  cplx<real>* A = reinterpret_cast<cplx<real>*>(smem_raw);
+  cplx<real>* B = A + S;
+  for (int e = threadIdx.x; e < S; e += blockDim.x) A[e] = {a.rho[g.offset + e], (real)0};
+  __syncthreads();
+  for (int ax = 0; ax < D; ++ax) fft_axis_inplace<real>(A, dims, logs, S, ax, false, a.tw, a.log_nmax);
+  const real norm = (real)1 / (real)S;
+  for (int m = 0; m < D; ++m) {
+    for (int e = threadIdx.x; e < S; e += blockDim.x) {
+      int idx[3];
+      idx[0] = e & (dims[0] - 1);
+      idx[1] = (e >> logs[0]) & (dims[1] - 1);
+      idx[2] = D == 3 ? (e >> (logs[0] + logs[1])) : 0;
+      real k2 = 0, km = 0;
+      bool nyq_m = false;
+      for (int q = 0; q < D; ++q) {
+        const real kq = (real)(g.kfac[q] * (double)sfreq(idx[q], dims[q]));
+        k2 += kq * kq;
+        if (q == m) {
+          km = kq;
+          nyq_m = idx[q] == (dims[q] >> 1);
+        }
+      }
+      const cplx<real> r = A[e];
+      if (k2 == (real)0 || nyq_m) {
+        B[e] = {(real)0, (real)0};
+      } else {
+        const real fac = km / k2 * norm;
+        B[e] = {r.y * fac, -r.x * fac};
+      }
+    }
+    __syncthreads();
+    for (int ax = 0; ax < D; ++ax) fft_axis_inplace<real>(B, dims, logs, S, ax, true, a.tw, a.log_nmax);
+    for (int e = threadIdx.x; e < S; e += blockDim.x) a.E[(size_t)m * a.S + g.offset + e] = B[e].x;
+    __syncthreads();
+  }
+}
+
+template <typename real>
+int launch_solve_small(const SolveArena<real>& a, int ngrids, int max_size, cudaStream_t s) {
+  if (ngrids == 0) return SG_OK;
+  int threads = max_size / 2;
+  threads = threads < 64 ? 64 : (threads > 1024 ? 1024 : threads);
+  size_t smem = (size_t)2 * max_size * sizeof(cplx<real>);
+  static bool attr_set = false;
+  if (!attr_set) {
+    SG_CUDA(cudaFuncSetAttribute(k_solve_small<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  k_solve_small<real><<<ngrids, threads, smem, s>>>(a);
+  SG_CHECK_LAUNCH();
+  return SG_OK;
+}
+
+template int launch_solve_small<float>(const SolveArena<float>&, int, int, cudaStream_t);
+template int launch_solve_small<double>(const SolveArena<double>&, int, int, cudaStream_t);
 
 // In-place FFT of a whole N^D complex array along one axis (regular grid).
 template <typename real>

@@ -353,6 +353,81 @@ int launch_unpermute(const PArrays<real, D>& src, const PArrays<real, D>& dst, s
   return SG_OK;
 }
 
+// ---------------------------------------------------------------- tile counting sort
+template <typename real, int D>
+__global__ void __launch_bounds__(256) k_tile_keys(PArrays<real, D> p, size_t np, int n, SortFuse sf,
+                                                   unsigned* status) {
+  const int N = 1 << n;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < np;
+  uint32_t t = 0;
+  unsigned long long part = 0;
+  if (valid) {
+    int c[D];
+    bool bad = false;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      real u = p.u[m][i];
+      bad |= !(u >= (real)0 && u < (real)1);
+      c[m] = cell_of(u, n, N);
+    }
+    if (bad) atomicOr(status, ST_KEY_RANGE);
+    uint32_t k = morton_key<D>(c, n);
+    t = k >> (D * sf.tile_shift);
+    sf.keys[i] = t;
+    part = (unsigned long long)k + 1ull;
+  }
+  const unsigned peers = __match_any_sync(0xffffffffu, valid ? t : 0xFFFFFFFFu);
+  if (valid && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&sf.tile_count[t], (uint32_t)__popc(peers));
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0 && part && sf.checksum) atomicAdd(sf.checksum, part);
+}
+
+template <typename real, int D>
+int launch_tile_keys(const PArrays<real, D>& p, size_t np, int n, const SortFuse& sf, unsigned* status,
+                     cudaStream_t s) {
+  if (np == 0) return SG_OK;
+  k_tile_keys<real, D><<<(unsigned)((np + 255) / 256), 256, 0, s>>>(p, np, n, sf, status);
+  SG_CHECK_LAUNCH();
+  return SG_OK;
+}
+
+// Lanes with equal tiles take consecutive slots (leader reserves the group's
+// range); within a tile the order follows warps' arrival, so the step sort is
+// a valid, not a stable, counting sort by tile key.
+template <typename real, int D>
+__global__ void __launch_bounds__(256) k_tile_scatter(PArrays<real, D> src, PArrays<real, D> dst,
+                                                      const uint32_t* __restrict__ keys, uint32_t* cursor,
+                                                      size_t np) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < np;
+  const uint32_t t = valid ? keys[i] : 0xFFFFFFFFu;
+  const unsigned peers = __match_any_sync(0xffffffffu, t);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (valid && lane == leader) base = atomicAdd(&cursor[t], (uint32_t)__popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (!valid) return;
+  const uint32_t pos = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    dst.u[m][pos] = src.u[m][i];
+    dst.v[m][pos] = src.v[m][i];
+  }
+  dst.w[pos] = src.w[i];
+  dst.pid[pos] = src.pid[i];
+}
+
+template <typename real, int D>
+int launch_tile_scatter(const PArrays<real, D>& src, const PArrays<real, D>& dst, const uint32_t* keys,
+                        uint32_t* cursor, size_t np, cudaStream_t s) {
+  if (np == 0) return SG_OK;
+  k_tile_scatter<real, D><<<(unsigned)((np + 255) / 256), 256, 0, s>>>(src, dst, keys, cursor, np);
+  SG_CHECK_LAUNCH();
+  return SG_OK;
+}
+
 __global__ void __launch_bounds__(256) k_counts(const uint32_t* keys, size_t np, uint32_t* counts) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool valid = i < np;
@@ -375,7 +450,11 @@ int launch_counts(const uint32_t* keys, size_t np, uint32_t* counts, cudaStream_
                                         unsigned long long*, unsigned*, cudaStream_t);                  \
   template int launch_permute<real, D>(const PArrays<real, D>&, const PArrays<real, D>&, const uint32_t*, \
                                        size_t, cudaStream_t);                                             \
-  template int launch_unpermute<real, D>(const PArrays<real, D>&, const PArrays<real, D>&, size_t, cudaStream_t);
+  template int launch_unpermute<real, D>(const PArrays<real, D>&, const PArrays<real, D>&, size_t, cudaStream_t); \
+  template int launch_tile_keys<real, D>(const PArrays<real, D>&, size_t, int, const SortFuse&, unsigned*,         \
+                                         cudaStream_t);                                                            \
+  template int launch_tile_scatter<real, D>(const PArrays<real, D>&, const PArrays<real, D>&, const uint32_t*,     \
+                                            uint32_t*, size_t, cudaStream_t);
 
 SG_INST_SORT(float, 2)
 SG_INST_SORT(float, 3)
