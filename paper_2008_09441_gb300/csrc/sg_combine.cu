@@ -26,20 +26,23 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
   const int row = blockIdx.x;
   const int y = row & (N - 1);
   const int z = (D == 3) ? (row >> n) : 0;
+  __shared__ int s_start[18];  // level lists staged in shared memory (dynamic indexing)
+  if (threadIdx.x < 18) s_start[threadIdx.x] = ll.start[threadIdx.x];
+  __syncthreads();
 
-  // zero the levels below lmin that Horner reads (none) and fill the rest
+  // every (level, x index) of the levels Horner reads
   for (int e = threadIdx.x + (1 << lmin); e < 2 * N; e += blockDim.x) {
     const int l = 31 - __clz(e);
     const int kx = e - (1 << l);
     Acc<real> acc[D];
-    for (int gi = ll.start[l]; gi < ll.start[l + 1]; ++gi) {
+    for (int gi = s_start[l]; gi < s_start[l + 1]; ++gi) {
       const GridDesc g = grids[ll.grid[gi]];
       const int nx = 1 << l;
       const int ry = n - g.l[1];
       const int ny = 1 << g.l[1];
       const int ky0 = y >> ry;
       const int ky1 = (ky0 + 1) & (ny - 1);
-      const real fy = (real)(y & ((1 << ry) - 1)) / (real)(1 << ry);
+      const real fy = (real)(y & ((1 << ry) - 1)) * ((real)1 / (real)(1 << ry));  // exact: power of two
       int kz0 = 0, kz1 = 0, nz = 1;
       real fz = (real)0;
       if (D == 3) {
@@ -47,7 +50,7 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
         nz = 1 << g.l[2];
         kz0 = z >> rz;
         kz1 = (kz0 + 1) & (nz - 1);
-        fz = (real)(z & ((1 << rz) - 1)) / (real)(1 << rz);
+        fz = (real)(z & ((1 << rz) - 1)) * ((real)1 / (real)(1 << rz));
       }
       const real c = (real)g.coeff;
 #pragma unroll
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
     const int cnt = 2 << l;  // size of level l+1
     const int half = 1 << l;
     for (int e2 = threadIdx.x; e2 < D * cnt; e2 += blockDim.x) {
-      const int m = e2 / cnt, e = e2 - m * cnt;
+      const int m = e2 >> (l + 1), e = e2 & (cnt - 1);
       Acc<real>* Am = A + m * 2 * N;
       const int k = e >> 1;
       Acc<real> v = Am[half + k];
@@ -92,7 +95,7 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
   }
   Acc<real> energy;
   for (int e2 = threadIdx.x; e2 < D * N; e2 += blockDim.x) {
-    const int m = e2 / N, x = e2 - m * N;
+    const int m = e2 >> n, x = e2 & (N - 1);
     const Acc<real> v = A[m * 2 * N + N + x];
     const size_t o = (size_t)m * ND + (size_t)row * N + x;
     Ehi[o] = (real)v.hi();

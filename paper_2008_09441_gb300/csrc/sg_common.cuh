@@ -84,15 +84,29 @@ struct GridDesc {
 // ---------------------------------------------------------------------------
 // Morton (Z-order) key: bit b of axis m -> key bit b*D + m.
 // ---------------------------------------------------------------------------
+// Spread the low bits of x so that bit b lands on bit 2b (resp. 3b): the
+// usual mask-and-shift interleave, valid for x < 2^16 (resp. 2^10).
+__host__ __device__ __forceinline__ uint32_t spread2(uint32_t x) {
+  x &= 0x0000FFFFu;
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+__host__ __device__ __forceinline__ uint32_t spread3(uint32_t x) {
+  x &= 0x000003FFu;
+  x = (x | (x << 16)) & 0xFF0000FFu;
+  x = (x | (x << 8)) & 0x0300F00Fu;
+  x = (x | (x << 4)) & 0x030C30C3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+
 template <int D>
-__host__ __device__ __forceinline__ uint32_t morton_key(const int* c, int n) {
-  uint32_t key = 0;
-#pragma unroll 1
-  for (int b = 0; b < n; ++b) {
-#pragma unroll
-    for (int m = 0; m < D; ++m) key |= (uint32_t)((c[m] >> b) & 1) << (b * D + m);
-  }
-  return key;
+__host__ __device__ __forceinline__ uint32_t morton_key(const int* c, int /*n*/) {
+  if (D == 2) return spread2((uint32_t)c[0]) | (spread2((uint32_t)c[1]) << 1);
+  return spread3((uint32_t)c[0]) | (spread3((uint32_t)c[1]) << 1) | (spread3((uint32_t)c[D - 1]) << 2);
 }
 
 // Cell index floor(u 2^n) of a position already wrapped into [0,1).  The

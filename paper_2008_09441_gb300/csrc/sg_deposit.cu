@@ -237,58 +237,58 @@ __global__ void __launch_bounds__(256) k_restrict_lines(const LineJob* __restric
   const int len = 1 << top;
   const int C = J.lines_per_block;
   const int line0 = (b - J.block_begin) * C;
-  const int nl = min(C, J.lines - line0);
-  if (nl <= 0) return;
-  long long stride = 1;
-  for (int m = 0; m < J.axis; ++m) stride *= J.dims[m];
+  // All extents are powers of two and lines_per_block divides the line
+  // count, so index arithmetic is shifts and masks.
+  const int nl = C;
+  const int logC = __ffs(C) - 1;
+  int ls = 0;  // log2 of the stride of the line axis
+  for (int m = 0; m < J.axis; ++m) ls += __ffs(J.dims[m]) - 1;
+  const long long smask = (1ll << ls) - 1;
   const real* src = reinterpret_cast<const real*>(J.src);
-  // level l of line i sits at buf[i * 2 len + (2 len - 2^(l+1))]... store
-  // levels as a heap: level l at offset (2^(l) .. 2^(l+1)) within a 2*len slot
+  // levels as a heap: level l of line li at [li * 2 len + 2^l, li * 2 len + 2^(l+1))
   const int slot = 2 * len;
-  for (int e = threadIdx.x; e < nl * len; e += blockDim.x) {
+  for (int e = threadIdx.x; e < (nl << top); e += blockDim.x) {
     int li, t;
     if (J.axis == 0) {
-      li = e / len;
-      t = e % len;
+      li = e >> top;
+      t = e & (len - 1);
     } else {  // consecutive threads take consecutive lines (coalesced columns)
-      li = e % nl;
-      t = e / nl;
+      li = e & (nl - 1);
+      t = e >> logC;
     }
-    long long L = line0 + li;
-    long long low = L % stride, high = L / stride;
-    long long addr = low + stride * (t + (long long)len * high);
+    const long long L = line0 + li;
+    const long long addr = (L & smask) + (((long long)t + ((L >> ls) << top)) << ls);
     buf[li * slot + len + t] = src[addr];
   }
   __syncthreads();
   for (int l = top - 1; l >= 0; --l) {
-    int cnt = 1 << l;
-    int up = 1 << (l + 1);  // size of the finer level
-    for (int e = threadIdx.x; e < nl * cnt; e += blockDim.x) {
-      int li = e / cnt, k = e % cnt;
+    const int cnt = 1 << l;
+    const int up = 1 << (l + 1);  // size of the finer level
+    for (int e = threadIdx.x; e < (nl << l); e += blockDim.x) {
+      const int li = e >> l, k = e & (cnt - 1);
       const real* a = buf + li * slot + up;
-      real am = a[(2 * k - 1 + up) & (up - 1)];
-      real a0 = a[2 * k];
-      real ap = a[(2 * k + 1) & (up - 1)];
+      const real am = a[(2 * k - 1 + up) & (up - 1)];
+      const real a0 = a[2 * k];
+      const real ap = a[(2 * k + 1) & (up - 1)];
       buf[li * slot + cnt + k] = (real)0.25 * am + (real)0.5 * a0 + (real)0.25 * ap;
     }
     __syncthreads();
   }
   for (int tg = 0; tg < J.ntargets; ++tg) {
-    int tl = J.tlev[tg];
-    int tlen = 1 << tl;
+    const int tl = J.tlev[tg];
+    const int tlen = 1 << tl;
     real* dst = reinterpret_cast<real*>(J.dst[tg]);
-    for (int e = threadIdx.x; e < nl * tlen; e += blockDim.x) {
+    for (int e = threadIdx.x; e < (nl << tl); e += blockDim.x) {
       int li, t;
       if (J.axis == 0) {
-        li = e / tlen;
-        t = e % tlen;
+        li = e >> tl;
+        t = e & (tlen - 1);
       } else {
-        li = e % nl;
-        t = e / nl;
+        li = e & (nl - 1);
+        t = e >> logC;
       }
-      long long L = line0 + li;
-      long long low = L % stride, high = L / stride;
-      long long addr = low + stride * (t + (long long)tlen * high);
+      const long long L = line0 + li;
+      const long long addr = (L & smask) + (((long long)t + ((L >> ls) << tl)) << ls);
       dst[addr] = buf[li * slot + tlen + t];
     }
   }

@@ -42,42 +42,43 @@ __device__ __forceinline__ void fft_smem(cplx<real>* buf, int nl, int logn, bool
 
 __device__ __forceinline__ int bitrev(int t, int logn) { return logn == 0 ? 0 : (int)(__brev((unsigned)t) >> (32 - logn)); }
 
-// element (line li of the block, position t) -> array offset, for lines along
-// `axis` of an array with dims; consecutive threads take consecutive lines
-// when axis > 0 so that strided columns are read together.
-__device__ __forceinline__ long long line_addr(long long L, int t, long long stride, int len) {
-  long long low = L % stride, high = L / stride;
-  return low + stride * ((long long)t + (long long)len * high);
+// element (line L, position t) -> array offset for lines along an axis whose
+// stride is 2^ls in an array of power-of-two extents (line length 2^logn).
+__device__ __forceinline__ long long line_addr(long long L, int t, int ls, int logn) {
+  return (L & ((1ll << ls) - 1)) + (((long long)t + ((L >> ls) << logn)) << ls);
 }
 
 __device__ __forceinline__ int sfreq(int i, int N) { return i < (N >> 1) ? i : i - N; }
 
+// Lines per block (C) are a power of two dividing the line count; for lines
+// along axis > 0 consecutive threads take consecutive lines so that strided
+// columns are read together.
 template <typename real>
 __global__ void __launch_bounds__(256) k_fft_pass(int kind, SolveArena<real> a, const FftJob* __restrict__ jobs,
                                                   int njobs) {
   extern __shared__ unsigned char smem_raw[];
-  int b = blockIdx.x;
+  const int b = blockIdx.x;
   const int j = find_job(jobs, njobs);
   const FftJob& J = jobs[j];
   const GridDesc g = a.grids[J.grid];
   const int logn = J.logn;
   const int len = 1 << logn;
   const int C = J.lines_per_block;
+  const int logC = __ffs(C) - 1;
   const int line0 = (b - J.block_begin) * C;
-  const int nl = min(C, J.lines - line0);
-  if (nl <= 0) return;
+  const int nl = C;
   cplx<real>* buf0 = reinterpret_cast<cplx<real>*>(smem_raw);
   cplx<real>* buf1 = buf0 + C * len;
-  long long stride = 1;
-  for (int m = 0; m < J.axis; ++m) stride *= J.dims[m];
+  int ls = 0;
+  for (int m = 0; m < J.axis; ++m) ls += __ffs(J.dims[m]) - 1;
   const size_t S = a.S;
   const bool contiguous = (J.axis == 0);
+  const int total = nl << logn;
 
-  // load
-  for (int e = threadIdx.x; e < nl * len; e += blockDim.x) {
-    int li = contiguous ? e / len : e % nl;
-    int t = contiguous ? e % len : e / nl;
-    long long off = line_addr(line0 + li, t, stride, len);
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int li = contiguous ? (e >> logn) : (e & (nl - 1));
+    const int t = contiguous ? (e & (len - 1)) : (e >> logC);
+    const long long off = line_addr(line0 + li, t, ls, logn);
     cplx<real> v;
     if (kind == FFT_FWD_FIRST) {
       v.x = a.rho[g.offset + off];
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(int kind, SolveArena<real> a, 
     } else {
       v = a.B[(size_t)J.comp * S + g.offset + off];
     }
-    buf0[li * len + bitrev(t, logn)] = v;
+    buf0[(li << logn) + bitrev(t, logn)] = v;
   }
   __syncthreads();
   const bool inverse = (kind == FFT_INV_MID || kind == FFT_INV_LAST);
@@ -96,57 +97,58 @@ __global__ void __launch_bounds__(256) k_fft_pass(int kind, SolveArena<real> a, 
   if (kind == FFT_LAST) {
     const int D = a.dim;
     const real norm = (real)1 / (real)g.size;
+    const int l0 = __ffs(J.dims[0]) - 1;
     for (int m = 0; m < D; ++m) {
-      for (int e = threadIdx.x; e < nl * len; e += blockDim.x) {
-        int li = e / len, t = e % len;
-        long long L = line0 + li;  // combined index of the axes before the last
+      for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int li = e >> logn, t = e & (len - 1);
+        const int L = line0 + li;  // combined index of the axes before the last
         int idx[3];
         idx[D - 1] = t;
         if (D == 2) {
-          idx[0] = (int)L;
+          idx[0] = L;
         } else {
-          idx[0] = (int)(L % J.dims[0]);
-          idx[1] = (int)(L / J.dims[0]);
+          idx[0] = L & (J.dims[0] - 1);
+          idx[1] = L >> l0;
         }
         real k2 = 0, km = 0;
         bool nyq_m = false;
         for (int q = 0; q < D; ++q) {
-          int Nq = J.dims[q];
-          real kq = (real)(g.kfac[q] * (double)sfreq(idx[q], Nq));
+          const int Nq = J.dims[q];
+          const real kq = (real)(g.kfac[q] * (double)sfreq(idx[q], Nq));
           k2 += kq * kq;
           if (q == m) {
             km = kq;
             nyq_m = (idx[q] == (Nq >> 1));
           }
         }
-        cplx<real> r = buf0[li * len + t];
+        const cplx<real> r = buf0[(li << logn) + t];
         cplx<real> out;
         if (k2 == (real)0 || nyq_m) {
           out = {(real)0, (real)0};
         } else {
-          real fac = km / k2 * norm;  // -i k_m rho^/|k|^2 : (a + ib) -> (b, -a)
+          const real fac = km / k2 * norm;  // -i k_m rho^/|k|^2 : (a + ib) -> (b, -a)
           out = {r.y * fac, -r.x * fac};
         }
-        buf1[li * len + bitrev(t, logn)] = out;
+        buf1[(li << logn) + bitrev(t, logn)] = out;
       }
       __syncthreads();
       fft_smem<real>(buf1, nl, logn, true, a.tw, a.log_nmax);
-      for (int e = threadIdx.x; e < nl * len; e += blockDim.x) {
-        int li = contiguous ? e / len : e % nl;
-        int t = contiguous ? e % len : e / nl;
-        long long off = line_addr(line0 + li, t, stride, len);
-        a.B[(size_t)m * S + g.offset + off] = buf1[li * len + t];
+      for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int li = contiguous ? (e >> logn) : (e & (nl - 1));
+        const int t = contiguous ? (e & (len - 1)) : (e >> logC);
+        const long long off = line_addr(line0 + li, t, ls, logn);
+        a.B[(size_t)m * S + g.offset + off] = buf1[(li << logn) + t];
       }
       __syncthreads();
     }
     return;
   }
 
-  for (int e = threadIdx.x; e < nl * len; e += blockDim.x) {
-    int li = contiguous ? e / len : e % nl;
-    int t = contiguous ? e % len : e / nl;
-    long long off = line_addr(line0 + li, t, stride, len);
-    cplx<real> v = buf0[li * len + t];
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int li = contiguous ? (e >> logn) : (e & (nl - 1));
+    const int t = contiguous ? (e & (len - 1)) : (e >> logC);
+    const long long off = line_addr(line0 + li, t, ls, logn);
+    const cplx<real> v = buf0[(li << logn) + t];
     if (kind == FFT_FWD_FIRST || kind == FFT_FWD_MID) {
       a.A[g.offset + off] = v;
     } else if (kind == FFT_INV_MID) {
@@ -178,16 +180,18 @@ int launch_fft_pass(int kind, const SolveArena<real>& a, const FftJob* jobs_dev,
 // transforms it along every axis in place (bit-reversal swap, then the
 // butterfly stages), forms each E^_m and transforms it back.
 template <typename real>
-__device__ void fft_axis_inplace(cplx<real>* buf, const int* dims, const int* logs, int S, int ax, bool inverse,
+__device__ void fft_axis_inplace(cplx<real>* buf, const int* logs, int S, int ax, bool inverse,
                                  const cplx<real>* __restrict__ tw, int log_nmax) {
-  const int len = dims[ax], logn = logs[ax];
-  int stride = 1;
-  for (int m = 0; m < ax; ++m) stride *= dims[m];
+  const int logn = logs[ax];
+  const int len = 1 << logn;
+  int ls = 0;
+  for (int m = 0; m < ax; ++m) ls += logs[m];
+  const int smask = (1 << ls) - 1;
   for (int e = threadIdx.x; e < S; e += blockDim.x) {
-    const int t = (e / stride) & (len - 1);
+    const int t = (e >> ls) & (len - 1);
     const int r = bitrev(t, logn);
     if (r > t) {
-      const int e2 = e + (r - t) * stride;
+      const int e2 = e + ((r - t) << ls);
       cplx<real> x = buf[e];
       buf[e] = buf[e2];
       buf[e2] = x;
@@ -204,14 +208,13 @@ __device__ void fft_axis_inplace(cplx<real>* buf, const int* dims, const int* lo
       const int pos = jj & (half - 1);
       const int grp = jj >> (s - 1);
       const int t0 = grp * 2 * half + pos;
-      const int low = L % stride, high = L / stride;
-      const int i0 = low + stride * (t0 + len * high);
-      const int i1 = i0 + half * stride;
+      const int i0 = (L & smask) + ((t0 + ((L >> ls) << logn)) << ls);
+      const int i1 = i0 + (half << ls);
       cplx<real> w = tw[pos << tshift];
       if (inverse) w.y = -w.y;
-      cplx<real> x0 = buf[i0], x1 = buf[i1];
-      real bx = x1.x * w.x - x1.y * w.y;
-      real by = x1.x * w.y + x1.y * w.x;
+      const cplx<real> x0 = buf[i0], x1 = buf[i1];
+      const real bx = x1.x * w.x - x1.y * w.y;
+      const real by = x1.x * w.y + x1.y * w.x;
       buf[i0] = {x0.x + bx, x0.y + by};
       buf[i1] = {x0.x - bx, x0.y - by};
     }
@@ -220,36 +223,38 @@ __device__ void fft_axis_inplace(cplx<real>* buf, const int* dims, const int* lo
 }
 
 template <typename real>
-__global__ void __launch_bounds__(1024) k_solve_small(SolveArena<real> a) {
+__global__ void __launch_bounds__(1024) k_solve_small(SolveArena<real> a, int max_size) {
   extern __shared__ unsigned char smem_raw[];
   const GridDesc g = a.grids[blockIdx.x];
   const int D = a.dim;
-  int dims[3] = {1, 1, 1}, logs[3] = {0, 0, 0};
-  for (int m = 0; m < D; ++m) {
-    logs[m] = g.l[m];
-    dims[m] = 1 << g.l[m];
-  }
+  int logs[3] = {0, 0, 0};
+  for (int m = 0; m < D; ++m) logs[m] = g.l[m];
   const int S = g.size;
   cplx<real>* A = reinterpret_cast<cplx<real>*>(smem_raw);
-  cplx<real>* B = A + S;
+  cplx<real>* B = A + max_size;
+  cplx<real>* tws = B + max_size;  // twiddle table staged in shared memory
+  const int ntw = 1 << (a.log_nmax - 1);
+  for (int e = threadIdx.x; e < ntw; e += blockDim.x) tws[e] = a.tw[e];
   for (int e = threadIdx.x; e < S; e += blockDim.x) A[e] = {a.rho[g.offset + e], (real)0};
   __syncthreads();
-  for (int ax = 0; ax < D; ++ax) fft_axis_inplace<real>(A, dims, logs, S, ax, false, a.tw, a.log_nmax);
+  for (int ax = 0; ax < D; ++ax) fft_axis_inplace<real>(A, logs, S, ax, false, tws, a.log_nmax);
   const real norm = (real)1 / (real)S;
+  const int n0 = 1 << logs[0], n1 = 1 << logs[1];
   for (int m = 0; m < D; ++m) {
     for (int e = threadIdx.x; e < S; e += blockDim.x) {
       int idx[3];
-      idx[0] = e & (dims[0] - 1);
-      idx[1] = (e >> logs[0]) & (dims[1] - 1);
+      idx[0] = e & (n0 - 1);
+      idx[1] = (e >> logs[0]) & (n1 - 1);
       idx[2] = D == 3 ? (e >> (logs[0] + logs[1])) : 0;
       real k2 = 0, km = 0;
       bool nyq_m = false;
       for (int q = 0; q < D; ++q) {
-        const real kq = (real)(g.kfac[q] * (double)sfreq(idx[q], dims[q]));
+        const int Nq = 1 << logs[q];
+        const real kq = (real)(g.kfac[q] * (double)sfreq(idx[q], Nq));
         k2 += kq * kq;
         if (q == m) {
           km = kq;
-          nyq_m = idx[q] == (dims[q] >> 1);
+          nyq_m = idx[q] == (Nq >> 1);
         }
       }
       const cplx<real> r = A[e];
@@ -261,7 +266,7 @@ __global__ void __launch_bounds__(1024) k_solve_small(SolveArena<real> a) {
       }
     }
     __syncthreads();
-    for (int ax = 0; ax < D; ++ax) fft_axis_inplace<real>(B, dims, logs, S, ax, true, a.tw, a.log_nmax);
+    for (int ax = 0; ax < D; ++ax) fft_axis_inplace<real>(B, logs, S, ax, true, tws, a.log_nmax);
     for (int e = threadIdx.x; e < S; e += blockDim.x) a.E[(size_t)m * a.S + g.offset + e] = B[e].x;
     __syncthreads();
   }
@@ -272,13 +277,13 @@ int launch_solve_small(const SolveArena<real>& a, int ngrids, int max_size, cuda
   if (ngrids == 0) return SG_OK;
   int threads = max_size / 2;
   threads = threads < 64 ? 64 : (threads > 1024 ? 1024 : threads);
-  size_t smem = (size_t)2 * max_size * sizeof(cplx<real>);
+  size_t smem = ((size_t)2 * max_size + ((size_t)1 << (a.log_nmax - 1))) * sizeof(cplx<real>);
   static bool attr_set = false;
   if (!attr_set) {
     SG_CUDA(cudaFuncSetAttribute(k_solve_small<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  k_solve_small<real><<<ngrids, threads, smem, s>>>(a);
+  k_solve_small<real><<<ngrids, threads, smem, s>>>(a, max_size);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
@@ -293,25 +298,22 @@ __global__ void __launch_bounds__(256) k_fft_array(cplx<real>* data, int D, int 
   extern __shared__ unsigned char smem_raw[];
   cplx<real>* buf = reinterpret_cast<cplx<real>*>(smem_raw);
   const int len = 1 << logn;
-  long long lines = 1;
-  for (int m = 0; m < D - 1; ++m) lines *= len;
-  long long line0 = (long long)blockIdx.x * C;
-  int nl = (int)min((long long)C, lines - line0);
-  if (nl <= 0) return;
-  long long stride = 1;
-  for (int m = 0; m < axis; ++m) stride *= len;
+  const long long line0 = (long long)blockIdx.x * C;  // C is a power of two dividing the line count
+  const int nl = C;
+  const int logC = __ffs(C) - 1;
+  const int ls = axis * logn;
   const bool contiguous = axis == 0;
-  for (int e = threadIdx.x; e < nl * len; e += blockDim.x) {
-    int li = contiguous ? e / len : e % nl;
-    int t = contiguous ? e % len : e / nl;
-    buf[li * len + bitrev(t, logn)] = data[line_addr(line0 + li, t, stride, len)];
+  for (int e = threadIdx.x; e < (nl << logn); e += blockDim.x) {
+    const int li = contiguous ? (e >> logn) : (e & (nl - 1));
+    const int t = contiguous ? (e & (len - 1)) : (e >> logC);
+    buf[(li << logn) + bitrev(t, logn)] = data[line_addr(line0 + li, t, ls, logn)];
   }
   __syncthreads();
   fft_smem<real>(buf, nl, logn, inverse != 0, tw, log_nmax);
-  for (int e = threadIdx.x; e < nl * len; e += blockDim.x) {
-    int li = contiguous ? e / len : e % nl;
-    int t = contiguous ? e % len : e / nl;
-    data[line_addr(line0 + li, t, stride, len)] = buf[li * len + t];
+  for (int e = threadIdx.x; e < (nl << logn); e += blockDim.x) {
+    const int li = contiguous ? (e >> logn) : (e & (nl - 1));
+    const int t = contiguous ? (e & (len - 1)) : (e >> logC);
+    data[line_addr(line0 + li, t, ls, logn)] = buf[(li << logn) + t];
   }
 }
 

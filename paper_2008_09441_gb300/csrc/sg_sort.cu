@@ -395,35 +395,54 @@ int launch_tile_keys(const PArrays<real, D>& p, size_t np, int n, const SortFuse
 // Lanes with equal tiles take consecutive slots (leader reserves the group's
 // range); within a tile the order follows warps' arrival, so the step sort is
 // a valid, not a stable, counting sort by tile key.
+// Each warp takes TS_ROUNDS x 32 consecutive particles and reserves the slots
+// of all its rounds before moving any payload, so the reservations' round
+// trips overlap.
+constexpr int TS_ROUNDS = 8;
+
 template <typename real, int D>
 __global__ void __launch_bounds__(256) k_tile_scatter(PArrays<real, D> src, PArrays<real, D> dst,
                                                       const uint32_t* __restrict__ keys, uint32_t* cursor,
                                                       size_t np) {
-  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = i < np;
-  const uint32_t t = valid ? keys[i] : 0xFFFFFFFFu;
-  const unsigned peers = __match_any_sync(0xffffffffu, t);
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  uint32_t base = 0;
-  if (valid && lane == leader) base = atomicAdd(&cursor[t], (uint32_t)__popc(peers));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (!valid) return;
-  const uint32_t pos = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+  const size_t wbase = ((size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * TS_ROUNDS);
+  uint32_t base[TS_ROUNDS], rank[TS_ROUNDS], pos[TS_ROUNDS];
+  int leader[TS_ROUNDS];
 #pragma unroll
-  for (int m = 0; m < D; ++m) {
-    dst.u[m][pos] = src.u[m][i];
-    dst.v[m][pos] = src.v[m][i];
+  for (int r = 0; r < TS_ROUNDS; ++r) {
+    const size_t i = wbase + (size_t)r * 32 + lane;
+    const bool valid = i < np;
+    const uint32_t t = valid ? keys[i] : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xffffffffu, t);
+    leader[r] = __ffs(peers) - 1;
+    rank[r] = (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    base[r] = 0;
+    if (valid && lane == leader[r]) base[r] = atomicAdd(&cursor[t], (uint32_t)__popc(peers));
   }
-  dst.w[pos] = src.w[i];
-  dst.pid[pos] = src.pid[i];
+  // broadcast the reservations only after every round has issued its own
+#pragma unroll
+  for (int r = 0; r < TS_ROUNDS; ++r) pos[r] = __shfl_sync(0xffffffffu, base[r], leader[r]) + rank[r];
+#pragma unroll
+  for (int r = 0; r < TS_ROUNDS; ++r) {
+    const size_t i = wbase + (size_t)r * 32 + lane;
+    if (i >= np) continue;
+    const uint32_t p = pos[r];
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      dst.u[m][p] = src.u[m][i];
+      dst.v[m][p] = src.v[m][i];
+    }
+    dst.w[p] = src.w[i];
+    dst.pid[p] = src.pid[i];
+  }
 }
 
 template <typename real, int D>
 int launch_tile_scatter(const PArrays<real, D>& src, const PArrays<real, D>& dst, const uint32_t* keys,
                         uint32_t* cursor, size_t np, cudaStream_t s) {
   if (np == 0) return SG_OK;
-  k_tile_scatter<real, D><<<(unsigned)((np + 255) / 256), 256, 0, s>>>(src, dst, keys, cursor, np);
+  const size_t per_block = (size_t)256 * TS_ROUNDS;
+  k_tile_scatter<real, D><<<(unsigned)((np + per_block - 1) / per_block), 256, 0, s>>>(src, dst, keys, cursor, np);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }

@@ -308,3 +308,84 @@ def _flat_to_axes(flat, levels):
     d = len(levels)
     out = flat.reshape((flat.shape[0],) + shape_rev)
     return np.ascontiguousarray(np.transpose(out, (0,) + tuple(range(d, 0, -1))))
+
+
+# ------------------------------------------------------------------ serving
+class Server:
+    """Independent runs admitted by device-memory footprint and advanced
+    together tick by tick (sg_serve_*)."""
+
+    def __init__(self, hbm_budget_bytes, max_slots):
+        self.h = C.c_void_p()
+        check(lib().sg_serve_create(int(hbm_budget_bytes), int(max_slots), C.byref(self.h)), "sg_serve_create")
+        self.meta = {}
+
+    def submit(self, L_box, n, u, v, w, dt, nsteps, *, tau=1, qm=-1.0, precision="fp32", B=(0.0, 0.0, 0.0),
+               eext_lin=(0.0, 0.0, 0.0), sort_every=0):
+        d = len(L_box)
+        prec = L.SG_FP32 if precision in ("fp32", L.SG_FP32) else L.SG_FP64
+        dt_np = _DT[prec]
+        ucols = _columns(u, d, dt_np)
+        vcols = _columns(v, d, dt_np)
+        wcol = _columns([w], 1, dt_np)[0]
+        req = L.sg_request()
+        req.domain.dim = d
+        for m in range(3):
+            req.domain.L[m] = float(L_box[m]) if m < d else 1.0
+        req.level_n = n
+        req.dim = d
+        req.particles.n = int(ucols[0].shape[0])
+        req.particles.on_device = 0
+        for m in range(d):
+            req.particles.u[m] = _ptr(ucols[m]).value
+            req.particles.v[m] = _ptr(vcols[m]).value
+        req.particles.w = _ptr(wcol).value
+        req.params = make_params(prec, tau, dt, qm, B, eext_lin, 0.01, 5.0, L.SG_TAU_CONST_PAPER, sort_every, None)
+        req.nsteps = int(nsteps)
+        t = C.c_ulonglong()
+        check(lib().sg_serve_submit(self.h, C.byref(req), C.byref(t)), "sg_serve_submit")
+        self.meta[t.value] = (d, int(ucols[0].shape[0]), dt_np)
+        return t.value
+
+    def tick(self):
+        a = C.c_int()
+        check(lib().sg_serve_tick(self.h, C.byref(a)), "sg_serve_tick")
+        return a.value
+
+    def poll(self, ticket):
+        st = C.c_int()
+        dg = L.sg_diag()
+        check(lib().sg_serve_poll(self.h, ticket, C.byref(st), C.byref(dg)), "sg_serve_poll")
+        return st.value, dg.as_dict()
+
+    def result(self, ticket):
+        d, N, dt_np = self.meta[ticket]
+        u = np.empty((d, N), dtype=dt_np)
+        v = np.empty((d, N), dtype=dt_np)
+        w = np.empty(N, dtype=dt_np)
+        o = L.sg_particles_out()
+        o.n = N
+        o.on_device = 0
+        for m in range(d):
+            o.u[m] = u[m].ctypes.data
+            o.v[m] = v[m].ctypes.data
+        o.w = w.ctypes.data
+        check(lib().sg_serve_result(self.h, ticket, C.byref(o)), "sg_serve_result")
+        return u.T.copy(), v.T.copy(), w
+
+    def stats(self):
+        p50, p99, pst = C.c_double(), C.c_double(), C.c_double()
+        n = C.c_ulonglong()
+        check(lib().sg_serve_stats(self.h, C.byref(p50), C.byref(p99), C.byref(pst), C.byref(n)), "sg_serve_stats")
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "particle_steps_per_s": pst.value, "steps": n.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sg_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
