@@ -27,7 +27,10 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
   const int y = row & (N - 1);
   const int z = (D == 3) ? (row >> n) : 0;
   __shared__ int s_start[18];  // level lists staged in shared memory (dynamic indexing)
-  if (threadIdx.x < 18) s_start[threadIdx.x] = ll.start[threadIdx.x];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < 18; ++i) s_start[i] = ll.start[i];  // constant indices: no local copy
+  }
   __syncthreads();
 
   // every (level, x index) of the levels Horner reads
