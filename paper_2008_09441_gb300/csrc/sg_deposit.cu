@@ -15,47 +15,31 @@ namespace sg {
 
 // ---------------------------------------------------------------- deposit
 //
-// Each block takes DEP_CHUNK consecutive particles (consecutive in the
-// cell-key order after a sort, so they occupy a compact Morton block).  It
-// sizes a window of regular nodes around them (periodic displacement from
-// the chunk's middle particle), accumulates the CIC weights in shared memory
-// and adds the non-zero window nodes to the global grid.  Particles whose
-// corners fall outside a window clamped to the shared-memory capacity add
-// directly to the global grid.
+// Each block takes DEP_CHUNK consecutive particles (consecutive in tile-key
+// order after a sort, so they occupy a compact block of cells).  All of them
+// are loaded first (16-byte vector loads); the chunk's middle particle fixes
+// the anchor cell and the periodic bounding box of the chunk's cells sizes a
+// window of regular nodes in shared memory.  Charges accumulate there in
+// 64-bit fixed point: integer adds are native shared-memory atomics and are
+// associative, so the window's sums do not depend on the order of the adds.
+// The scale is 2^62 / (sum of the chunk's |q_p| / V), rounded down to a power
+// of two, so no node can overflow; a contribution is rounded once, to
+// 2^-62 of the chunk's charge.  Non-zero window nodes are then added to the
+// global grid in the run's precision.  Corners outside a window clamped to
+// the shared-memory capacity add directly to the global grid.
 template <typename real, int D>
 __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, size_t np, int n,
-                                                         real inv_cell_vol, real* __restrict__ rho,
-                                                         int win_cap) {
+                                                         real inv_cell_vol, real* __restrict__ rho, int side) {
   extern __shared__ unsigned char smem_raw[];
-  real* win = reinterpret_cast<real*>(smem_raw);
-  __shared__ int s_anchor[D], s_min[D], s_max[D], s_org[D], s_ext[D];
-  __shared__ int s_nwin;
+  unsigned long long* win = reinterpret_cast<unsigned long long*>(smem_raw);
+  __shared__ int s_anchor[D], s_min[D], s_max[D];
+  __shared__ double s_wq[DEP_THREADS / 32];
   const int N = 1 << n;
   const int mask = N - 1;
   const size_t chunk = (size_t)blockIdx.x * DEP_CHUNK;
-  if (threadIdx.x == 0) {
-    size_t mid = chunk + DEP_CHUNK / 2;
-    if (mid >= np) mid = np - 1;
-#pragma unroll
-    for (int m = 0; m < D; ++m) {
-      s_anchor[m] = cell_of(p.u[m][mid], n, N);
-      s_min[m] = INT_MAX;
-      s_max[m] = INT_MIN;
-    }
-  }
-  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  int c[DEP_ITEMS][D];
-  real f[DEP_ITEMS][D];
-  real q[DEP_ITEMS];
-  int dmin[D], dmax[D];
-#pragma unroll
-  for (int m = 0; m < D; ++m) {
-    dmin[m] = INT_MAX;
-    dmax[m] = INT_MIN;
-  }
-  // Items: DEP_ITEMS / 4 vectors of four consecutive particles per thread
-  // (16-byte loads); the ragged end of the last chunk is read element-wise.
+  // ---- load the chunk: DEP_ITEMS / 4 vectors of four consecutive particles
   real ub[DEP_ITEMS][D], wb[DEP_ITEMS];
 #pragma unroll
   for (int j = 0; j < DEP_ITEMS / 4; ++j) {
@@ -80,31 +64,68 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
       }
     }
   }
+  // ---- anchor: the cell of the chunk's middle (or last) particle
+  {
+    size_t mid = chunk + DEP_CHUNK / 2;
+    if (mid >= np) mid = np - 1;
+    const int rel = (int)(mid - chunk);
+    const int holder = (rel & (DEP_THREADS * 4 - 1)) >> 2;
+    if ((int)threadIdx.x == holder) {
+      const int item = 4 * (rel / (DEP_THREADS * 4)) + (rel & 3);
+#pragma unroll
+      for (int it = 0; it < DEP_ITEMS; ++it)
+        if (it == item) {
+#pragma unroll
+          for (int m = 0; m < D; ++m) s_anchor[m] = cell_of(ub[it][m], n, N);
+        }
+    }
+    if (threadIdx.x < D) {
+      s_min[threadIdx.x] = INT_MAX;
+      s_max[threadIdx.x] = INT_MIN;
+    }
+  }
+  __syncthreads();
+
+  int c[DEP_ITEMS][D];
+  real f[DEP_ITEMS][D];
+  real q[DEP_ITEMS];
+  int dmin[D], dmax[D];
+  int anchor[D];
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    dmin[m] = INT_MAX;
+    dmax[m] = INT_MIN;
+    anchor[m] = s_anchor[m];
+  }
+  double qabs = 0.0;
 #pragma unroll
   for (int it = 0; it < DEP_ITEMS; ++it) {
     const size_t i = chunk + ((size_t)(it >> 2) * DEP_THREADS + threadIdx.x) * 4 + (it & 3);
     if (i < np) {
 #pragma unroll
       for (int m = 0; m < D; ++m) {
-        real s = ub[it][m] * (real)N;
+        const real s = ub[it][m] * (real)N;
         int ci = (int)s;
         ci = ci < 0 ? 0 : (ci > mask ? mask : ci);
         c[it][m] = ci;
         f[it][m] = s - (real)ci;
-        int dd = ((ci - s_anchor[m] + (N >> 1)) & mask) - (N >> 1);
+        const int dd = ((ci - anchor[m] + (N >> 1)) & mask) - (N >> 1);
         dmin[m] = min(dmin[m], dd);
         dmax[m] = max(dmax[m], dd);
       }
       q[it] = wb[it] * inv_cell_vol;
+      qabs += fabs((double)q[it]);
     } else {
       q[it] = (real)0;
 #pragma unroll
       for (int m = 0; m < D; ++m) {
-        c[it][m] = s_anchor[m];
+        c[it][m] = anchor[m];
         f[it][m] = (real)0;
       }
     }
   }
+  qabs = warp_sum(qabs);
+  if (lane == 0) s_wq[warp] = qabs;
 #pragma unroll
   for (int m = 0; m < D; ++m) {
 #pragma unroll
@@ -112,52 +133,40 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
       dmin[m] = min(dmin[m], __shfl_xor_sync(0xffffffffu, dmin[m], o));
       dmax[m] = max(dmax[m], __shfl_xor_sync(0xffffffffu, dmax[m], o));
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
       atomicMin(&s_min[m], dmin[m]);
       atomicMax(&s_max[m], dmax[m]);
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int side = 1;
-    while (true) {  // largest side with side^D <= win_cap
-      long long nxt = 1;
-      for (int m = 0; m < D; ++m) nxt *= (side + 1);
-      if (nxt > win_cap) break;
-      ++side;
-    }
-    long long nw = 1;
-    for (int m = 0; m < D; ++m) {
-      int lo = s_min[m], ext;
-      if (lo == INT_MAX) {  // empty chunk (cannot happen for launched blocks)
-        lo = 0;
-        ext = 1;
-      } else {
-        ext = s_max[m] - lo + 2;  // +1 node for the upper corner
-      }
-      if (ext >= N) {  // the window spans the whole axis
-        ext = N;
-        lo = -(N >> 1);
-      }
-      if (ext > side) {  // clamp around the anchor; outliers add to global
-        ext = side;
-        lo = -(side >> 1);
-      }
-      s_org[m] = (s_anchor[m] + lo) & mask;
-      s_ext[m] = ext;
-      nw *= ext;
-    }
-    s_nwin = (int)nw;
-  }
-  __syncthreads();
-  const int nwin = s_nwin;
-  for (int i = threadIdx.x; i < nwin; i += DEP_THREADS) win[i] = (real)0;
+
+  // ---- window and fixed-point scale (every thread derives the same values)
   int org[D], ext[D];
+  int nwin = 1;
 #pragma unroll
   for (int m = 0; m < D; ++m) {
-    org[m] = s_org[m];
-    ext[m] = s_ext[m];
+    int lo = s_min[m];
+    int e = s_max[m] - lo + 2;  // +1 node for the upper corner
+    if (e >= N) {               // the window spans the whole axis
+      e = N;
+      lo = -(N >> 1);
+    }
+    if (e > side) {  // clamp around the anchor; outliers add to global
+      e = side;
+      lo = -(side >> 1);
+    }
+    org[m] = (anchor[m] + lo) & mask;
+    ext[m] = e;
+    nwin *= e;
   }
+  double qsum = 0.0;
+#pragma unroll
+  for (int w = 0; w < DEP_THREADS / 32; ++w) qsum += s_wq[w];
+  int ex = 0;
+  frexp(qsum, &ex);  // qsum < 2^ex
+  const real scale = qsum > 0.0 ? (real)ldexp(1.0, 62 - ex) : (real)1;
+  const real inv_scale = qsum > 0.0 ? (real)ldexp(1.0, ex - 62) : (real)1;
+  for (int i = threadIdx.x; i < nwin; i += DEP_THREADS) win[i] = 0ull;
   __syncthreads();
 
 #pragma unroll
@@ -170,35 +179,37 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
       bool inside = true;
 #pragma unroll
       for (int m = 0; m < D; ++m) {
-        int b = (corner >> m) & 1;
+        const int b = (corner >> m) & 1;
         wgt *= b ? f[it][m] : ((real)1 - f[it][m]);
-        int g = (c[it][m] + b) & mask;
-        int l = (g - org[m]) & mask;
+        const int g = (c[it][m] + b) & mask;
+        const int l = (g - org[m]) & mask;
         inside &= l < ext[m];
         loc += l * lstride;
         lstride *= ext[m];
         glob += g * gstride;
         gstride *= N;
       }
-      if (inside)
-        atomicAdd(&win[loc], wgt);
-      else
+      if (inside) {
+        const long long v = sizeof(real) == 4 ? __float2ll_rn((float)(wgt * scale)) : __double2ll_rn((double)(wgt * scale));
+        atomicAdd(&win[loc], (unsigned long long)v);
+      } else {
         atomicAdd(&rho[glob], wgt);
+      }
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nwin; i += DEP_THREADS) {
-    real val = win[i];
-    if (val != (real)0) {
+    const long long sv = (long long)win[i];
+    if (sv != 0) {
       int rem = i, glob = 0, gstride = 1;
 #pragma unroll
       for (int m = 0; m < D; ++m) {
-        int l = rem % ext[m];
+        const int l = rem % ext[m];
         rem /= ext[m];
         glob += ((org[m] + l) & mask) * gstride;
         gstride *= N;
       }
-      atomicAdd(&rho[glob], val);
+      atomicAdd(&rho[glob], (real)sv * inv_scale);
     }
   }
 }
@@ -208,13 +219,22 @@ int launch_deposit(const PArrays<real, D>& p, size_t np, int n, real inv_cell_vo
                    cudaStream_t s) {
   if (np == 0) return SG_OK;
   unsigned blocks = (unsigned)((np + DEP_CHUNK - 1) / DEP_CHUNK);
-  size_t smem = (size_t)win_cap_nodes * sizeof(real);
+  int side = 1;  // largest side with side^D <= capacity
+  while (true) {
+    long long nxt = 1;
+    for (int m = 0; m < D; ++m) nxt *= (side + 1);
+    if (nxt > win_cap_nodes) break;
+    ++side;
+  }
+  long long nodes = 1;
+  for (int m = 0; m < D; ++m) nodes *= side;
+  size_t smem = (size_t)nodes * sizeof(unsigned long long);
   static bool attr_set = false;
   if (smem > 48 * 1024 && !attr_set) {
     SG_CUDA(cudaFuncSetAttribute(k_deposit<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  k_deposit<real, D><<<blocks, DEP_THREADS, smem, s>>>(p, np, n, inv_cell_vol, rho, win_cap_nodes);
+  k_deposit<real, D><<<blocks, DEP_THREADS, smem, s>>>(p, np, n, inv_cell_vol, rho, side);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }

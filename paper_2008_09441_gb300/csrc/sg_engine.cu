@@ -130,6 +130,8 @@ class Engine final : public EngineBase {
     // Initial state: sort, fields at t = 0, backward half kick.
     SG_TRY(enqueue_sort());
     SG_TRY(enqueue_fields());
+    SG_TRY(tune_solve());
+    SG_TRY(enqueue_combine());
     SG_TRY(launch_finalize_step(fe_partials_, nrows_, nullptr, 0, fe_scale(), dd_, stream_));
     SG_TRY(enqueue_push(-0.5 * cfg_.dt, false, nullptr));
     SG_CUDA(cudaStreamSynchronize(stream_));
@@ -296,7 +298,9 @@ class Engine final : public EngineBase {
     if (tau == tau_) return SG_OK;
     SG_CUDA(cudaStreamSynchronize(stream_));
     SG_TRY(build_grid_set(tau));
-    SG_TRY(enqueue_restrict_solve_combine());
+    SG_TRY(enqueue_restrict());
+    SG_TRY(tune_solve());
+    SG_TRY(enqueue_combine());
     SG_TRY(launch_finalize_step(fe_partials_, nrows_, nullptr, 0, fe_scale(), dd_, stream_));
     return SG_OK;
   }
@@ -603,6 +607,7 @@ class Engine final : public EngineBase {
   // ------------------------------------------------------------ grid set
   int build_grid_set(int tau) {
     invalidate_graphs();
+    solve_mode_ = -1;
     tau_ = tau;
     grids_ = combination_grids(D, n_, tau);
     ngrids_ = (int)grids_.size();
@@ -870,6 +875,7 @@ class Engine final : public EngineBase {
     return SG_OK;
   }
   int sort_finish() {
+    SG_TRY(launch_tile_hist(keys_, np_, tile_count_, stream_));
     SG_TRY(exclusive_scan_u32(tile_count_, cursor_, ntiles_, scan_sums_, stream_));
     SG_TRY(launch_tile_scatter<real, D>(P_[cur_], P_[cur_ ^ 1], keys_, cursor_, np_, stream_));
     cur_ ^= 1;
@@ -904,8 +910,45 @@ class Engine final : public EngineBase {
     a.dim = D;
     int maxsize = 0;
     for (auto& g : gdesc_) maxsize = std::max(maxsize, g.size);
-    if (maxsize <= small_solve_max<real>()) return launch_solve_small<real>(a, ngrids_, maxsize, stream_);
+    const bool small_ok = maxsize <= small_solve_max<real>();
+    if (small_ok && (solve_mode_ == 1 || (solve_mode_ == -1 && force_mode_ < 0)))
+      return launch_solve_small<real>(a, ngrids_, maxsize, stream_);
     for (auto& P : fpasses_) SG_TRY(launch_fft_pass<real>(P.kind, a, P.dev, P.njobs, P.nblocks, P.smem, stream_));
+    return SG_OK;
+  }
+
+  // Autotuning of the solve: time the one-block-per-grid kernel against the
+  // per-axis passes on this grid set (both read the component densities and
+  // write the component fields, so repeating them is harmless) and keep the
+  // faster.  Runs at init and whenever the grid set changes.
+  int tune_solve() {
+    int maxsize = 0;
+    for (auto& g : gdesc_) maxsize = std::max(maxsize, g.size);
+    if (maxsize > small_solve_max<real>()) {
+      solve_mode_ = 0;
+      return SG_OK;
+    }
+    cudaEvent_t e0, e1;
+    SG_CUDA(cudaEventCreate(&e0));
+    SG_CUDA(cudaEventCreate(&e1));
+    float best[2] = {1e30f, 1e30f};
+    for (int rep = 0; rep < 3; ++rep) {
+      for (int mode = 0; mode < 2; ++mode) {
+        solve_mode_ = mode;
+        SG_CUDA(cudaEventRecord(e0, stream_));
+        SG_TRY(enqueue_solve());
+        SG_CUDA(cudaEventRecord(e1, stream_));
+        SG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        SG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        best[mode] = std::min(best[mode], ms);
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    solve_mode_ = best[1] < best[0] ? 1 : 0;
+    solve_ms_[0] = best[0];
+    solve_ms_[1] = best[1];
     return SG_OK;
   }
 
@@ -1050,6 +1093,9 @@ class Engine final : public EngineBase {
   std::vector<GridDesc> gdesc_;
   int ngrids_ = 0, lmin_ = 0;
   LevelLists levels_{};
+  int solve_mode_ = -1;  // -1 untuned, 0 per-axis passes, 1 one block per grid
+  int force_mode_ = -1;
+  float solve_ms_[2] = {0, 0};
   GridDesc* grids_dev_ = nullptr;
   double* charges_dev_ = nullptr;
   real* rho_arena_ = nullptr;

@@ -194,6 +194,8 @@ int push_blocks(size_t np);
 template <typename real, int D>
 int launch_tile_keys(const PArrays<real, D>& p, size_t np, int n, const SortFuse& sf, unsigned* status,
                      cudaStream_t s);
+// tile_count[key] += 1 for every key (counts zeroed by the caller).
+int launch_tile_hist(const uint32_t* keys, size_t np, uint32_t* tile_count, cudaStream_t s);
 // Scatter every particle to its tile's next free slot (cursor = exclusive
 // scan of the tile counts): one pass, reads key + payload, writes payload.
 template <typename real, int D>

@@ -167,28 +167,12 @@ __global__ void __launch_bounds__(256) k_push(PArrays<real, D> p, size_t np, int
         cks += (unsigned long long)full + 1ull;
       }
     }
-    if (sf.keys) {
-      // the four particles usually share a tile: count them together, then
-      // combine equal tiles across the warp
-      *reinterpret_cast<uint4*>(sf.keys + i0) = make_uint4(tiles[0], tiles[1], tiles[2], tiles[3]);
-      uint32_t c0 = 0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (tiles[j] == tiles[0])
-          ++c0;
-        else
-          atomicAdd(&sf.tile_count[tiles[j]], 1u);
-      }
-      const unsigned act = __activemask();
-      const unsigned peers = __match_any_sync(act, tiles[0]);
-      const uint32_t sum = __reduce_add_sync(peers, c0);
-      if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&sf.tile_count[tiles[0]], sum);
-    }
 #pragma unroll
     for (int m = 0; m < D; ++m) {
       if (pp.drift) st4(p.u[m] + i0, U[m]);
       st4(p.v[m] + i0, Vv[m]);
     }
+    if (sf.keys) *reinterpret_cast<uint4*>(sf.keys + i0) = make_uint4(tiles[0], tiles[1], tiles[2], tiles[3]);
   }
   // ragged tail (np not a multiple of 4): block 0 takes it particle by particle
   if (blockIdx.x == 0) {
@@ -212,7 +196,6 @@ __global__ void __launch_bounds__(256) k_push(PArrays<real, D> p, size_t np, int
         uint32_t t = tile_key<real, D>(u, n, sf.tile_shift, &full);
         sf.keys[i] = t;
         cks += (unsigned long long)full + 1ull;
-        atomicAdd(&sf.tile_count[t], 1u);
       }
     }
   }

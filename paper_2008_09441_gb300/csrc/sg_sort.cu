@@ -354,15 +354,15 @@ int launch_unpermute(const PArrays<real, D>& src, const PArrays<real, D>& dst, s
 }
 
 // ---------------------------------------------------------------- tile counting sort
+// Tile keys of the current positions (the push emits them on sort steps;
+// this kernel serves init and checkpoint load) and sum (cell key + 1).
 template <typename real, int D>
 __global__ void __launch_bounds__(256) k_tile_keys(PArrays<real, D> p, size_t np, int n, SortFuse sf,
                                                    unsigned* status) {
   const int N = 1 << n;
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = i < np;
-  uint32_t t = 0;
   unsigned long long part = 0;
-  if (valid) {
+  if (i < np) {
     int c[D];
     bool bad = false;
 #pragma unroll
@@ -373,12 +373,9 @@ __global__ void __launch_bounds__(256) k_tile_keys(PArrays<real, D> p, size_t np
     }
     if (bad) atomicOr(status, ST_KEY_RANGE);
     uint32_t k = morton_key<D>(c, n);
-    t = k >> (D * sf.tile_shift);
-    sf.keys[i] = t;
+    sf.keys[i] = k >> (D * sf.tile_shift);
     part = (unsigned long long)k + 1ull;
   }
-  const unsigned peers = __match_any_sync(0xffffffffu, valid ? t : 0xFFFFFFFFu);
-  if (valid && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&sf.tile_count[t], (uint32_t)__popc(peers));
   part = warp_sum(part);
   if ((threadIdx.x & 31) == 0 && part && sf.checksum) atomicAdd(sf.checksum, part);
 }
@@ -392,48 +389,102 @@ int launch_tile_keys(const PArrays<real, D>& p, size_t np, int n, const SortFuse
   return SG_OK;
 }
 
-// Lanes with equal tiles take consecutive slots (leader reserves the group's
-// range); within a tile the order follows warps' arrival, so the step sort is
-// a valid, not a stable, counting sort by tile key.
-// Each warp takes TS_ROUNDS x 32 consecutive particles and reserves the slots
-// of all its rounds before moving any payload, so the reservations' round
-// trips overlap.
+// Per-tile counts of the keys: each warp reads TS_ROUNDS x 32 keys (vectors
+// of four), combines equal keys within the warp and adds the group counts.
 constexpr int TS_ROUNDS = 8;
 
+__global__ void __launch_bounds__(256) k_tile_hist(const uint32_t* __restrict__ keys, size_t np,
+                                                   uint32_t* tile_count) {
+  const int lane = threadIdx.x & 31;
+  const size_t wbase = ((size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (128 * (TS_ROUNDS / 4));
+#pragma unroll
+  for (int r = 0; r < TS_ROUNDS / 4; ++r) {
+    const size_t i0 = wbase + ((size_t)r * 32 + lane) * 4;
+    uint32_t t[4];
+    if (i0 + 4 <= np) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(keys + i0));
+      t[0] = v.x;
+      t[1] = v.y;
+      t[2] = v.z;
+      t[3] = v.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) t[k] = i0 + k < np ? keys[i0 + k] : 0xFFFFFFFFu;
+    }
+    uint32_t c0 = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (t[k] == t[0])
+        ++c0;
+      else if (t[k] != 0xFFFFFFFFu)
+        atomicAdd(&tile_count[t[k]], 1u);
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, t[0]);
+    const uint32_t sum = __reduce_add_sync(peers, c0);
+    if (t[0] != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&tile_count[t[0]], sum);
+  }
+}
+
+int launch_tile_hist(const uint32_t* keys, size_t np, uint32_t* tile_count, cudaStream_t s) {
+  if (np == 0) return SG_OK;
+  const size_t per_block = (size_t)256 * TS_ROUNDS;  // 8 warps x (TS_ROUNDS / 4) rounds x 128 keys
+  k_tile_hist<<<(unsigned)((np + per_block - 1) / per_block), 256, 0, s>>>(keys, np, tile_count);
+  SG_CHECK_LAUNCH();
+  return SG_OK;
+}
+
+// Scatter every particle to its tile's next free slot.  Each warp takes
+// TS_ROUNDS x 32 consecutive particles: it reserves the slots of all rounds
+// (lanes with equal tiles share one reservation) and loads all payloads
+// before storing any, so the round trips overlap.  Within a tile the order
+// follows the warps' arrival: the step sort is a valid, not a stable,
+// counting sort by tile key.
 template <typename real, int D>
 __global__ void __launch_bounds__(256) k_tile_scatter(PArrays<real, D> src, PArrays<real, D> dst,
                                                       const uint32_t* __restrict__ keys, uint32_t* cursor,
                                                       size_t np) {
+  constexpr int R = 4;
   const int lane = threadIdx.x & 31;
-  const size_t wbase = ((size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * TS_ROUNDS);
-  uint32_t base[TS_ROUNDS], rank[TS_ROUNDS], pos[TS_ROUNDS];
-  int leader[TS_ROUNDS];
+  const size_t wbase = ((size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * R);
+  uint32_t base[R], rank[R];
+  int leader[R];
 #pragma unroll
-  for (int r = 0; r < TS_ROUNDS; ++r) {
+  for (int r = 0; r < R; ++r) {
     const size_t i = wbase + (size_t)r * 32 + lane;
     const bool valid = i < np;
-    const uint32_t t = valid ? keys[i] : 0xFFFFFFFFu;
+    const uint32_t t = valid ? __ldg(keys + i) : 0xFFFFFFFFu;
     const unsigned peers = __match_any_sync(0xffffffffu, t);
     leader[r] = __ffs(peers) - 1;
     rank[r] = (uint32_t)__popc(peers & ((1u << lane) - 1u));
     base[r] = 0;
     if (valid && lane == leader[r]) base[r] = atomicAdd(&cursor[t], (uint32_t)__popc(peers));
   }
-  // broadcast the reservations only after every round has issued its own
+  real pu[R][D], pv[R][D], pw[R];
+  uint32_t pid[R];
 #pragma unroll
-  for (int r = 0; r < TS_ROUNDS; ++r) pos[r] = __shfl_sync(0xffffffffu, base[r], leader[r]) + rank[r];
-#pragma unroll
-  for (int r = 0; r < TS_ROUNDS; ++r) {
+  for (int r = 0; r < R; ++r) {
     const size_t i = wbase + (size_t)r * 32 + lane;
-    if (i >= np) continue;
-    const uint32_t p = pos[r];
+    const bool valid = i < np;
 #pragma unroll
     for (int m = 0; m < D; ++m) {
-      dst.u[m][p] = src.u[m][i];
-      dst.v[m][p] = src.v[m][i];
+      pu[r][m] = valid ? __ldg(src.u[m] + i) : (real)0;
+      pv[r][m] = valid ? __ldg(src.v[m] + i) : (real)0;
     }
-    dst.w[p] = src.w[i];
-    dst.pid[p] = src.pid[i];
+    pw[r] = valid ? __ldg(src.w + i) : (real)0;
+    pid[r] = valid ? __ldg(src.pid + i) : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t pos = __shfl_sync(0xffffffffu, base[r], leader[r]) + rank[r];
+    const size_t i = wbase + (size_t)r * 32 + lane;
+    if (i >= np) continue;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      dst.u[m][pos] = pu[r][m];
+      dst.v[m][pos] = pv[r][m];
+    }
+    dst.w[pos] = pw[r];
+    dst.pid[pos] = pid[r];
   }
 }
 
@@ -441,7 +492,7 @@ template <typename real, int D>
 int launch_tile_scatter(const PArrays<real, D>& src, const PArrays<real, D>& dst, const uint32_t* keys,
                         uint32_t* cursor, size_t np, cudaStream_t s) {
   if (np == 0) return SG_OK;
-  const size_t per_block = (size_t)256 * TS_ROUNDS;
+  const size_t per_block = (size_t)256 * 4;
   k_tile_scatter<real, D><<<(unsigned)((np + per_block - 1) / per_block), 256, 0, s>>>(src, dst, keys, cursor, np);
   SG_CHECK_LAUNCH();
   return SG_OK;
