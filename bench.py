@@ -301,7 +301,7 @@ def main():
                 "traffic": (tr["dram_bytes_per_launch"] * (np_ / tr["particles"]) if tr else None),
                 "per_kernel": {k: {"achieved_gbs": rl[k]["achieved"], "frac": rl[k]["frac"],
                                    "ms": rl[k]["ms"], "alg_bytes": rl[k]["alg_bytes"]} for k in rl},
-                "stage_ms": stage_avg}
+                "stage_ms": stage_avg, "autotune": run.tuning()}
 
     # ---- end to end through the public API with host buffers
     e2e = None

@@ -198,7 +198,9 @@ int sg_pic_kernel_launches(sg_pic* h, unsigned long long* count);
  * (0 gather-push, 1 sort, 2 deposit, 3 restrict, 4 solve, 5 combine) in
  * milliseconds, summed over that call's steps.  Enabled with
  * sg_pic_set_profiling(h, 1), which replaces graph replay by direct launches
- * with events between the stages while on. */
+ * with events between the stages while on.  With cap >= 9, entries 6..8
+ * report the init-time autotuner: the solve variant in use (0 per-axis
+ * passes, 1 one block per grid) and the two timings (ms) it compared. */
 int sg_pic_set_profiling(sg_pic* h, int on);
 int sg_pic_stage_times(sg_pic* h, double* ms, int cap);
 
@@ -239,7 +241,12 @@ typedef struct {
 #define SG_REQ_DONE 2
 #define SG_REQ_FAILED 3
 
+#define SG_SERVE_BATCHED 0 /* one CUDA graph per tick, every resident run a parallel branch */
+#define SG_SERVE_PLAIN 1   /* runs stepped in turn, direct launches, one solve launch per grid */
+
 int sg_serve_create(size_t hbm_budget_bytes, int max_slots, sg_server** out);
+/* Select how ticks advance the resident runs (default SG_SERVE_BATCHED). */
+int sg_serve_set_mode(sg_server* s, int mode);
 /* Queue a request (copies its particle arrays); returns a ticket. */
 int sg_serve_submit(sg_server* s, const sg_request* req, unsigned long long* ticket);
 /* Admit what fits, then advance every resident run by one step. *active

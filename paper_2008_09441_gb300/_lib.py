@@ -28,6 +28,7 @@ SG_TAU_ADAPTIVE = -1
 SG_TAU_CONST_PAPER = 0
 SG_TAU_CONST_EMPIRICAL = 1
 SG_REQ_QUEUED, SG_REQ_RUNNING, SG_REQ_DONE, SG_REQ_FAILED = 0, 1, 2, 3
+SG_SERVE_BATCHED, SG_SERVE_PLAIN = 0, 1
 
 
 class sg_domain(C.Structure):
@@ -95,6 +96,7 @@ SIGNATURES = {
     "sg_version": (C.c_char_p, []),
     "sg_cell_sort": (C.c_int, [C.c_int, C.c_int, C.c_int, _SZ, C.POINTER(_P), _P, _P, _P, _P]),
     "sg_serve_create": (C.c_int, [_SZ, C.c_int, C.POINTER(_P)]),
+    "sg_serve_set_mode": (C.c_int, [_P, C.c_int]),
     "sg_serve_submit": (C.c_int, [_P, C.POINTER(sg_request), C.POINTER(C.c_ulonglong)]),
     "sg_serve_tick": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "sg_serve_poll": (C.c_int, [_P, C.c_ulonglong, C.POINTER(C.c_int), C.POINTER(sg_diag)]),

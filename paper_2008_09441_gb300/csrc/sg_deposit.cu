@@ -13,25 +13,45 @@
 
 namespace sg {
 
+// Shared-memory accumulator of the deposit window.  FP32 path: 32-bit fixed
+// point (native integer shared atomics; a contribution is rounded once, to
+// 2^-30 of the chunk's total |charge|, and integer sums are order-independent).
+// FP64 path: plain double.
+template <typename real>
+struct WinAcc;
+template <>
+struct WinAcc<float> {
+  using T = int;
+  static constexpr int bits = 30;
+  static __device__ __forceinline__ T quantize(float x) { return __float2int_rn(x); }
+  static __device__ __forceinline__ float value(T s, float inv_scale) { return (float)s * inv_scale; }
+};
+template <>
+struct WinAcc<double> {
+  using T = double;
+  static constexpr int bits = 0;
+  static __device__ __forceinline__ T quantize(double x) { return x; }
+  static __device__ __forceinline__ double value(T s, double) { return s; }
+};
+
 // ---------------------------------------------------------------- deposit
 //
 // Each block takes DEP_CHUNK consecutive particles (consecutive in tile-key
 // order after a sort, so they occupy a compact block of cells).  All of them
 // are loaded first (16-byte vector loads); the chunk's middle particle fixes
 // the anchor cell and the periodic bounding box of the chunk's cells sizes a
-// window of regular nodes in shared memory.  Charges accumulate there in
-// 64-bit fixed point: integer adds are native shared-memory atomics and are
-// associative, so the window's sums do not depend on the order of the adds.
-// The scale is 2^62 / (sum of the chunk's |q_p| / V), rounded down to a power
-// of two, so no node can overflow; a contribution is rounded once, to
-// 2^-62 of the chunk's charge.  Non-zero window nodes are then added to the
-// global grid in the run's precision.  Corners outside a window clamped to
+// window of regular nodes in shared memory, accumulated with WinAcc (for
+// the FP32 path the fixed-point scale is 2^30 / (sum of the chunk's |q_p| / V)
+// rounded down to a power of two, so no node can overflow).  Non-zero window
+// nodes are then added to the global grid in the run's precision.  Corners outside a window clamped to
 // the shared-memory capacity add directly to the global grid.
 template <typename real, int D>
 __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, size_t np, int n,
                                                          real inv_cell_vol, real* __restrict__ rho, int side) {
   extern __shared__ unsigned char smem_raw[];
-  unsigned long long* win = reinterpret_cast<unsigned long long*>(smem_raw);
+  using W = WinAcc<real>;
+  using T = typename W::T;
+  T* win = reinterpret_cast<T*>(smem_raw);
   __shared__ int s_anchor[D], s_min[D], s_max[D];
   __shared__ double s_wq[DEP_THREADS / 32];
   const int N = 1 << n;
@@ -164,9 +184,10 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
   for (int w = 0; w < DEP_THREADS / 32; ++w) qsum += s_wq[w];
   int ex = 0;
   frexp(qsum, &ex);  // qsum < 2^ex
-  const real scale = qsum > 0.0 ? (real)ldexp(1.0, 62 - ex) : (real)1;
-  const real inv_scale = qsum > 0.0 ? (real)ldexp(1.0, ex - 62) : (real)1;
-  for (int i = threadIdx.x; i < nwin; i += DEP_THREADS) win[i] = 0ull;
+  const bool fixed = W::bits > 0 && qsum > 0.0;
+  const real scale = fixed ? (real)ldexp(1.0, W::bits - ex) : (real)1;
+  const real inv_scale = fixed ? (real)ldexp(1.0, ex - W::bits) : (real)1;
+  for (int i = threadIdx.x; i < nwin; i += DEP_THREADS) win[i] = (T)0;
   __syncthreads();
 
 #pragma unroll
@@ -190,8 +211,7 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
         gstride *= N;
       }
       if (inside) {
-        const long long v = sizeof(real) == 4 ? __float2ll_rn((float)(wgt * scale)) : __double2ll_rn((double)(wgt * scale));
-        atomicAdd(&win[loc], (unsigned long long)v);
+        atomicAdd(&win[loc], W::quantize(wgt * scale));
       } else {
         atomicAdd(&rho[glob], wgt);
       }
@@ -199,8 +219,8 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nwin; i += DEP_THREADS) {
-    const long long sv = (long long)win[i];
-    if (sv != 0) {
+    const T sv = win[i];
+    if (sv != (T)0) {
       int rem = i, glob = 0, gstride = 1;
 #pragma unroll
       for (int m = 0; m < D; ++m) {
@@ -209,7 +229,7 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
         glob += ((org[m] + l) & mask) * gstride;
         gstride *= N;
       }
-      atomicAdd(&rho[glob], (real)sv * inv_scale);
+      atomicAdd(&rho[glob], W::value(sv, inv_scale));
     }
   }
 }
@@ -219,16 +239,18 @@ int launch_deposit(const PArrays<real, D>& p, size_t np, int n, real inv_cell_vo
                    cudaStream_t s) {
   if (np == 0) return SG_OK;
   unsigned blocks = (unsigned)((np + DEP_CHUNK - 1) / DEP_CHUNK);
+  using T = typename WinAcc<real>::T;
+  const long long cap = (long long)win_cap_nodes * 8 / (long long)sizeof(T);  // same bytes for either type
   int side = 1;  // largest side with side^D <= capacity
   while (true) {
     long long nxt = 1;
     for (int m = 0; m < D; ++m) nxt *= (side + 1);
-    if (nxt > win_cap_nodes) break;
+    if (nxt > cap) break;
     ++side;
   }
   long long nodes = 1;
   for (int m = 0; m < D; ++m) nodes *= side;
-  size_t smem = (size_t)nodes * sizeof(unsigned long long);
+  size_t smem = (size_t)nodes * sizeof(T);
   static bool attr_set = false;
   if (smem > 48 * 1024 && !attr_set) {
     SG_CUDA(cudaFuncSetAttribute(k_deposit<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));

@@ -515,6 +515,10 @@ class Engine final : public EngineBase {
 
   int stage_times(double* ms, int cap) override {
     for (int i = 0; i < 6 && i < cap; ++i) ms[i] = stage_ms_[i];
+    // autotuner record: chosen solve variant and the timings it compared
+    if (cap > 6) ms[6] = solve_mode_;
+    if (cap > 7) ms[7] = solve_ms_[0];
+    if (cap > 8) ms[8] = solve_ms_[1];
     return SG_OK;
   }
 
@@ -523,6 +527,30 @@ class Engine final : public EngineBase {
   cudaStream_t stream() const override { return stream_; }
   size_t n_particles() const override { return np_; }
   long long steps_done() const override { return step_; }
+  bool next_step_sorts() const override { return ((step_ + 1) % sort_every_) == 0; }
+  int cur_set() const override { return cur_; }
+  int capture_step(bool do_sort) override {
+    const int cb = cur_;
+    const int st = enqueue_step(do_sort);
+    cur_ = cb;
+    return st;
+  }
+  void commit_step(bool did_sort, unsigned long long kernels) override {
+    if (did_sort) cur_ ^= 1;
+    ++step_;
+    launches_ += kernels;
+  }
+  int step_plain() override {
+    const bool do_sort = next_step_sorts();
+    const unsigned long long l0 = launches_so_far();
+    per_grid_ = true;
+    const int st = enqueue_step(do_sort);
+    per_grid_ = false;
+    if (st != SG_OK) return st;
+    ++step_;
+    launches_ += launches_so_far() - l0;
+    return SG_OK;
+  }
 
  private:
   // ------------------------------------------------------------ memory
@@ -765,7 +793,7 @@ class Engine final : public EngineBase {
     } else {
       seq = {{FFT_FWD_FIRST, 0}, {FFT_FWD_MID, 1}, {FFT_LAST, 2}, {FFT_INV_MID, 1}, {FFT_INV_LAST, 0}};
     }
-    const int CAPC = 2048;  // complex values per buffer
+    const int CAPC = 1024;  // complex values per buffer: one butterfly per thread of 512 per stage
     for (auto& ka : seq) {
       const int kind = ka.first, axis = ka.second;
       const bool per_comp = (kind == FFT_INV_MID || kind == FFT_INV_LAST);
@@ -911,6 +939,10 @@ class Engine final : public EngineBase {
     int maxsize = 0;
     for (auto& g : gdesc_) maxsize = std::max(maxsize, g.size);
     const bool small_ok = maxsize <= small_solve_max<real>();
+    if (small_ok && per_grid_) {  // plain path: one launch per component grid
+      for (int g = 0; g < ngrids_; ++g) SG_TRY(launch_solve_small<real>(a, 1, gdesc_[g].size, stream_, g));
+      return SG_OK;
+    }
     if (small_ok && (solve_mode_ == 1 || (solve_mode_ == -1 && force_mode_ < 0)))
       return launch_solve_small<real>(a, ngrids_, maxsize, stream_);
     for (auto& P : fpasses_) SG_TRY(launch_fft_pass<real>(P.kind, a, P.dev, P.njobs, P.nblocks, P.smem, stream_));
@@ -1093,6 +1125,7 @@ class Engine final : public EngineBase {
   std::vector<GridDesc> gdesc_;
   int ngrids_ = 0, lmin_ = 0;
   LevelLists levels_{};
+  bool per_grid_ = false;
   int solve_mode_ = -1;  // -1 untuned, 0 per-axis passes, 1 one block per grid
   int force_mode_ = -1;
   float solve_ms_[2] = {0, 0};

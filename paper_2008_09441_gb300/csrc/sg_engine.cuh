@@ -58,6 +58,16 @@ class EngineBase {
   virtual cudaStream_t stream() const = 0;
   virtual size_t n_particles() const = 0;
   virtual long long steps_done() const = 0;
+  // Batched serving: whether the next step sorts, which particle set is
+  // current, enqueue one step on the run's stream inside a caller's stream
+  // capture (host state unchanged), then commit the host state after the
+  // captured graph ran.
+  virtual bool next_step_sorts() const = 0;
+  virtual int cur_set() const = 0;
+  virtual int capture_step(bool do_sort) = 0;
+  virtual void commit_step(bool did_sort, unsigned long long kernels) = 0;
+  // Plain path: direct launches, one solve launch per component grid.
+  virtual int step_plain() = 0;
 };
 
 EngineBase* make_engine(int precision, int dim);

@@ -142,7 +142,7 @@ int launch_fft_pass(int kind, const SolveArena<real>& a, const FftJob* jobs_dev,
 // All component grids in one launch, one block per grid, whole grid in shared
 // memory (used when every grid has at most SMALL_SOLVE_MAX<real> points).
 template <typename real>
-int launch_solve_small(const SolveArena<real>& a, int ngrids, int max_size, cudaStream_t s);
+int launch_solve_small(const SolveArena<real>& a, int ngrids, int max_size, cudaStream_t s, int grid0 = 0);
 template <typename real>
 constexpr int small_solve_max() { return sizeof(real) == 4 ? 4096 : 2048; }
 

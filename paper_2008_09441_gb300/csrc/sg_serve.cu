@@ -1,12 +1,19 @@
 // Serving: many independent runs resident on one GPU, admitted in arrival
-// order by device-memory footprint, advanced together tick by tick.  Each
-// resident run owns a stream, so the runs' kernels overlap on the device;
-// per-step latency is measured with events on the run's stream.
+// order by device-memory footprint, advanced together tick by tick.
+//
+// Batched mode (default): one tick is one CUDA graph that forks from the
+// server's stream into every resident run's stream, enqueues one step of
+// each run there (the runs' kernels overlap on the device) and joins back;
+// graphs are cached per resident set and particle-buffer parity, so a tick is
+// a single graph launch.  Plain mode: each run steps in turn with direct
+// kernel launches and one solve launch per component grid, waiting for each
+// run before the next (the per-grid, per-run launch path).
 #include <algorithm>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "sg_engine.cuh"
@@ -16,10 +23,10 @@ using namespace sg;
 namespace {
 
 struct Request {
-  unsigned long long ticket;
+  unsigned long long ticket = 0;
   sg_request req;
-  std::vector<char> u[3], v[3], w;  // host copies
-  size_t footprint;
+  std::vector<char> u[3], v[3], w;  // host copies until admission
+  size_t footprint = 0;
   int state = SG_REQ_QUEUED;
   EngineBase* eng = nullptr;
   cudaStream_t stream = nullptr;
@@ -29,11 +36,17 @@ struct Request {
   std::vector<char> result_u[3], result_v[3], result_w;
 };
 
+struct CachedGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<unsigned long long> kernels;  // per resident run
+};
+
 }  // namespace
 
 struct sg_server {
   size_t budget = 0;
   int max_slots = 0;
+  int mode = SG_SERVE_BATCHED;
   size_t in_use = 0;
   unsigned long long next_ticket = 1;
   std::deque<Request*> queue;
@@ -43,12 +56,21 @@ struct sg_server {
   double device_ms = 0;
   double particle_steps = 0;
   unsigned long long steps_served = 0;
+  cudaStream_t ds = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+  std::map<std::string, CachedGraph> graphs;
   std::mutex mu;
 };
 
 static int serr(const char* m, int code = SG_ERR_INVALID) {
   set_error(m);
   return code;
+}
+
+static void clear_graphs(sg_server* s) {
+  for (auto& kv : s->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  s->graphs.clear();
 }
 
 static void finish(sg_server* s, Request* r, int state) {
@@ -89,6 +111,123 @@ static void finish(sg_server* s, Request* r, int state) {
   r->state = state;
 }
 
+static int admit(sg_server* s, bool* changed) {
+  while (!s->queue.empty() && (int)s->resident.size() < s->max_slots &&
+         s->in_use + s->queue.front()->footprint <= s->budget) {
+    Request* r = s->queue.front();
+    s->queue.pop_front();
+    s->in_use += r->footprint;
+    *changed = true;
+    if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&r->ev0) != cudaSuccess || cudaEventCreate(&r->ev1) != cudaSuccess) {
+      finish(s, r, SG_REQ_FAILED);
+      continue;
+    }
+    EngineConfig cfg;
+    const sg_request& q = r->req;
+    cfg.dim = q.dim;
+    cfg.n = q.level_n;
+    cfg.tau = q.params.tau;
+    cfg.precision = q.params.precision;
+    for (int m = 0; m < 3; ++m) {
+      cfg.L[m] = m < q.dim ? q.domain.L[m] : 1.0;
+      cfg.B[m] = q.params.B[m];
+      cfg.eext_lin[m] = q.params.Eext_lin[m];
+    }
+    cfg.dt = q.params.dt;
+    cfg.qm = q.params.qm;
+    cfg.alpha = q.params.alpha;
+    cfg.pc_ref = q.params.pc_ref;
+    cfg.tau_constants = q.params.tau_constants;
+    cfg.sort_every = q.params.sort_every;
+    sg_particles hp;
+    std::memset(&hp, 0, sizeof(hp));
+    hp.n = q.particles.n;
+    hp.on_device = 0;
+    for (int m = 0; m < q.dim; ++m) {
+      hp.u[m] = r->u[m].data();
+      hp.v[m] = r->v[m].data();
+    }
+    hp.w = r->w.data();
+    r->eng = make_engine(q.params.precision, q.dim);
+    if (!r->eng || r->eng->init(cfg, &hp, r->stream) != SG_OK) {
+      finish(s, r, SG_REQ_FAILED);
+      continue;
+    }
+    r->state = SG_REQ_RUNNING;
+    s->resident.push_back(r);
+  }
+  return SG_OK;
+}
+
+// One graph over every resident run that still has steps to take.
+static int tick_batched(sg_server* s, std::vector<Request*>& act) {
+  std::string key;
+  std::vector<bool> sorts(act.size());
+  for (size_t i = 0; i < act.size(); ++i) {
+    sorts[i] = act[i]->eng->next_step_sorts();
+    key += std::to_string(act[i]->ticket) + ":" + std::to_string(act[i]->eng->cur_set()) + (sorts[i] ? "s" : "n") + ";";
+  }
+  auto it = s->graphs.find(key);
+  if (it == s->graphs.end()) {
+    CachedGraph cg;
+    cudaGraph_t g;
+    SG_CUDA(cudaStreamBeginCapture(s->ds, cudaStreamCaptureModeThreadLocal));
+    int st = SG_OK;
+    cudaEventRecord(s->ev_start, s->ds);
+    for (size_t i = 0; i < act.size() && st == SG_OK; ++i) {
+      Request* r = act[i];
+      cudaStreamWaitEvent(r->stream, s->ev_start, 0);
+      const unsigned long long l0 = launches_so_far();
+      st = r->eng->capture_step(sorts[i]);
+      cg.kernels.push_back(launches_so_far() - l0);
+      cudaEventRecord(r->ev1, r->stream);
+      cudaStreamWaitEvent(s->ds, r->ev1, 0);
+    }
+    cudaEventRecord(s->ev_end, s->ds);
+    cudaError_t e = cudaStreamEndCapture(s->ds, &g);
+    if (st != SG_OK) return st;
+    if (e != cudaSuccess) {
+      set_error(std::string("serving graph capture: ") + cudaGetErrorString(e));
+      return SG_ERR_CUDA;
+    }
+    cudaError_t e2 = cudaGraphInstantiate(&cg.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+      set_error(std::string("serving graph instantiate: ") + cudaGetErrorString(e2));
+      return SG_ERR_CUDA;
+    }
+    it = s->graphs.emplace(key, cg).first;
+  }
+  SG_CUDA(cudaGraphLaunch(it->second.exec, s->ds));
+  SG_CUDA(cudaStreamSynchronize(s->ds));
+  float tick_ms = 0;
+  cudaEventElapsedTime(&tick_ms, s->ev_start, s->ev_end);
+  s->device_ms += tick_ms;
+  for (size_t i = 0; i < act.size(); ++i) {
+    Request* r = act[i];
+    float ms = 0;
+    cudaEventElapsedTime(&ms, s->ev_start, r->ev1);
+    s->step_ms.push_back(ms);
+    r->eng->commit_step(sorts[i], it->second.kernels[i]);
+  }
+  return SG_OK;
+}
+
+static int tick_plain(sg_server* s, std::vector<Request*>& act) {
+  for (Request* r : act) {
+    SG_CUDA(cudaEventRecord(r->ev0, r->stream));
+    SG_TRY(r->eng->step_plain());
+    SG_CUDA(cudaEventRecord(r->ev1, r->stream));
+    SG_CUDA(cudaEventSynchronize(r->ev1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, r->ev0, r->ev1);
+    s->step_ms.push_back(ms);
+    s->device_ms += ms;
+  }
+  return SG_OK;
+}
+
 extern "C" {
 
 int sg_serve_create(size_t hbm_budget_bytes, int max_slots, sg_server** out) {
@@ -97,7 +236,21 @@ int sg_serve_create(size_t hbm_budget_bytes, int max_slots, sg_server** out) {
   sg_server* s = new sg_server;
   s->budget = hbm_budget_bytes;
   s->max_slots = max_slots;
+  if (cudaStreamCreateWithFlags(&s->ds, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&s->ev_start) != cudaSuccess || cudaEventCreate(&s->ev_end) != cudaSuccess) {
+    delete s;
+    return serr("sg_serve_create: stream/event creation failed", SG_ERR_CUDA);
+  }
   *out = s;
+  return SG_OK;
+}
+
+int sg_serve_set_mode(sg_server* s, int mode) {
+  if (!s) return serr("sg_serve_set_mode: NULL server");
+  if (mode != SG_SERVE_BATCHED && mode != SG_SERVE_PLAIN) return serr("sg_serve_set_mode: unknown mode");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->mode = mode;
+  clear_graphs(s);
   return SG_OK;
 }
 
@@ -144,79 +297,37 @@ int sg_serve_submit(sg_server* s, const sg_request* req, unsigned long long* tic
 int sg_serve_tick(sg_server* s, int* active) {
   if (!s) return serr("sg_serve_tick: NULL server");
   std::lock_guard<std::mutex> lk(s->mu);
-  // admit in arrival order while memory and slots allow
-  while (!s->queue.empty() && (int)s->resident.size() < s->max_slots &&
-         s->in_use + s->queue.front()->footprint <= s->budget) {
-    Request* r = s->queue.front();
-    s->queue.pop_front();
-    s->in_use += r->footprint;
-    if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreate(&r->ev0) != cudaSuccess || cudaEventCreate(&r->ev1) != cudaSuccess) {
-      finish(s, r, SG_REQ_FAILED);
-      continue;
+  bool changed = false;
+  SG_TRY(admit(s, &changed));
+  std::vector<Request*> act;
+  for (Request* r : s->resident)
+    if (r->steps_left > 0) act.push_back(r);
+  if (!act.empty()) {
+    int st = s->mode == SG_SERVE_BATCHED ? tick_batched(s, act) : tick_plain(s, act);
+    if (st != SG_OK) {
+      for (Request* r : act) r->steps_left = -1;
+    } else {
+      for (Request* r : act) {
+        s->particle_steps += (double)r->req.particles.n;
+        ++s->steps_served;
+        --r->steps_left;
+      }
     }
-    EngineConfig cfg;
-    const sg_request& q = r->req;
-    cfg.dim = q.dim;
-    cfg.n = q.level_n;
-    cfg.tau = q.params.tau;
-    cfg.precision = q.params.precision;
-    for (int m = 0; m < 3; ++m) {
-      cfg.L[m] = m < q.dim ? q.domain.L[m] : 1.0;
-      cfg.B[m] = q.params.B[m];
-      cfg.eext_lin[m] = q.params.Eext_lin[m];
-    }
-    cfg.dt = q.params.dt;
-    cfg.qm = q.params.qm;
-    cfg.alpha = q.params.alpha;
-    cfg.pc_ref = q.params.pc_ref;
-    cfg.tau_constants = q.params.tau_constants;
-    cfg.sort_every = q.params.sort_every;
-    sg_particles hp;
-    std::memset(&hp, 0, sizeof(hp));
-    hp.n = q.particles.n;
-    hp.on_device = 0;
-    for (int m = 0; m < q.dim; ++m) {
-      hp.u[m] = r->u[m].data();
-      hp.v[m] = r->v[m].data();
-    }
-    hp.w = r->w.data();
-    r->eng = make_engine(q.params.precision, q.dim);
-    if (!r->eng || r->eng->init(cfg, &hp, r->stream) != SG_OK) {
-      finish(s, r, SG_REQ_FAILED);
-      continue;
-    }
-    r->state = SG_REQ_RUNNING;
-    s->resident.push_back(r);
-  }
-  // one step of every resident run, each on its own stream
-  for (Request* r : s->resident) {
-    if (r->steps_left <= 0) continue;
-    cudaEventRecord(r->ev0, r->stream);
-    if (r->eng->step(1) != SG_OK) r->steps_left = -1;
-    cudaEventRecord(r->ev1, r->stream);
   }
   std::vector<Request*> keep;
   for (Request* r : s->resident) {
-    if (r->steps_left > 0) {
-      cudaEventSynchronize(r->ev1);
-      float ms = 0;
-      cudaEventElapsedTime(&ms, r->ev0, r->ev1);
-      s->step_ms.push_back(ms);
-      s->device_ms += ms;
-      s->particle_steps += (double)r->req.particles.n;
-      ++s->steps_served;
-      --r->steps_left;
-    }
     if (r->steps_left == 0) {
       finish(s, r, SG_REQ_DONE);
+      changed = true;
     } else if (r->steps_left < 0) {
       finish(s, r, SG_REQ_FAILED);
+      changed = true;
     } else {
       keep.push_back(r);
     }
   }
   s->resident.swap(keep);
+  if (changed) clear_graphs(s);
   if (active) *active = (int)s->resident.size();
   return SG_OK;
 }
@@ -273,8 +384,12 @@ int sg_serve_stats(sg_server* s, double* p50_ms, double* p99_ms, double* particl
 
 void sg_serve_destroy(sg_server* s) {
   if (!s) return;
+  clear_graphs(s);
   for (Request* r : s->resident) finish(s, r, SG_REQ_FAILED);
   for (auto& kv : s->all) delete kv.second;
+  if (s->ev_start) cudaEventDestroy(s->ev_start);
+  if (s->ev_end) cudaEventDestroy(s->ev_end);
+  if (s->ds) cudaStreamDestroy(s->ds);
   delete s;
 }
 

@@ -54,7 +54,7 @@ __device__ __forceinline__ int sfreq(int i, int N) { return i < (N >> 1) ? i : i
 // along axis > 0 consecutive threads take consecutive lines so that strided
 // columns are read together.
 template <typename real>
-__global__ void __launch_bounds__(256) k_fft_pass(int kind, SolveArena<real> a, const FftJob* __restrict__ jobs,
+__global__ void __launch_bounds__(512) k_fft_pass(int kind, SolveArena<real> a, const FftJob* __restrict__ jobs,
                                                   int njobs) {
   extern __shared__ unsigned char smem_raw[];
   const int b = blockIdx.x;
@@ -67,7 +67,11 @@ __global__ void __launch_bounds__(256) k_fft_pass(int kind, SolveArena<real> a, 
   const int logC = __ffs(C) - 1;
   const int line0 = (b - J.block_begin) * C;
   const int nl = C;
-  cplx<real>* buf0 = reinterpret_cast<cplx<real>*>(smem_raw);
+  // twiddles staged in shared memory, then the two line buffers
+  cplx<real>* tws = reinterpret_cast<cplx<real>*>(smem_raw);
+  const int ntw = 1 << (a.log_nmax - 1);
+  for (int e = threadIdx.x; e < ntw; e += blockDim.x) tws[e] = a.tw[e];
+  cplx<real>* buf0 = tws + ntw;
   cplx<real>* buf1 = buf0 + C * len;
   int ls = 0;
   for (int m = 0; m < J.axis; ++m) ls += __ffs(J.dims[m]) - 1;
@@ -92,7 +96,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(int kind, SolveArena<real> a, 
   }
   __syncthreads();
   const bool inverse = (kind == FFT_INV_MID || kind == FFT_INV_LAST);
-  fft_smem<real>(buf0, nl, logn, inverse, a.tw, a.log_nmax);
+  fft_smem<real>(buf0, nl, logn, inverse, tws, a.log_nmax);
 
   if (kind == FFT_LAST) {
     const int D = a.dim;
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(int kind, SolveArena<real> a, 
         buf1[(li << logn) + bitrev(t, logn)] = out;
       }
       __syncthreads();
-      fft_smem<real>(buf1, nl, logn, true, a.tw, a.log_nmax);
+      fft_smem<real>(buf1, nl, logn, true, tws, a.log_nmax);
       for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int li = contiguous ? (e >> logn) : (e & (nl - 1));
         const int t = contiguous ? (e & (len - 1)) : (e >> logC);
@@ -168,7 +172,7 @@ int launch_fft_pass(int kind, const SolveArena<real>& a, const FftJob* jobs_dev,
     SG_CUDA(cudaFuncSetAttribute(k_fft_pass<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  k_fft_pass<real><<<nblocks, 256, smem_bytes, s>>>(kind, a, jobs_dev, njobs);
+  k_fft_pass<real><<<nblocks, 512, smem_bytes + ((size_t)1 << (a.log_nmax - 1)) * sizeof(cplx<real>), s>>>(kind, a, jobs_dev, njobs);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
@@ -223,9 +227,9 @@ __device__ void fft_axis_inplace(cplx<real>* buf, const int* logs, int S, int ax
 }
 
 template <typename real>
-__global__ void __launch_bounds__(1024) k_solve_small(SolveArena<real> a, int max_size) {
+__global__ void __launch_bounds__(1024) k_solve_small(SolveArena<real> a, int max_size, int grid0) {
   extern __shared__ unsigned char smem_raw[];
-  const GridDesc g = a.grids[blockIdx.x];
+  const GridDesc g = a.grids[grid0 + blockIdx.x];
   const int D = a.dim;
   int logs[3] = {0, 0, 0};
   for (int m = 0; m < D; ++m) logs[m] = g.l[m];
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(1024) k_solve_small(SolveArena<real> a, int ma
 }
 
 template <typename real>
-int launch_solve_small(const SolveArena<real>& a, int ngrids, int max_size, cudaStream_t s) {
+int launch_solve_small(const SolveArena<real>& a, int ngrids, int max_size, cudaStream_t s, int grid0) {
   if (ngrids == 0) return SG_OK;
   int threads = max_size / 2;
   threads = threads < 64 ? 64 : (threads > 1024 ? 1024 : threads);
@@ -283,13 +287,13 @@ int launch_solve_small(const SolveArena<real>& a, int ngrids, int max_size, cuda
     SG_CUDA(cudaFuncSetAttribute(k_solve_small<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  k_solve_small<real><<<ngrids, threads, smem, s>>>(a, max_size);
+  k_solve_small<real><<<ngrids, threads, smem, s>>>(a, max_size, grid0);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
 
-template int launch_solve_small<float>(const SolveArena<float>&, int, int, cudaStream_t);
-template int launch_solve_small<double>(const SolveArena<double>&, int, int, cudaStream_t);
+template int launch_solve_small<float>(const SolveArena<float>&, int, int, cudaStream_t, int);
+template int launch_solve_small<double>(const SolveArena<double>&, int, int, cudaStream_t, int);
 
 // In-place FFT of a whole N^D complex array along one axis (regular grid).
 template <typename real>

@@ -389,102 +389,164 @@ int launch_tile_keys(const PArrays<real, D>& p, size_t np, int n, const SortFuse
   return SG_OK;
 }
 
-// Per-tile counts of the keys: each warp reads TS_ROUNDS x 32 keys (vectors
-// of four), combines equal keys within the warp and adds the group counts.
-constexpr int TS_ROUNDS = 8;
+// Block-level counting.  A block takes TB_ITEMS consecutive keys (the
+// particles were tile-sorted one step earlier, so the block sees a narrow
+// range of tiles); when that range fits TB_SPAN shared counters the block
+// counts there with native 32-bit shared atomics and issues one global
+// atomic per distinct tile, otherwise each key adds to the global counter.
+constexpr int TB_THREADS = 256;
+constexpr int TB_PER_THREAD = 8;
+constexpr int TB_ITEMS = TB_THREADS * TB_PER_THREAD;
+constexpr int TB_SPAN = 1024;
 
-__global__ void __launch_bounds__(256) k_tile_hist(const uint32_t* __restrict__ keys, size_t np,
-                                                   uint32_t* tile_count) {
-  const int lane = threadIdx.x & 31;
-  const size_t wbase = ((size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (128 * (TS_ROUNDS / 4));
+__device__ __forceinline__ void block_key_range(const uint32_t (&t)[TB_PER_THREAD], uint32_t* s_lo, uint32_t* s_hi) {
+  uint32_t lo = 0xFFFFFFFFu, hi = 0;
 #pragma unroll
-  for (int r = 0; r < TS_ROUNDS / 4; ++r) {
-    const size_t i0 = wbase + ((size_t)r * 32 + lane) * 4;
-    uint32_t t[4];
-    if (i0 + 4 <= np) {
-      const uint4 v = __ldg(reinterpret_cast<const uint4*>(keys + i0));
-      t[0] = v.x;
-      t[1] = v.y;
-      t[2] = v.z;
-      t[3] = v.w;
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) t[k] = i0 + k < np ? keys[i0 + k] : 0xFFFFFFFFu;
+  for (int k = 0; k < TB_PER_THREAD; ++k)
+    if (t[k] != 0xFFFFFFFFu) {
+      lo = min(lo, t[k]);
+      hi = max(hi, t[k]);
     }
-    uint32_t c0 = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (t[k] == t[0])
-        ++c0;
-      else if (t[k] != 0xFFFFFFFFu)
-        atomicAdd(&tile_count[t[k]], 1u);
-    }
-    const unsigned peers = __match_any_sync(0xffffffffu, t[0]);
-    const uint32_t sum = __reduce_add_sync(peers, c0);
-    if (t[0] != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&tile_count[t[0]], sum);
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
   }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(s_lo, lo);
+    atomicMax(s_hi, hi);
+  }
+}
+
+// Keys of item k of thread t: chunk + k * TB_THREADS + t (coalesced rounds).
+__device__ __forceinline__ void load_keys(const uint32_t* __restrict__ keys, size_t np, size_t chunk,
+                                          uint32_t (&t)[TB_PER_THREAD]) {
+#pragma unroll
+  for (int k = 0; k < TB_PER_THREAD; ++k) {
+    const size_t i = chunk + (size_t)k * TB_THREADS + threadIdx.x;
+    t[k] = i < np ? __ldg(keys + i) : 0xFFFFFFFFu;
+  }
+}
+
+__global__ void __launch_bounds__(TB_THREADS) k_tile_hist(const uint32_t* __restrict__ keys, size_t np,
+                                                          uint32_t* tile_count) {
+  __shared__ uint32_t s_cnt[TB_SPAN];
+  __shared__ uint32_t s_lo, s_hi;
+  const size_t chunk = (size_t)blockIdx.x * TB_ITEMS;
+  uint32_t t[TB_PER_THREAD];
+  load_keys(keys, np, chunk, t);
+  if (threadIdx.x == 0) {
+    s_lo = 0xFFFFFFFFu;
+    s_hi = 0;
+  }
+  for (int i = threadIdx.x; i < TB_SPAN; i += TB_THREADS) s_cnt[i] = 0;
+  __syncthreads();
+  block_key_range(t, &s_lo, &s_hi);
+  __syncthreads();
+  const uint32_t lo = s_lo;
+  const bool local = s_hi - lo < (uint32_t)TB_SPAN;
+#pragma unroll
+  for (int k = 0; k < TB_PER_THREAD; ++k) {
+    if (t[k] == 0xFFFFFFFFu) continue;
+    if (local)
+      atomicAdd(&s_cnt[t[k] - lo], 1u);
+    else
+      atomicAdd(&tile_count[t[k]], 1u);
+  }
+  if (!local) return;
+  __syncthreads();
+  for (int i = threadIdx.x; i < TB_SPAN; i += TB_THREADS)
+    if (s_cnt[i]) atomicAdd(&tile_count[lo + i], s_cnt[i]);
 }
 
 int launch_tile_hist(const uint32_t* keys, size_t np, uint32_t* tile_count, cudaStream_t s) {
   if (np == 0) return SG_OK;
-  const size_t per_block = (size_t)256 * TS_ROUNDS;  // 8 warps x (TS_ROUNDS / 4) rounds x 128 keys
-  k_tile_hist<<<(unsigned)((np + per_block - 1) / per_block), 256, 0, s>>>(keys, np, tile_count);
+  k_tile_hist<<<(unsigned)((np + TB_ITEMS - 1) / TB_ITEMS), TB_THREADS, 0, s>>>(keys, np, tile_count);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
 
-// Scatter every particle to its tile's next free slot.  Each warp takes
-// TS_ROUNDS x 32 consecutive particles: it reserves the slots of all rounds
-// (lanes with equal tiles share one reservation) and loads all payloads
-// before storing any, so the round trips overlap.  Within a tile the order
-// follows the warps' arrival: the step sort is a valid, not a stable,
-// counting sort by tile key.
+// Scatter every particle to its tile's slots.  Same blocks as the count: the
+// block ranks its particles per tile with shared atomics, reserves one range
+// per distinct tile with a single global atomic, then moves each particle's
+// payload (loads issued before the stores).  Blocks whose keys span more
+// tiles than the shared counters reserve per warp group instead.  Within a
+// tile the order depends on the atomics: the step sort is a valid, not a
+// stable, counting sort by tile key.
 template <typename real, int D>
-__global__ void __launch_bounds__(256) k_tile_scatter(PArrays<real, D> src, PArrays<real, D> dst,
-                                                      const uint32_t* __restrict__ keys, uint32_t* cursor,
-                                                      size_t np) {
-  constexpr int R = 4;
+__global__ void __launch_bounds__(TB_THREADS) k_tile_scatter(PArrays<real, D> src, PArrays<real, D> dst,
+                                                             const uint32_t* __restrict__ keys, uint32_t* cursor,
+                                                             size_t np) {
+  __shared__ uint32_t s_cnt[TB_SPAN];
+  __shared__ uint32_t s_lo, s_hi;
+  const size_t chunk = (size_t)blockIdx.x * TB_ITEMS;
   const int lane = threadIdx.x & 31;
-  const size_t wbase = ((size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * R);
-  uint32_t base[R], rank[R];
-  int leader[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const size_t i = wbase + (size_t)r * 32 + lane;
-    const bool valid = i < np;
-    const uint32_t t = valid ? __ldg(keys + i) : 0xFFFFFFFFu;
-    const unsigned peers = __match_any_sync(0xffffffffu, t);
-    leader[r] = __ffs(peers) - 1;
-    rank[r] = (uint32_t)__popc(peers & ((1u << lane) - 1u));
-    base[r] = 0;
-    if (valid && lane == leader[r]) base[r] = atomicAdd(&cursor[t], (uint32_t)__popc(peers));
+  uint32_t t[TB_PER_THREAD];
+  load_keys(keys, np, chunk, t);
+  if (threadIdx.x == 0) {
+    s_lo = 0xFFFFFFFFu;
+    s_hi = 0;
   }
-  real pu[R][D], pv[R][D], pw[R];
-  uint32_t pid[R];
+  for (int i = threadIdx.x; i < TB_SPAN; i += TB_THREADS) s_cnt[i] = 0;
+  __syncthreads();
+  block_key_range(t, &s_lo, &s_hi);
+  __syncthreads();
+  const uint32_t lo = s_lo;
+  const bool local = s_hi - lo < (uint32_t)TB_SPAN;
+  uint32_t pos[TB_PER_THREAD];
+  if (local) {
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const size_t i = wbase + (size_t)r * 32 + lane;
-    const bool valid = i < np;
+    for (int k = 0; k < TB_PER_THREAD; ++k)
+      pos[k] = t[k] != 0xFFFFFFFFu ? atomicAdd(&s_cnt[t[k] - lo], 1u) : 0u;  // rank within the block's tile
+    __syncthreads();
+    for (int i = threadIdx.x; i < TB_SPAN; i += TB_THREADS)
+      if (s_cnt[i]) s_cnt[i] = atomicAdd(&cursor[lo + i], s_cnt[i]);  // block's base in the tile
+    __syncthreads();
 #pragma unroll
-    for (int m = 0; m < D; ++m) {
-      pu[r][m] = valid ? __ldg(src.u[m] + i) : (real)0;
-      pv[r][m] = valid ? __ldg(src.v[m] + i) : (real)0;
+    for (int k = 0; k < TB_PER_THREAD; ++k)
+      if (t[k] != 0xFFFFFFFFu) pos[k] += s_cnt[t[k] - lo];
+  } else {
+#pragma unroll
+    for (int k = 0; k < TB_PER_THREAD; ++k) {
+      const bool valid = t[k] != 0xFFFFFFFFu;
+      const unsigned peers = __match_any_sync(0xffffffffu, t[k]);
+      const int leader = __ffs(peers) - 1;
+      uint32_t base = 0;
+      if (valid && lane == leader) base = atomicAdd(&cursor[t[k]], (uint32_t)__popc(peers));
+      pos[k] = __shfl_sync(0xffffffffu, base, leader) + (uint32_t)__popc(peers & ((1u << lane) - 1u));
     }
-    pw[r] = valid ? __ldg(src.w + i) : (real)0;
-    pid[r] = valid ? __ldg(src.pid + i) : 0u;
   }
+  // move the payload: loads of all items first, then the stores
+  constexpr int G = 4;
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const uint32_t pos = __shfl_sync(0xffffffffu, base[r], leader[r]) + rank[r];
-    const size_t i = wbase + (size_t)r * 32 + lane;
-    if (i >= np) continue;
+  for (int g0 = 0; g0 < TB_PER_THREAD; g0 += G) {
+    real pu[G][D], pv[G][D], pw[G];
+    uint32_t pid[G];
 #pragma unroll
-    for (int m = 0; m < D; ++m) {
-      dst.u[m][pos] = pu[r][m];
-      dst.v[m][pos] = pv[r][m];
+    for (int k = 0; k < G; ++k) {
+      const size_t i = chunk + (size_t)(g0 + k) * TB_THREADS + threadIdx.x;
+      const bool valid = i < np;
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        pu[k][m] = valid ? __ldg(src.u[m] + i) : (real)0;
+        pv[k][m] = valid ? __ldg(src.v[m] + i) : (real)0;
+      }
+      pw[k] = valid ? __ldg(src.w + i) : (real)0;
+      pid[k] = valid ? __ldg(src.pid + i) : 0u;
     }
-    dst.w[pos] = pw[r];
-    dst.pid[pos] = pid[r];
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      const size_t i = chunk + (size_t)(g0 + k) * TB_THREADS + threadIdx.x;
+      if (i >= np) continue;
+      const uint32_t p = pos[g0 + k];
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        dst.u[m][p] = pu[k][m];
+        dst.v[m][p] = pv[k][m];
+      }
+      dst.w[p] = pw[k];
+      dst.pid[p] = pid[k];
+    }
   }
 }
 
@@ -492,8 +554,7 @@ template <typename real, int D>
 int launch_tile_scatter(const PArrays<real, D>& src, const PArrays<real, D>& dst, const uint32_t* keys,
                         uint32_t* cursor, size_t np, cudaStream_t s) {
   if (np == 0) return SG_OK;
-  const size_t per_block = (size_t)256 * 4;
-  k_tile_scatter<real, D><<<(unsigned)((np + per_block - 1) / per_block), 256, 0, s>>>(src, dst, keys, cursor, np);
+  k_tile_scatter<real, D><<<(unsigned)((np + TB_ITEMS - 1) / TB_ITEMS), TB_THREADS, 0, s>>>(src, dst, keys, cursor, np);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }

@@ -296,6 +296,13 @@ class Run:
         check(lib().sg_pic_stage_times(self.h, ms.ctypes.data, 6), "sg_pic_stage_times")
         return dict(zip(["push", "sort", "deposit", "restrict", "solve", "combine"], ms.tolist()))
 
+    def tuning(self):
+        """Init-time autotuner record: solve variant and the compared timings (ms)."""
+        ms = np.zeros(9)
+        check(lib().sg_pic_stage_times(self.h, ms.ctypes.data, 9), "sg_pic_stage_times")
+        return {"solve_variant": "one-block-per-grid" if ms[6] == 1 else "per-axis-passes",
+                "passes_ms": float(ms[7]), "one_block_ms": float(ms[8])}
+
     def device_particles(self):
         o = L.sg_particles_out()
         check(lib().sg_pic_device_particles(self.h, C.byref(o)), "sg_pic_device_particles")
@@ -346,6 +353,11 @@ class Server:
         check(lib().sg_serve_submit(self.h, C.byref(req), C.byref(t)), "sg_serve_submit")
         self.meta[t.value] = (d, int(ucols[0].shape[0]), dt_np)
         return t.value
+
+    def set_mode(self, mode):
+        """"batched" (one graph per tick over all runs) or "plain" (per run, per grid launches)."""
+        m = L.SG_SERVE_BATCHED if mode in ("batched", L.SG_SERVE_BATCHED) else L.SG_SERVE_PLAIN
+        check(lib().sg_serve_set_mode(self.h, m), "sg_serve_set_mode")
 
     def tick(self):
         a = C.c_int()
