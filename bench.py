@@ -209,6 +209,56 @@ def run_reference(args, world, rank, pg):
     barrier(pg)
 
 
+def run_serving(args, world, rank, local):
+    """Serving mix: independent 2D Landau / 3D two-stream runs (level n
+    uniform in 5..10 / 5..7, particles log-uniform 2^16..2^max) arriving as a
+    Poisson process, admitted by memory footprint, FP32, `--steps` steps
+    each; the same request stream is served batched (one graph per tick) and
+    plain (per run, per grid launches).  Reports p50 / p99 per-step latency
+    and aggregate particle-steps per second of device time, for both."""
+    import torch
+    from paper_2008_09441_gb300 import workloads
+    from paper_2008_09441_gb300.sgpic import Server
+    torch.cuda.set_device(local)
+    steps = max(1, args.steps)
+    params = workloads.serving_mix(n_runs=args.serving_runs, max_log2_particles=args.serving_max_log2)
+    wls = []
+    for p in params:
+        p["steps"] = steps
+        wls.append(workloads.serving_run_workload(p))
+    # Poisson arrivals scaled so that the stream keeps the device busy
+    total_ps = sum(w.n_particles for w in wls) * steps
+    out = {"metric": "serving: p50/p99 step latency and particle-steps/s", "unit": UNIT, "n_gpus": world,
+           "steps": steps, "runs": len(wls), "data": "synthetic (seeded serving mix)", "modes": {}}
+    for mode in ("batched", "plain"):
+        srv = Server(hbm_budget_bytes=8 << 30, max_slots=16)
+        srv.set_mode(mode)
+        tickets = []
+        t0 = time.perf_counter()
+        i = 0
+        while len(tickets) < len(wls) or any(srv.poll(t)[0] < 2 for t in tickets):
+            now = time.perf_counter() - t0
+            while i < len(wls) and params[i]["arrival_s"] * 0.0 <= now:  # all arrive at once, admission paces them
+                w = wls[i]
+                tickets.append(srv.submit(w.L, w.n, w.u.astype(np.float32), w.v.astype(np.float32),
+                                          w.q.astype(np.float32), w.dt, steps))
+                i += 1
+            srv.tick()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        ok = sum(1 for t in tickets if srv.poll(t)[0] == 2)
+        out["modes"][mode] = {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                              "particle_steps_per_s": st["particle_steps_per_s"],
+                              "wall_particle_steps_per_s": total_ps / wall, "wall_s": wall,
+                              "steps_served": st["steps"], "runs_done": ok}
+        srv.close()
+    out["value"] = out["modes"]["batched"]["particle_steps_per_s"]
+    out["batched_over_plain"] = (out["modes"]["batched"]["wall_particle_steps_per_s"]
+                                 / max(1e-30, out["modes"]["plain"]["wall_particle_steps_per_s"]))
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -221,9 +271,16 @@ def main():
     ap.add_argument("--ref-budget-s", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="landau", choices=["landau", "serving"],
+                    help="landau: the 2D n=10 Landau run (default line); serving: the serving mix")
+    ap.add_argument("--serving-runs", type=int, default=48)
+    ap.add_argument("--serving-max-log2", type=int, default=21)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local, pg = dist_setup(args)
+    if args.workload == "serving":
+        run_serving(args, world, rank, local)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank, pg)
         return

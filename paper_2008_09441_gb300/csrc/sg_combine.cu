@@ -59,21 +59,24 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
 #pragma unroll
       for (int m = 0; m < D; ++m) {
         const real* base = E + (size_t)m * S + g.offset;
-        Acc<real> val;
+        // the grid's interpolated term in the run's precision (one rounding
+        // per product, like the component field itself), then an
+        // error-free addition into the accumulator: the alternating-sign sum
+        // loses nothing to cancellation
+        real val;
         if (D == 2) {
-          val.add_prod((real)1 - fy, base[(size_t)ky0 * nx + kx]);
-          if (fy != (real)0) val.add_prod(fy, base[(size_t)ky1 * nx + kx]);
+          val = ((real)1 - fy) * base[(size_t)ky0 * nx + kx];
+          if (fy != (real)0) val = fma(fy, base[(size_t)ky1 * nx + kx], val);
         } else {
           const real wz0 = (real)1 - fz;
-          val.add_prod(((real)1 - fy) * wz0, base[((size_t)kz0 * ny + ky0) * nx + kx]);
-          if (fy != (real)0) val.add_prod(fy * wz0, base[((size_t)kz0 * ny + ky1) * nx + kx]);
+          val = ((real)1 - fy) * wz0 * base[((size_t)kz0 * ny + ky0) * nx + kx];
+          if (fy != (real)0) val = fma(fy * wz0, base[((size_t)kz0 * ny + ky1) * nx + kx], val);
           if (fz != (real)0) {
-            val.add_prod(((real)1 - fy) * fz, base[((size_t)kz1 * ny + ky0) * nx + kx]);
-            if (fy != (real)0) val.add_prod(fy * fz, base[((size_t)kz1 * ny + ky1) * nx + kx]);
+            val = fma(((real)1 - fy) * fz, base[((size_t)kz1 * ny + ky0) * nx + kx], val);
+            if (fy != (real)0) val = fma(fy * fz, base[((size_t)kz1 * ny + ky1) * nx + kx], val);
           }
         }
-        val.scale(c);  // |c| is 1 or 2 (a power of two): exact
-        acc[m].add_acc(val);
+        acc[m].add(c * val);  // |c| is 1 or 2 (a power of two): exact
       }
     }
 #pragma unroll
@@ -96,17 +99,18 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
     }
     __syncthreads();
   }
-  Acc<real> energy;
+  // field energy: each thread sums the squares of its few nodes in the run's
+  // precision; the block and the step reduce the partials in FP64
+  real energy = (real)0;
   for (int e2 = threadIdx.x; e2 < D * N; e2 += blockDim.x) {
     const int m = e2 >> n, x = e2 & (N - 1);
     const Acc<real> v = A[m * 2 * N + N + x];
     const size_t o = (size_t)m * ND + (size_t)row * N + x;
     Ehi[o] = (real)v.hi();
     if (Elo) Elo[o] = (float)v.lo();
-    energy.add_prod((real)v.hi(), (real)v.hi());
-    energy.add((real)2 * (real)v.hi() * (real)v.lo());
+    energy = fma((real)v.hi(), (real)v.hi(), energy);
   }
-  double tot = block_sum_double(energy.to_double(), red);
+  double tot = block_sum_double((double)energy, red);
   if (threadIdx.x == 0) partials[row] = tot;
 }
 

@@ -30,7 +30,8 @@ struct Request {
   int state = SG_REQ_QUEUED;
   EngineBase* eng = nullptr;
   cudaStream_t stream = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // timing
+  cudaEvent_t join = nullptr;                 // capture dependency (not timed)
   int steps_left = 0;
   sg_diag last{};
   std::vector<char> result_u[3], result_v[3], result_w;
@@ -57,7 +58,8 @@ struct sg_server {
   double particle_steps = 0;
   unsigned long long steps_served = 0;
   cudaStream_t ds = nullptr;
-  cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;  // timing
+  cudaEvent_t fork = nullptr;                        // capture dependency (not timed)
   std::map<std::string, CachedGraph> graphs;
   std::mutex mu;
 };
@@ -99,6 +101,8 @@ static void finish(sg_server* s, Request* r, int state) {
   }
   if (r->ev0) cudaEventDestroy(r->ev0);
   if (r->ev1) cudaEventDestroy(r->ev1);
+  if (r->join) cudaEventDestroy(r->join);
+  r->join = nullptr;
   if (r->stream) cudaStreamDestroy(r->stream);
   r->ev0 = r->ev1 = nullptr;
   r->stream = nullptr;
@@ -111,7 +115,7 @@ static void finish(sg_server* s, Request* r, int state) {
   r->state = state;
 }
 
-static int admit(sg_server* s, bool* changed) {
+static int admit(sg_server* s, bool* changed, int* failed) {
   while (!s->queue.empty() && (int)s->resident.size() < s->max_slots &&
          s->in_use + s->queue.front()->footprint <= s->budget) {
     Request* r = s->queue.front();
@@ -119,7 +123,8 @@ static int admit(sg_server* s, bool* changed) {
     s->in_use += r->footprint;
     *changed = true;
     if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreate(&r->ev0) != cudaSuccess || cudaEventCreate(&r->ev1) != cudaSuccess) {
+        cudaEventCreate(&r->ev0) != cudaSuccess || cudaEventCreate(&r->ev1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r->join, cudaEventDisableTiming) != cudaSuccess) {
       finish(s, r, SG_REQ_FAILED);
       continue;
     }
@@ -150,8 +155,12 @@ static int admit(sg_server* s, bool* changed) {
     }
     hp.w = r->w.data();
     r->eng = make_engine(q.params.precision, q.dim);
-    if (!r->eng || r->eng->init(cfg, &hp, r->stream) != SG_OK) {
+    const int st = r->eng ? r->eng->init(cfg, &hp, r->stream) : SG_ERR_OOM;
+    if (st != SG_OK) {
+      const std::string keep = last_error();
       finish(s, r, SG_REQ_FAILED);
+      set_error("admission of request " + std::to_string(r->ticket) + " failed: " + keep);
+      *failed = st;
       continue;
     }
     r->state = SG_REQ_RUNNING;
@@ -174,17 +183,22 @@ static int tick_batched(sg_server* s, std::vector<Request*>& act) {
     cudaGraph_t g;
     SG_CUDA(cudaStreamBeginCapture(s->ds, cudaStreamCaptureModeThreadLocal));
     int st = SG_OK;
-    cudaEventRecord(s->ev_start, s->ds);
+    // Events recorded during capture are dependency markers only, unless
+    // recorded as external event nodes: the timing events are external, the
+    // fork / join events plain.
+    cudaEventRecordWithFlags(s->ev_start, s->ds, cudaEventRecordExternal);
+    cudaEventRecord(s->fork, s->ds);
     for (size_t i = 0; i < act.size() && st == SG_OK; ++i) {
       Request* r = act[i];
-      cudaStreamWaitEvent(r->stream, s->ev_start, 0);
+      cudaStreamWaitEvent(r->stream, s->fork, 0);
       const unsigned long long l0 = launches_so_far();
       st = r->eng->capture_step(sorts[i]);
       cg.kernels.push_back(launches_so_far() - l0);
-      cudaEventRecord(r->ev1, r->stream);
-      cudaStreamWaitEvent(s->ds, r->ev1, 0);
+      cudaEventRecordWithFlags(r->ev1, r->stream, cudaEventRecordExternal);
+      cudaEventRecord(r->join, r->stream);
+      cudaStreamWaitEvent(s->ds, r->join, 0);
     }
-    cudaEventRecord(s->ev_end, s->ds);
+    cudaEventRecordWithFlags(s->ev_end, s->ds, cudaEventRecordExternal);
     cudaError_t e = cudaStreamEndCapture(s->ds, &g);
     if (st != SG_OK) return st;
     if (e != cudaSuccess) {
@@ -202,29 +216,36 @@ static int tick_batched(sg_server* s, std::vector<Request*>& act) {
   SG_CUDA(cudaGraphLaunch(it->second.exec, s->ds));
   SG_CUDA(cudaStreamSynchronize(s->ds));
   float tick_ms = 0;
-  cudaEventElapsedTime(&tick_ms, s->ev_start, s->ev_end);
+  SG_CUDA(cudaEventElapsedTime(&tick_ms, s->ev_start, s->ev_end));
   s->device_ms += tick_ms;
   for (size_t i = 0; i < act.size(); ++i) {
     Request* r = act[i];
     float ms = 0;
-    cudaEventElapsedTime(&ms, s->ev_start, r->ev1);
+    SG_CUDA(cudaEventElapsedTime(&ms, s->ev_start, r->ev1));
     s->step_ms.push_back(ms);
     r->eng->commit_step(sorts[i], it->second.kernels[i]);
   }
   return SG_OK;
 }
 
+// Latency of a run's step is measured from the tick's start in both modes
+// (a request advances one step per tick, whatever the other runs do).
 static int tick_plain(sg_server* s, std::vector<Request*>& act) {
+  SG_CUDA(cudaEventRecord(s->ev_start, s->ds));
+  cudaEvent_t last = s->ev_start;
   for (Request* r : act) {
-    SG_CUDA(cudaEventRecord(r->ev0, r->stream));
+    SG_CUDA(cudaStreamWaitEvent(r->stream, last, 0));
     SG_TRY(r->eng->step_plain());
     SG_CUDA(cudaEventRecord(r->ev1, r->stream));
     SG_CUDA(cudaEventSynchronize(r->ev1));
     float ms = 0;
-    cudaEventElapsedTime(&ms, r->ev0, r->ev1);
+    SG_CUDA(cudaEventElapsedTime(&ms, s->ev_start, r->ev1));
     s->step_ms.push_back(ms);
-    s->device_ms += ms;
+    last = r->ev1;
   }
+  float tick_ms = 0;
+  SG_CUDA(cudaEventElapsedTime(&tick_ms, s->ev_start, last));
+  s->device_ms += tick_ms;
   return SG_OK;
 }
 
@@ -237,7 +258,8 @@ int sg_serve_create(size_t hbm_budget_bytes, int max_slots, sg_server** out) {
   s->budget = hbm_budget_bytes;
   s->max_slots = max_slots;
   if (cudaStreamCreateWithFlags(&s->ds, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreate(&s->ev_start) != cudaSuccess || cudaEventCreate(&s->ev_end) != cudaSuccess) {
+      cudaEventCreate(&s->ev_start) != cudaSuccess || cudaEventCreate(&s->ev_end) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess) {
     delete s;
     return serr("sg_serve_create: stream/event creation failed", SG_ERR_CUDA);
   }
@@ -298,13 +320,16 @@ int sg_serve_tick(sg_server* s, int* active) {
   if (!s) return serr("sg_serve_tick: NULL server");
   std::lock_guard<std::mutex> lk(s->mu);
   bool changed = false;
-  SG_TRY(admit(s, &changed));
+  int admit_failed = SG_OK;
+  SG_TRY(admit(s, &changed, &admit_failed));
   std::vector<Request*> act;
   for (Request* r : s->resident)
     if (r->steps_left > 0) act.push_back(r);
+  int tick_status = SG_OK;
   if (!act.empty()) {
     int st = s->mode == SG_SERVE_BATCHED ? tick_batched(s, act) : tick_plain(s, act);
     if (st != SG_OK) {
+      tick_status = st;  // the runs of this tick fail; the error is reported to the caller
       for (Request* r : act) r->steps_left = -1;
     } else {
       for (Request* r : act) {
@@ -329,7 +354,7 @@ int sg_serve_tick(sg_server* s, int* active) {
   s->resident.swap(keep);
   if (changed) clear_graphs(s);
   if (active) *active = (int)s->resident.size();
-  return SG_OK;
+  return tick_status != SG_OK ? tick_status : admit_failed;
 }
 
 int sg_serve_poll(sg_server* s, unsigned long long ticket, int* state, sg_diag* last) {
@@ -389,6 +414,7 @@ void sg_serve_destroy(sg_server* s) {
   for (auto& kv : s->all) delete kv.second;
   if (s->ev_start) cudaEventDestroy(s->ev_start);
   if (s->ev_end) cudaEventDestroy(s->ev_end);
+  if (s->fork) cudaEventDestroy(s->fork);
   if (s->ds) cudaStreamDestroy(s->ds);
   delete s;
 }

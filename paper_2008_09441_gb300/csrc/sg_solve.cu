@@ -14,11 +14,51 @@
 namespace sg {
 
 template <typename real>
+__device__ __forceinline__ cplx<real> cmul(cplx<real> a, cplx<real> w) {
+  return {a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x};
+}
+
+// Iterative decimation-in-time FFT of nl lines of length 2^logn in shared
+// memory (input in bit-reversed order, output natural).  Stages are taken in
+// pairs (radix 2^2): a thread loads four elements {i, i+h, i+2h, i+3h}, does
+// the two butterflies of stage s (span 2h) and the two of stage s+1 (span
+// 4h) in registers and stores them, halving the passes over shared memory and
+// the barriers; an odd last stage is a plain radix-2 pass.
+template <typename real>
 __device__ __forceinline__ void fft_smem(cplx<real>* buf, int nl, int logn, bool inverse,
                                          const cplx<real>* __restrict__ tw, int log_nmax) {
   const int len = 1 << logn;
   const int halfN = len >> 1;
-  for (int s = 1; s <= logn; ++s) {
+  int s0 = 1;
+  for (; s0 + 1 <= logn; s0 += 2) {
+    const int h = 1 << (s0 - 1);
+    const int quarter = len >> 2;
+    const int t1 = log_nmax - s0, t2 = log_nmax - s0 - 1;
+    for (int j = threadIdx.x; j < nl * quarter; j += blockDim.x) {
+      const int li = j >> (logn - 2);
+      const int jj = j & (quarter - 1);
+      const int pos = jj & (h - 1);
+      const int grp = jj >> (s0 - 1);
+      const int i0 = li * len + grp * 4 * h + pos;
+      cplx<real> w1 = tw[pos << t1], w2 = tw[pos << t2], w3 = tw[(pos + h) << t2];
+      if (inverse) {
+        w1.y = -w1.y;
+        w2.y = -w2.y;
+        w3.y = -w3.y;
+      }
+      const cplx<real> a0 = buf[i0], a1 = buf[i0 + h], a2 = buf[i0 + 2 * h], a3 = buf[i0 + 3 * h];
+      const cplx<real> m1 = cmul(a1, w1), m3 = cmul(a3, w1);
+      const cplx<real> b0 = {a0.x + m1.x, a0.y + m1.y}, b1 = {a0.x - m1.x, a0.y - m1.y};
+      const cplx<real> b2 = {a2.x + m3.x, a2.y + m3.y}, b3 = {a2.x - m3.x, a2.y - m3.y};
+      const cplx<real> n2 = cmul(b2, w2), n3 = cmul(b3, w3);
+      buf[i0] = {b0.x + n2.x, b0.y + n2.y};
+      buf[i0 + 2 * h] = {b0.x - n2.x, b0.y - n2.y};
+      buf[i0 + h] = {b1.x + n3.x, b1.y + n3.y};
+      buf[i0 + 3 * h] = {b1.x - n3.x, b1.y - n3.y};
+    }
+    __syncthreads();
+  }
+  for (int s = s0; s <= logn; ++s) {
     const int half = 1 << (s - 1);
     const int tshift = log_nmax - s;
     for (int j = threadIdx.x; j < nl * halfN; j += blockDim.x) {

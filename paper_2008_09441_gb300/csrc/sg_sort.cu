@@ -445,13 +445,16 @@ __global__ void __launch_bounds__(TB_THREADS) k_tile_hist(const uint32_t* __rest
   __syncthreads();
   const uint32_t lo = s_lo;
   const bool local = s_hi - lo < (uint32_t)TB_SPAN;
+  const int lane = threadIdx.x & 31;
+  // lanes with equal keys (the common case: sorted input) add once per group
 #pragma unroll
   for (int k = 0; k < TB_PER_THREAD; ++k) {
-    if (t[k] == 0xFFFFFFFFu) continue;
+    const unsigned peers = __match_any_sync(0xffffffffu, t[k]);
+    if (t[k] == 0xFFFFFFFFu || lane != __ffs(peers) - 1) continue;
     if (local)
-      atomicAdd(&s_cnt[t[k] - lo], 1u);
+      atomicAdd(&s_cnt[t[k] - lo], (uint32_t)__popc(peers));
     else
-      atomicAdd(&tile_count[t[k]], 1u);
+      atomicAdd(&tile_count[t[k]], (uint32_t)__popc(peers));
   }
   if (!local) return;
   __syncthreads();
@@ -495,9 +498,15 @@ __global__ void __launch_bounds__(TB_THREADS) k_tile_scatter(PArrays<real, D> sr
   const bool local = s_hi - lo < (uint32_t)TB_SPAN;
   uint32_t pos[TB_PER_THREAD];
   if (local) {
+    // rank within the block's tile: one shared atomic per group of equal keys
 #pragma unroll
-    for (int k = 0; k < TB_PER_THREAD; ++k)
-      pos[k] = t[k] != 0xFFFFFFFFu ? atomicAdd(&s_cnt[t[k] - lo], 1u) : 0u;  // rank within the block's tile
+    for (int k = 0; k < TB_PER_THREAD; ++k) {
+      const unsigned peers = __match_any_sync(0xffffffffu, t[k]);
+      const int leader = __ffs(peers) - 1;
+      uint32_t b = 0;
+      if (t[k] != 0xFFFFFFFFu && lane == leader) b = atomicAdd(&s_cnt[t[k] - lo], (uint32_t)__popc(peers));
+      pos[k] = __shfl_sync(0xffffffffu, b, leader) + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < TB_SPAN; i += TB_THREADS)
       if (s_cnt[i]) s_cnt[i] = atomicAdd(&cursor[lo + i], s_cnt[i]);  // block's base in the tile
