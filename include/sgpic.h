@@ -219,6 +219,25 @@ const char* sg_version(void);
 int sg_cell_sort(int precision, int dim, int level, size_t n, const void* const* u,
                  uint32_t* keys_sorted, uint32_t* perm, uint32_t* counts, void* stream);
 
+/* sg_cell_sort_static: the same sort, with the same arguments and results,
+ * for callers that must not allocate device memory -- for example code that
+ * runs under a device-memory budget owned by another allocator, or loops
+ * where an allocation or free could synchronise the device or fail under
+ * fragmentation.  (An engineering addition; the paper has no counterpart.)
+ * Its scratch is a fixed array of SG_CELL_SORT_STATIC_WORDS 32-bit words
+ * (about 3.2 MB) inside the library image, present on every GPU that loads
+ * the library until the process exits; no call allocates or frees device
+ * memory.  At most SG_CELL_SORT_STATIC_MAX positions: larger n returns
+ * SG_ERR_SIZE without doing any work.  The first call on a device looks up
+ * the array's device address with that device current (make that first call
+ * before any stream capture on the device).  All calls share the array:
+ * calls whose work can overlap on the GPU (different streams without
+ * ordering) race and must be serialised by the caller. */
+#define SG_CELL_SORT_STATIC_MAX 262144
+#define SG_CELL_SORT_STATIC_WORDS 803072
+int sg_cell_sort_static(int precision, int dim, int level, size_t n, const void* const* u,
+                        uint32_t* keys_sorted, uint32_t* perm, uint32_t* counts, void* stream);
+
 /* ---- serving: independent runs admitted as memory allows -----------------
  * A server keeps many independent runs resident on one GPU and advances all
  * of them together in batched launches (one launch per stage covers every

@@ -95,6 +95,7 @@ SIGNATURES = {
     "sg_last_error": (C.c_char_p, []),
     "sg_version": (C.c_char_p, []),
     "sg_cell_sort": (C.c_int, [C.c_int, C.c_int, C.c_int, _SZ, C.POINTER(_P), _P, _P, _P, _P]),
+    "sg_cell_sort_static": (C.c_int, [C.c_int, C.c_int, C.c_int, _SZ, C.POINTER(_P), _P, _P, _P, _P]),
     "sg_serve_create": (C.c_int, [_SZ, C.c_int, C.POINTER(_P)]),
     "sg_serve_set_mode": (C.c_int, [_P, C.c_int]),
     "sg_serve_submit": (C.c_int, [_P, C.POINTER(sg_request), C.POINTER(C.c_ulonglong)]),
