@@ -193,6 +193,41 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
 #pragma unroll
   for (int it = 0; it < DEP_ITEMS; ++it) {
     if (q[it] == (real)0) continue;
+    // fast path: all 2^d corners inside the window (the common case)
+    int lc[D];
+    bool fast = true;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      lc[m] = (c[it][m] - org[m]) & mask;
+      fast &= lc[m] + 1 < ext[m];
+    }
+    if (fast) {
+      const real qs = q[it] * scale;
+      const real w0[2] = {(real)1 - f[it][0], f[it][0]};
+      if (D == 2) {
+        const int base = lc[0] + ext[0] * lc[1];
+        const real a = qs * ((real)1 - f[it][1]), b = qs * f[it][1];
+        atomicAdd(&win[base], W::quantize(a * w0[0]));
+        atomicAdd(&win[base + 1], W::quantize(a * w0[1]));
+        atomicAdd(&win[base + ext[0]], W::quantize(b * w0[0]));
+        atomicAdd(&win[base + ext[0] + 1], W::quantize(b * w0[1]));
+      } else {
+        const int sy = ext[0], sz = ext[0] * ext[1 % D];
+        const int base = lc[0] + sy * lc[1 % D] + sz * lc[(D - 1)];
+        const real wy[2] = {(real)1 - f[it][1 % D], f[it][1 % D]};
+        const real wz[2] = {(real)1 - f[it][D - 1], f[it][D - 1]};
+#pragma unroll
+        for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+          for (int ky = 0; ky < 2; ++ky) {
+            const real a = qs * wz[kz] * wy[ky];
+            const int o = base + kz * sz + ky * sy;
+            atomicAdd(&win[o], W::quantize(a * w0[0]));
+            atomicAdd(&win[o + 1], W::quantize(a * w0[1]));
+          }
+      }
+      continue;
+    }
 #pragma unroll
     for (int corner = 0; corner < (1 << D); ++corner) {
       real wgt = q[it];

@@ -94,6 +94,8 @@ class Engine final : public EngineBase {
     if (sizeof(real) == 4) SG_TRY(alloc((void**)&Elo_, (size_t)D * ND_ * sizeof(float)));
     nrows_ = (int)(ND_ / (size_t)N_);
     SG_TRY(alloc((void**)&fe_partials_, (size_t)nrows_ * sizeof(double)));
+    SG_TRY(alloc((void**)&comb_counter_, sizeof(unsigned)));
+    SG_CUDA(cudaMemsetAsync(comb_counter_, 0, sizeof(unsigned), stream_));
     {
       std::vector<cplx<real>> tw(std::max(1, N_ / 2));
       for (int k = 0; k < N_ / 2; ++k) {
@@ -131,8 +133,7 @@ class Engine final : public EngineBase {
     SG_TRY(enqueue_sort());
     SG_TRY(enqueue_fields());
     SG_TRY(tune_solve());
-    SG_TRY(enqueue_combine());
-    SG_TRY(launch_finalize_step(fe_partials_, nrows_, nullptr, 0, fe_scale(), dd_, stream_));
+    SG_TRY(enqueue_combine(false));
     SG_TRY(enqueue_push(-0.5 * cfg_.dt, false, nullptr));
     SG_CUDA(cudaStreamSynchronize(stream_));
     step_ = 0;
@@ -300,8 +301,7 @@ class Engine final : public EngineBase {
     SG_TRY(build_grid_set(tau));
     SG_TRY(enqueue_restrict());
     SG_TRY(tune_solve());
-    SG_TRY(enqueue_combine());
-    SG_TRY(launch_finalize_step(fe_partials_, nrows_, nullptr, 0, fe_scale(), dd_, stream_));
+    SG_TRY(enqueue_combine(true, nullptr));
     return SG_OK;
   }
 
@@ -674,7 +674,11 @@ class Engine final : public EngineBase {
         for (int g = 0; g < ngrids_; ++g)
           if (gdesc_[g].l[0] == l) order.push_back(g);
       }
-      levels_.start[n_ + 1] = (int)order.size();
+      for (int l = n_ + 1; l < 18; ++l) levels_.start[l] = (int)order.size();
+      if ((int)order.size() > CB_MAX_GRIDS) {
+        set_error("too many component grids for the combination kernel");
+        return SG_ERR_UNSUPPORTED;
+      }
       int* dev = nullptr;
       SG_TRY(galloc((void**)&dev, order.size() * sizeof(int)));
       SG_CUDA(cudaMemcpyAsync(dev, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, stream_));
@@ -984,26 +988,36 @@ class Engine final : public EngineBase {
     return SG_OK;
   }
 
-  int enqueue_combine() {
-    return launch_combine<real, D>(grids_dev_, levels_, lmin_, E_arena_, S_, n_, Ehi_, Elo_, fe_partials_, stream_);
+  // The combination's last block also closes the step's FP64 bookkeeping
+  // (field energy, previous field energy, kinetic energy of the push when
+  // ke is given) unless finalize is false.
+  int enqueue_combine(bool finalize = true, const double* ke = nullptr) {
+    CombineFinal fin;
+    fin.active = finalize ? 1 : 0;
+    fin.ke_partials = ke;
+    fin.n_ke = nke_;
+    fin.fe_scale = fe_scale();
+    fin.dd = dd_;
+    fin.counter = comb_counter_;
+    return launch_combine<real, D>(grids_dev_, levels_, lmin_, E_arena_, S_, n_, Ehi_, Elo_, fe_partials_, fin,
+                                   stream_);
   }
 
-  int enqueue_restrict_solve_combine() {
+  int enqueue_restrict_solve_combine(const double* ke = nullptr) {
     SG_TRY(enqueue_restrict());
     SG_TRY(enqueue_solve());
-    return enqueue_combine();
+    return enqueue_combine(true, ke);
   }
 
-  int enqueue_fields() {
+  int enqueue_fields(const double* ke = nullptr) {
     SG_TRY(enqueue_deposit());
-    return enqueue_restrict_solve_combine();
+    return enqueue_restrict_solve_combine(ke);
   }
 
   int enqueue_step(bool do_sort) {
     SG_TRY(enqueue_push(cfg_.dt, true, ke_partials_, do_sort));
     if (do_sort) SG_TRY(sort_finish());
-    SG_TRY(enqueue_fields());
-    return launch_finalize_step(fe_partials_, nrows_, ke_partials_, nke_, fe_scale(), dd_, stream_);
+    return enqueue_fields(ke_partials_);
   }
 
   // Graph variants: (current particle set, sort or not).
@@ -1055,8 +1069,7 @@ class Engine final : public EngineBase {
     SG_CUDA(cudaEventRecord(ev_[4], stream_));
     SG_TRY(enqueue_solve());
     SG_CUDA(cudaEventRecord(ev_[5], stream_));
-    SG_TRY(enqueue_combine());
-    SG_TRY(launch_finalize_step(fe_partials_, nrows_, ke_partials_, nke_, fe_scale(), dd_, stream_));
+    SG_TRY(enqueue_combine(true, ke_partials_));
     SG_CUDA(cudaEventRecord(ev_[6], stream_));
     SG_CUDA(cudaEventSynchronize(ev_[6]));
     for (int i = 0; i < 6; ++i) {
@@ -1081,8 +1094,7 @@ class Engine final : public EngineBase {
     } else if (st != SG_OK && st != SG_ERR_RANGE) {
       return st;
     }
-    SG_TRY(enqueue_restrict_solve_combine());
-    SG_TRY(launch_finalize_step(fe_partials_, nrows_, ke_partials_, nke_, fe_scale(), dd_, stream_));
+    SG_TRY(enqueue_restrict_solve_combine(ke_partials_));
     launches_ += launches_so_far() - l0;
     return SG_OK;
   }
@@ -1114,6 +1126,7 @@ class Engine final : public EngineBase {
   unsigned long long* checksum_ = nullptr;
   double* ke_partials_ = nullptr;
   double* fe_partials_ = nullptr;
+  unsigned* comb_counter_ = nullptr;
   int nke_ = 0, nrows_ = 0;
 
   real* rho_reg_ = nullptr;

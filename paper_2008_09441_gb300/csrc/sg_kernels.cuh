@@ -153,15 +153,15 @@ int launch_fft_array_axis(cplx<real>* data, int D, int logn, int axis, bool inve
                           const cplx<real>* tw, int log_nmax, cudaStream_t s);
 
 // ---------------------------------------------------------------- combine
-// Grids grouped by their x level: grid[start[l] .. start[l+1]) have l_1 = l.
+// Grids grouped by their x level: grid[start[l] .. start[l+1]) have l_1 = l;
+// start[l] for l > n holds the total count.
+constexpr int CB_MAX_GRIDS = 128;
 struct LevelLists {
   int start[18];
   const int* grid;
 };
 
-template <typename real, int D>
-int launch_combine(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n,
-                   real* Ehi, float* Elo, double* energy_partials, cudaStream_t s);
+
 
 // ---------------------------------------------------------------- push
 template <typename real>
@@ -221,6 +221,23 @@ struct DevDiag {
 
 int launch_finalize_step(const double* fe_partials, int n_fe, const double* ke_partials, int n_ke,
                          double fe_scale, DevDiag* dd, cudaStream_t s);
+
+// Step bookkeeping closed by the last block of the combination kernel:
+// field energy from the per-row partials (scaled by fe_scale), the previous
+// field energy, and the kinetic energy from the push partials when given.
+struct CombineFinal {
+  int active;
+  int n_ke;
+  const double* ke_partials;
+  double fe_scale;
+  DevDiag* dd;
+  unsigned* counter;  // zero between launches; the last block resets it
+};
+
+template <typename real, int D>
+int launch_combine(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n,
+                   real* Ehi, float* Elo, double* energy_partials, const CombineFinal& fin,
+                   cudaStream_t s);
 
 template <typename real>
 int launch_grid_charges(const GridDesc* grids, int ngrids, const real* rho, const double* vol,

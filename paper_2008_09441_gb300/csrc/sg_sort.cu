@@ -86,8 +86,8 @@ int launch_keys_raw(const real* const* u, size_t np, int n, uint32_t* keys, uint
 }
 
 // ---------------------------------------------------------------- scan
-constexpr int SC_THREADS = 256;
-constexpr int SC_ITEMS = 16;
+constexpr int SC_THREADS = 1024;  // short serial runs per thread: the scan is latency-bound
+constexpr int SC_ITEMS = 4;
 constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
 
 size_t scan_block_sums_words(size_t m) { return (m + SC_TILE - 1) / SC_TILE + 1; }

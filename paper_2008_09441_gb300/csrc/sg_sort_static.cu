@@ -105,6 +105,10 @@ extern "C" int sg_cell_sort_static(int precision, int dim, int level, size_t n, 
   uint32_t* keys_alt = buf + 2 * kStaticMax;
   uint32_t* scr = buf + 3 * kStaticMax;
   const size_t scr_words = sort_scratch_words(n);
+  if (3 * kStaticMax + scr_words + 1 > (size_t)SG_CELL_SORT_STATIC_WORDS) {
+    set_error("sg_cell_sort_static: scan layout exceeds the fixed scratch capacity");
+    return SG_ERR_SIZE;
+  }
   unsigned* status = (unsigned*)(scr + scr_words);
   SG_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), s));  // the one word that must start at zero
   SortScratch sc;
