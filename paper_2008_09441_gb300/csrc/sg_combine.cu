@@ -1,7 +1,9 @@
 // Signed combination of the component fields on the regular nodes:
 //   E_comb(x_j) = sum_i c_i (P_i E_i)(x_j)
 // (eq. sparse_filter's c_i and P_i of eq. restriction, applied to the
-// fields).  One block per regular row (a y line in 2D, a (y, z) line in
+// fields).  Two kernels share the scheme below: a warp per line for lines of
+// up to 1024 nodes (values in registers), a block per line beyond.  Block
+// per line: one block per regular row (a y line in 2D, a (y, z) line in
 // 3D).  Every (level l, coarse x index k) pair of the row is an independent
 // work item: it interpolates, in the transverse axes, every grid whose x level
 // is l at the row's coordinate and adds c_i times the result (grids in a fixed
@@ -13,6 +15,312 @@
 #include "sg_kernels.cuh"
 
 namespace sg {
+
+// ---------------------------------------------------------------- warp-per-line combination
+//
+// For lines of at most 1024 nodes: one warp per (regular line, field
+// component), the level-l partial sum held in registers (2^l / 32
+// consecutive values per lane once 2^l >= 32, one value on 2^l lanes
+// before).  Each Horner step prolongs in place (even nodes copy, odd nodes
+// average the two neighbours, the right neighbour's first value by shuffle)
+// and adds the transverse interpolation of the grids whose x level is the
+// new level, read with vector loads.  No block barriers.
+//
+// FP32 path: the values are float pairs hi + lo carried without
+// renormalisation: every hi addition is an error-free two_sum whose error
+// goes to lo, so lo collects the exact rounding errors of hi and the pair
+// stays accurate to ~2^-48 of the largest intermediate, whatever the
+// cancellation; one final two_sum renormalises before the hi / lo planes
+// are stored.  FP64 path: plain double.
+template <typename real>
+struct CAcc;
+template <>
+struct CAcc<float> {
+  float hi, lo;
+  static __device__ __forceinline__ CAcc zero() { return {0.f, 0.f}; }
+  static __device__ __forceinline__ CAcc avg(const CAcc& a, const CAcc& b) {
+    const ff s = two_sum(a.hi, b.hi);
+    return {s.hi * 0.5f, (a.lo + b.lo + s.lo) * 0.5f};
+  }
+  static __device__ __forceinline__ CAcc add(const CAcc& a, const CAcc& b) {
+    const ff s = two_sum(a.hi, b.hi);
+    return {s.hi, a.lo + b.lo + s.lo};
+  }
+  static __device__ __forceinline__ CAcc first(float t) { return {t, 0.f}; }
+  static __device__ __forceinline__ CAcc add_term(const CAcc& a, float t) {
+    const ff s = two_sum(a.hi, t);
+    return {s.hi, a.lo + s.lo};
+  }
+  __device__ __forceinline__ CAcc shfl(int src) const {
+    return {__shfl_sync(0xffffffffu, hi, src), __shfl_sync(0xffffffffu, lo, src)};
+  }
+  __device__ __forceinline__ ff normalised() const { return two_sum(hi, lo); }
+};
+template <>
+struct CAcc<double> {
+  double v;
+  static __device__ __forceinline__ CAcc zero() { return {0.0}; }
+  static __device__ __forceinline__ CAcc avg(const CAcc& a, const CAcc& b) { return {(a.v + b.v) * 0.5}; }
+  static __device__ __forceinline__ CAcc add(const CAcc& a, const CAcc& b) { return {a.v + b.v}; }
+  static __device__ __forceinline__ CAcc first(double t) { return {t}; }
+  static __device__ __forceinline__ CAcc add_term(const CAcc& a, double t) { return {a.v + t}; }
+  __device__ __forceinline__ CAcc shfl(int src) const { return {__shfl_sync(0xffffffffu, v, src)}; }
+};
+
+// Transverse interpolation weights and coarse-row offsets of one grid at
+// regular line (y, z): the 2^(d-1) coarse x-lines that bracket the line,
+// each weight times the grid's coefficient (dyadic products: exact).
+template <typename real, int D>
+struct RowTerm {
+  int off[1 << (D - 1)];
+  real w[1 << (D - 1)];
+};
+
+template <typename real, int D>
+__device__ __forceinline__ RowTerm<real, D> row_term(const GridDesc& g, int n, int y, int z) {
+  RowTerm<real, D> t;
+  const int nx = 1 << g.l[0];
+  const int ry = n - g.l[1];
+  const int ny = 1 << g.l[1];
+  const int ky0 = y >> ry;
+  const int ky1 = (ky0 + 1) & (ny - 1);
+  const real c = (real)g.coeff;
+  const real fy = (real)(y & ((1 << ry) - 1)) * ((real)1 / (real)(1 << ry));
+  if (D == 2) {
+    t.off[0] = g.offset + ky0 * nx;
+    t.off[(1 << (D - 1)) - 1] = g.offset + ky1 * nx;
+    t.w[0] = c * ((real)1 - fy);
+    t.w[(1 << (D - 1)) - 1] = c * fy;
+  } else {
+    const int rz = n - g.l[D - 1];
+    const int nz = 1 << g.l[D - 1];
+    const int kz0 = z >> rz;
+    const int kz1 = (kz0 + 1) & (nz - 1);
+    const real fz = (real)(z & ((1 << rz) - 1)) * ((real)1 / (real)(1 << rz));
+    constexpr int R = 1 << (D - 1);
+    t.off[0] = g.offset + (kz0 * ny + ky0) * nx;
+    t.off[1 % R] = g.offset + (kz0 * ny + ky1) * nx;
+    t.off[2 % R] = g.offset + (kz1 * ny + ky0) * nx;
+    t.off[3 % R] = g.offset + (kz1 * ny + ky1) * nx;
+    t.w[0] = c * (((real)1 - fy) * ((real)1 - fz));
+    t.w[1 % R] = c * (fy * ((real)1 - fz));
+    t.w[2 % R] = c * (((real)1 - fy) * fz);
+    t.w[3 % R] = c * (fy * fz);
+  }
+  return t;
+}
+
+// Adds, to the K consecutive values T[0..K) at x index x0.. (K and x0
+// multiples of 4), c_i times the transverse interpolation of every grid of
+// x level `level`; the grids' row terms come from this warp's shared-memory
+// table.  Grid by grid, all of a grid's loads first (one latency per grid).
+template <typename real, int D, int K>
+__device__ __forceinline__ void add_level_terms(CAcc<real>* T, const RowTerm<real, D>* rt_tab, const int* lstart,
+                                                int level, const real* __restrict__ Em, int x0) {
+  constexpr int R = 1 << (D - 1);
+  for (int gi = lstart[level]; gi < lstart[level + 1]; ++gi) {
+    const RowTerm<real, D> rt = rt_tab[gi];
+    real t[K];
+#pragma unroll
+    for (int k = 0; k < K; k += 4) {
+      const V4<real> a = ld4(Em + rt.off[0] + x0 + k);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t[k + q] = rt.w[0] * a.x[q];
+    }
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+#pragma unroll
+      for (int k = 0; k < K; k += 4) {
+        const V4<real> a = ld4(Em + rt.off[r] + x0 + k);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) t[k + q] = fma(rt.w[r], a.x[q], t[k + q]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) T[k] = CAcc<real>::add_term(T[k], t[k]);
+  }
+}
+
+// The same at one x index (lines with fewer than 4 values per lane).
+template <typename real, int D>
+__device__ __forceinline__ CAcc<real> level_term1(const RowTerm<real, D>* rt_tab, const int* lstart, int level,
+                                                  const real* __restrict__ Em, int x) {
+  constexpr int R = 1 << (D - 1);
+  CAcc<real> acc = CAcc<real>::zero();
+  bool first = true;
+  for (int gi = lstart[level]; gi < lstart[level + 1]; ++gi) {
+    const RowTerm<real, D> rt = rt_tab[gi];
+    real t = rt.w[0] * Em[rt.off[0] + x];
+#pragma unroll
+    for (int r = 1; r < R; ++r) t = fma(rt.w[r], Em[rt.off[r] + x], t);
+    acc = first ? CAcc<real>::first(t) : CAcc<real>::add_term(acc, t);
+    first = false;
+  }
+  return acc;
+}
+
+// One Horner step in the register phase: Vc values per lane -> 2 Vc, then
+// add the new level's terms; recurse up to level n (2 Vc <= VMAX).
+template <typename real, int D, int Vc, int VMAX>
+struct CombLevels {
+  static __device__ __forceinline__ void run(CAcc<real>* T, int& level, int n, int lane,
+                                             const RowTerm<real, D>* rt_tab, const int* lstart,
+                                             const real* __restrict__ Em) {
+    if constexpr (2 * Vc <= VMAX) {
+      const CAcc<real> right = T[0].shfl((lane + 1) & 31);
+#pragma unroll
+      for (int i = Vc - 1; i >= 0; --i) {  // in place, high to low
+        const CAcc<real> nxt = (i == Vc - 1) ? right : T[i + 1];
+        T[2 * i + 1] = CAcc<real>::avg(T[i], nxt);
+        T[2 * i] = T[i];
+      }
+      ++level;
+      constexpr int K = 2 * Vc;
+      if constexpr (K >= 4) {
+        add_level_terms<real, D, K>(T, rt_tab, lstart, level, Em, lane * K);
+      } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          T[k] = CAcc<real>::add(T[k], level_term1<real, D>(rt_tab, lstart, level, Em, lane * K + k));
+      }
+      if (level < n) CombLevels<real, D, 2 * Vc, VMAX>::run(T, level, n, lane, rt_tab, lstart, Em);
+    }
+  }
+};
+
+// Shared by both combination kernels: the last block to finish reduces the
+// energy partials (and the push's kinetic-energy partials) in FP64, in a
+// fixed order, so the step needs no separate bookkeeping launch.
+__device__ __forceinline__ void combine_finalize(const double* partials, int n_part, const CombineFinal& fin,
+                                                 double* red) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(fin.counter, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n_part; i += blockDim.x) a += __ldcg(partials + i);
+  const double fe = block_sum_double(a, red);
+  double b = 0.0;
+  if (fin.ke_partials)
+    for (int i = threadIdx.x; i < fin.n_ke; i += blockDim.x) b += __ldcg(fin.ke_partials + i);
+  const double ke = block_sum_double(b, red);
+  if (threadIdx.x == 0) {
+    DevDiag* dd = fin.dd;
+    dd->field_energy_prev = dd->field_energy;
+    dd->field_energy = fe * fin.fe_scale;
+    if (fin.ke_partials) dd->kinetic_energy = ke;
+    *fin.counter = 0u;
+  }
+}
+
+template <typename real, int D, int V>
+__global__ void __launch_bounds__(256) k_combine_warp(const GridDesc* __restrict__ grids, LevelLists ll, int lmin,
+                                                      const real* __restrict__ E, size_t S, int n,
+                                                      real* __restrict__ Ehi, float* __restrict__ Elo,
+                                                      double* __restrict__ partials, const CombineFinal fin) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  const int N = 1 << n;
+  const int rows = D == 2 ? N : N * N;
+  const size_t ND = (size_t)rows * N;
+  const int wib = threadIdx.x >> 5;
+  const int task = blockIdx.x * (blockDim.x >> 5) + wib;  // (row, component)
+  const int lane = threadIdx.x & 31;
+  const int m = task % D, row = task / D;
+  const int y = row & (N - 1);
+  const int z = D == 3 ? (row >> n) : 0;
+  const real* Em = E + (size_t)m * S;
+  __shared__ int s_start[18];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < 18; ++i) s_start[i] = ll.start[i];  // constant indices: no local copy
+  }
+  const int ngl = ll.start[17];
+  RowTerm<real, D>* rt_tab = reinterpret_cast<RowTerm<real, D>*>(smem_raw) + (size_t)wib * ngl;
+  for (int gi = lane; gi < ngl; gi += 32) rt_tab[gi] = row_term<real, D>(grids[ll.grid[gi]], n, y, z);
+  __syncthreads();
+  real energy = (real)0;
+  if (row < rows) {
+    CAcc<real> T[V];
+    // coarse phase: one value on 2^level lanes, up to 32 values; the terms
+    // of all coarse levels are read first (independent loads)
+    int level = min(lmin, min(n, 5));
+    const int ltop = min(n, 5);
+    CAcc<real> sc[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const int l = level + j;
+      sc[j] = (l <= ltop && lane < (1 << l)) ? level_term1<real, D>(rt_tab, s_start, l, Em, lane)
+                                             : CAcc<real>::zero();
+    }
+    T[0] = sc[0];
+#pragma unroll
+    for (int j = 1; j < 6; ++j) {
+      if (level < ltop) {
+        const int h = 1 << level;
+        const int k = lane >> 1;
+        const CAcc<real> a = T[0].shfl(k & (h - 1));
+        const CAcc<real> b = T[0].shfl((k + 1) & (h - 1));
+        T[0] = (lane & 1) ? CAcc<real>::avg(a, b) : a;
+        ++level;
+        if (lane < (1 << level)) T[0] = CAcc<real>::add(T[0], sc[j]);
+      }
+    }
+    // register phase: 2^level / 32 consecutive values per lane
+    if (level < n) CombLevels<real, D, 1, V>::run(T, level, n, lane, rt_tab, s_start, Em);
+    const size_t o0 = (size_t)m * ND + (size_t)row * N;
+    if constexpr (sizeof(real) == 4) {
+      if constexpr (V >= 4) {
+#pragma unroll
+        for (int k = 0; k < V; k += 4) {
+          ff v[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            v[q] = T[k + q].normalised();
+            energy = fmaf(v[q].hi, v[q].hi, energy);
+          }
+          const size_t o = o0 + (size_t)lane * V + k;
+          *reinterpret_cast<float4*>(Ehi + o) = make_float4(v[0].hi, v[1].hi, v[2].hi, v[3].hi);
+          *reinterpret_cast<float4*>(Elo + o) = make_float4(v[0].lo, v[1].lo, v[2].lo, v[3].lo);
+        }
+      } else {
+        const int per = N >= 32 ? V : 1;
+        if (N >= 32 || lane < N) {
+#pragma unroll
+          for (int k = 0; k < V; ++k)
+            if (k < per) {
+              const ff v = T[k].normalised();
+              Ehi[o0 + (size_t)lane * per + k] = v.hi;
+              Elo[o0 + (size_t)lane * per + k] = v.lo;
+              energy = fmaf(v.hi, v.hi, energy);
+            }
+        }
+      }
+    } else {
+      const int per = N >= 32 ? V : 1;
+      if (N >= 32 || lane < N) {
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+          if (k < per) {
+            Ehi[o0 + (size_t)lane * per + k] = T[k].v;
+            energy = fma(T[k].v, T[k].v, energy);
+          }
+      }
+    }
+  }
+  const double tot = warp_sum((double)energy);
+  if (lane == 0 && row < rows) partials[task] = tot;
+  if (!fin.active) return;
+  combine_finalize(partials, rows * D, fin, red);
+}
+
+// ---------------------------------------------------------------- block-per-line combination (lines > 1024)
 
 template <typename real, int D>
 __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ grids, LevelLists ll, int lmin,
@@ -125,39 +433,47 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
   double tot = block_sum_double((double)energy, red);
   if (threadIdx.x == 0) partials[row] = tot;
   if (!fin.active) return;
+  combine_finalize(partials, (int)gridDim.x, fin, red);
+}
 
-  // The last block to finish reduces every row's partial (and the push's
-  // kinetic-energy partials) in FP64, in a fixed order, so the step needs no
-  // separate bookkeeping launch.
-  __shared__ int s_last;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned t = atomicAdd(fin.counter, 1u);
-    s_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  double a = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) a += __ldcg(partials + i);
-  const double fe = block_sum_double(a, red);
-  double b = 0.0;
-  if (fin.ke_partials)
-    for (int i = threadIdx.x; i < fin.n_ke; i += blockDim.x) b += __ldcg(fin.ke_partials + i);
-  const double ke = block_sum_double(b, red);
-  if (threadIdx.x == 0) {
-    DevDiag* dd = fin.dd;
-    dd->field_energy_prev = dd->field_energy;
-    dd->field_energy = fe * fin.fe_scale;
-    if (fin.ke_partials) dd->kinetic_energy = ke;
-    *fin.counter = 0u;
-  }
+template <typename real, int D, int V>
+static int launch_combine_warp(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n,
+                               real* Ehi, float* Elo, double* energy_partials, const CombineFinal& fin,
+                               cudaStream_t s) {
+  const int N = 1 << n;
+  const long long tasks = (long long)(D == 2 ? N : N * N) * D;
+  const int warps = 8;
+  const unsigned blocks = (unsigned)((tasks + warps - 1) / warps);
+  const size_t smem = (size_t)warps * ll.start[17] * sizeof(RowTerm<real, D>);
+  k_combine_warp<real, D, V><<<blocks, 32 * warps, smem, s>>>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials,
+                                                              fin);
+  SG_CHECK_LAUNCH();
+  return SG_OK;
 }
 
 template <typename real, int D>
 int launch_combine(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n, real* Ehi,
                    float* Elo, double* energy_partials, const CombineFinal& fin, cudaStream_t s) {
   const int N = 1 << n;
+  switch (N) {  // lines of up to 1024 nodes: warp per line, values in registers
+    case 4:
+    case 8:
+    case 16:
+    case 32:
+      return launch_combine_warp<real, D, 1>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+    case 64:
+      return launch_combine_warp<real, D, 2>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+    case 128:
+      return launch_combine_warp<real, D, 4>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+    case 256:
+      return launch_combine_warp<real, D, 8>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+    case 512:
+      return launch_combine_warp<real, D, 16>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+    case 1024:
+      return launch_combine_warp<real, D, 32>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+    default:
+      break;
+  }
   unsigned rows = (unsigned)(D == 2 ? N : N * N);
   size_t smem = (size_t)D * 2 * N * sizeof(Acc<real>);
   static bool attr_set = false;

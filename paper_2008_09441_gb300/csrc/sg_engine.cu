@@ -1,5 +1,6 @@
 // Engine<real, D>: one sparse-grid PIC run on one GPU.
 #include <algorithm>
+#include <climits>
 #include <map>
 #include <set>
 
@@ -93,7 +94,7 @@ class Engine final : public EngineBase {
     SG_TRY(alloc((void**)&Ehi_, (size_t)D * ND_ * sizeof(real)));
     if (sizeof(real) == 4) SG_TRY(alloc((void**)&Elo_, (size_t)D * ND_ * sizeof(float)));
     nrows_ = (int)(ND_ / (size_t)N_);
-    SG_TRY(alloc((void**)&fe_partials_, (size_t)nrows_ * sizeof(double)));
+    SG_TRY(alloc((void**)&fe_partials_, (size_t)nrows_ * D * sizeof(double)));  // per (line, component)
     SG_TRY(alloc((void**)&comb_counter_, sizeof(unsigned)));
     SG_CUDA(cudaMemsetAsync(comb_counter_, 0, sizeof(unsigned), stream_));
     {
@@ -702,21 +703,26 @@ class Engine final : public EngineBase {
 
   struct Pass {
     LineJob* dev = nullptr;
-    int njobs = 0, nblocks = 0, smem = 0;
+    int njobs = 0, nblocks = 0, lpb = 1, vpl = 1, smem = 0;
   };
   struct FPass {
     FftJob* dev = nullptr;
     int kind = 0, njobs = 0, nblocks = 0, smem = 0;
   };
 
-  // Restriction: axis by axis, each pass restricting every distinct prefix
-  // of the grid set's level vectors.
+  // Restriction: axis by axis.  Pass a restricts, along axis a, one source
+  // array per distinct prefix (l_0 .. l_{a-1}) of the grid set's level
+  // vectors, to every level l_a that some grid with that prefix needs.  All
+  // arrays keep the natural layout (x fastest): the source of pass a is
+  // [outer][N][inner] with inner = the already restricted axes and outer =
+  // the axes not reached yet; the last pass writes the component grids.
   int build_restrict_jobs() {
     rpasses_.clear();
-    const int CAP = 8192;  // reals of shared memory per block for the pyramid
-    // level prefixes: pass a produces arrays keyed by (l_0..l_a)
     std::map<std::vector<int>, real*> prev;  // arrays of the previous pass
     prev[{}] = rho_reg_;
+    int S = N_ + ((N_ >> 5) << 2);  // tile row: 4 padding words per 32, = 4 (mod 32)
+    S = (S + 3) & ~3;
+    while ((S & 31) != 4) S += 4;
     for (int a = 0; a < D; ++a) {
       std::map<std::vector<int>, std::set<int>> targets;  // prefix -> levels along axis a
       for (auto& g : grids_) {
@@ -725,31 +731,26 @@ class Engine final : public EngineBase {
       }
       std::vector<LineJob> jobs;
       std::map<std::vector<int>, real*> next;
-      int blocks = 0, smem = 0;
+      long long total_lines = 0;
       for (auto& kv : targets) {
         LineJob J;
         std::memset(&J, 0, sizeof(J));
         J.src = prev.at(kv.first);
-        for (int m = 0; m < 3; ++m) J.dims[m] = 1;
-        for (int m = 0; m < D; ++m) J.dims[m] = m < a ? (1 << kv.first[m]) : N_;
-        J.axis = a;
         J.top = n_;
-        long long lines = 1;
-        for (int m = 0; m < D; ++m)
-          if (m != a) lines *= J.dims[m];
-        J.lines = (int)lines;
-        int C = std::max(1, CAP / (2 * N_));
-        if (C > lines) C = (int)lines;
-        J.lines_per_block = C;
-        J.block_begin = blocks;
-        blocks += (int)((lines + C - 1) / C);
-        smem = std::max(smem, (int)(C * 2 * N_ * sizeof(real)));
-        J.ntargets = 0;
+        long long inner = 1, outer = 1;
+        for (int m = 0; m < a; ++m) inner <<= kv.first[m];
+        for (int m = a + 1; m < D; ++m) outer *= N_;
+        J.inner = (int)inner;
+        J.outer = (int)outer;
+        J.tile_stride = S;
+        J.tmin = n_;
         for (int tl : kv.second) {
-          if (J.ntargets >= LJ_MAX_TARGETS) {
-            set_error("restriction: too many target levels");
+          if (tl < 0 || tl >= RJ_LEVELS) {
+            set_error("restriction: level out of range");
             return SG_ERR_UNSUPPORTED;
           }
+          J.tmask |= 1 << tl;
+          J.tmin = std::min(J.tmin, tl);
           std::vector<int> key = kv.first;
           key.push_back(tl);
           real* dst;
@@ -757,21 +758,39 @@ class Engine final : public EngineBase {
             int gi = find_grid(key);
             dst = rho_arena_ + gdesc_[gi].offset;
           } else {
-            size_t cnt = (size_t)(1 << tl);
-            for (int m = 0; m < D; ++m) cnt *= (m < a ? (size_t)(1 << kv.first[m]) : (m == a ? 1 : (size_t)N_));
-            SG_TRY(galloc((void**)&dst, cnt * sizeof(real)));
+            SG_TRY(galloc((void**)&dst, ((size_t)outer << tl) * (size_t)inner * sizeof(real)));
             next[key] = dst;
           }
-          J.tlev[J.ntargets] = tl;
-          J.dst[J.ntargets] = dst;
-          ++J.ntargets;
+          J.dst[tl] = dst;
         }
+        total_lines += outer * inner;
         jobs.push_back(J);
+      }
+      // lines per block: contiguous lines (pass 0) need no tile, so blocks
+      // are sized to cover every SM twice; strided lines take tiles of 8
+      // adjacent lines (32-byte row segments) within 160 KB of shared memory
+      int lpb = 8;
+      if (a == 0) {
+        while (lpb > 1 && total_lines / lpb < 2 * 152) lpb >>= 1;
+      } else {
+        while (lpb > 1 && (size_t)lpb * S * sizeof(real) > 160 * 1024) lpb >>= 1;
+      }
+      int blocks = 0;
+      for (auto& J : jobs) {
+        J.block_begin = blocks;
+        if (J.inner == 1) {
+          blocks += (J.outer + lpb - 1) / lpb;
+        } else {
+          const int cpb = std::min(lpb, J.inner);
+          blocks += J.outer * (J.inner / cpb);
+        }
       }
       Pass P;
       P.njobs = (int)jobs.size();
       P.nblocks = blocks;
-      P.smem = smem;
+      P.lpb = lpb;
+      P.vpl = std::max(1, N_ / 32);
+      P.smem = a == 0 ? 0 : (int)((size_t)lpb * S * sizeof(real));
       SG_TRY(galloc((void**)&P.dev, jobs.size() * sizeof(LineJob)));
       SG_CUDA(cudaMemcpyAsync(P.dev, jobs.data(), jobs.size() * sizeof(LineJob), cudaMemcpyHostToDevice, stream_));
       SG_CUDA(cudaStreamSynchronize(stream_));
@@ -804,7 +823,7 @@ class Engine final : public EngineBase {
       std::vector<FftJob> jobs;
       int blocks = 0, smem = 0;
       for (int g = 0; g < ngrids_; ++g) {
-        for (int comp = 0; comp < (per_comp ? D : 1); ++comp) {
+        for (int comp = 0; comp < (per_comp ? (D + 1) / 2 : 1); ++comp) {  // component pairs
           FftJob J;
           std::memset(&J, 0, sizeof(J));
           J.grid = g;
@@ -925,7 +944,8 @@ class Engine final : public EngineBase {
   }
 
   int enqueue_restrict() {
-    for (auto& P : rpasses_) SG_TRY(launch_restrict_pass<real>(P.dev, P.njobs, P.nblocks, P.smem, stream_));
+    for (auto& P : rpasses_)
+      SG_TRY(launch_restrict_pass<real>(P.dev, P.njobs, P.nblocks, P.lpb, P.vpl, P.smem, stream_));
     return SG_OK;
   }
 

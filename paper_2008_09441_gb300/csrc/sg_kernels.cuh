@@ -56,8 +56,8 @@ int exclusive_scan_u32(const uint32_t* in, uint32_t* out, size_t m, uint32_t* bl
 size_t scan_block_sums_words(size_t m);
 
 // ---------------------------------------------------------------- deposit
-constexpr int DEP_THREADS = 256;
-constexpr int DEP_ITEMS = 8;
+constexpr int DEP_THREADS = 512;
+constexpr int DEP_ITEMS = 4;
 constexpr int DEP_CHUNK = DEP_THREADS * DEP_ITEMS;
 
 template <typename real, int D>
@@ -65,20 +65,18 @@ int launch_deposit(const PArrays<real, D>& p, size_t np, int n, real inv_cell_vo
                    int win_cap_nodes, cudaStream_t s);
 
 // ---------------------------------------------------------------- line passes
-// A batch of lines of one array, processed by one kernel launch together
-// with the other jobs of the same pass.
-constexpr int LJ_MAX_TARGETS = 14;
+// The lines of one array along one axis, processed by one kernel launch
+// together with the other jobs of the same pass.
+constexpr int RJ_LEVELS = 13;  // levels 0..12 (2D n <= 12, 3D n <= 8)
 struct LineJob {
-  const void* src;
-  int dims[3];
-  int axis;
-  int top;        // log2(dims[axis])
-  int ntargets;
-  int lines;      // number of lines in the array
-  int lines_per_block;
-  int block_begin;  // first block of this job in the launch
-  int tlev[LJ_MAX_TARGETS];
-  void* dst[LJ_MAX_TARGETS];
+  const void* src;       // [outer][2^top][inner] reals
+  int top;               // log2 of the line length
+  int outer, inner;      // powers of two; lines = outer * inner
+  int block_begin;       // first block of this job in the launch
+  int tile_stride;       // reals per tile row in shared memory (inner > 1)
+  int tmask;             // bit l set: level l is written
+  int tmin;              // lowest level written
+  void* dst[RJ_LEVELS];  // level l: [outer][2^l][inner]
 };
 
 // Block -> job of a pass: the last job whose block_begin <= blockIdx.x.  The
@@ -102,11 +100,12 @@ __device__ __forceinline__ int find_job(const Job* __restrict__ jobs, int njobs)
   return s_job;
 }
 
-// Restriction pyramid (full weighting 1/4, 1/2, 1/4 per level halving, the
-// exact form of R along one axis for nested node-centred grids).
+// Restriction along one axis of every job's lines (full weighting 1/4,
+// 1/2, 1/4 per level halving, the exact form of R along one axis for nested
+// node-centred grids), outputs in the natural layout.
 template <typename real>
-int launch_restrict_pass(const LineJob* jobs_dev, int njobs, int nblocks, int smem_bytes,
-                         cudaStream_t s);
+int launch_restrict_pass(const LineJob* jobs_dev, int njobs, int nblocks, int lines_per_block, int vpl,
+                         int smem_bytes, cudaStream_t s);
 
 // FFT passes over the component grids.
 enum FftKind { FFT_FWD_FIRST = 0, FFT_FWD_MID = 1, FFT_LAST = 2, FFT_INV_MID = 3, FFT_INV_LAST = 4 };
@@ -119,7 +118,7 @@ struct FftJob {
   int lines;
   int lines_per_block;
   int block_begin;
-  int comp;          // field component for the inverse passes
+  int comp;          // inverse passes: component pair (2 comp, 2 comp + 1)
 };
 
 template <typename real>

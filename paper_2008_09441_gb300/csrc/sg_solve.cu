@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(512) k_fft_pass(int kind, SolveArena<real> a, 
     const int D = a.dim;
     const real norm = (real)1 / (real)g.size;
     const int l0 = __ffs(J.dims[0]) - 1;
-    for (int m = 0; m < D; ++m) {
+    for (int p = 0; 2 * p < D; ++p) {
+      const int ma = 2 * p, mb = 2 * p + 1;  // mb == D: no second component
       for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int li = e >> logn, t = e & (len - 1);
         const int L = line0 + li;  // combined index of the axes before the last
@@ -154,24 +155,36 @@ __global__ void __launch_bounds__(512) k_fft_pass(int kind, SolveArena<real> a, 
           idx[0] = L & (J.dims[0] - 1);
           idx[1] = L >> l0;
         }
-        real k2 = 0, km = 0;
-        bool nyq_m = false;
+        real k2 = 0, ka = 0, kb = 0;
+        bool nyq_a = false, nyq_b = false;
         for (int q = 0; q < D; ++q) {
           const int Nq = J.dims[q];
           const real kq = (real)(g.kfac[q] * (double)sfreq(idx[q], Nq));
           k2 += kq * kq;
-          if (q == m) {
-            km = kq;
-            nyq_m = (idx[q] == (Nq >> 1));
+          if (q == ma) {
+            ka = kq;
+            nyq_a = (idx[q] == (Nq >> 1));
+          }
+          if (q == mb) {
+            kb = kq;
+            nyq_b = (idx[q] == (Nq >> 1));
           }
         }
         const cplx<real> r = buf0[(li << logn) + t];
-        cplx<real> out;
-        if (k2 == (real)0 || nyq_m) {
-          out = {(real)0, (real)0};
-        } else {
-          const real fac = km / k2 * norm;  // -i k_m rho^/|k|^2 : (a + ib) -> (b, -a)
-          out = {r.y * fac, -r.x * fac};
+        // E^_m = -i k_m rho^ / |k|^2 : (x + iy) -> (y, -x) * k_m / |k|^2
+        cplx<real> out = {(real)0, (real)0};
+        if (k2 != (real)0) {
+          const real inv = norm / k2;
+          if (!nyq_a) {
+            const real fa = ka * inv;
+            out.x += r.y * fa;
+            out.y -= r.x * fa;
+          }
+          if (mb < D && !nyq_b) {  // + i E^_b: (y, -x) * fb times i -> (x, y) * fb
+            const real fb = kb * inv;
+            out.x += r.x * fb;
+            out.y += r.y * fb;
+          }
         }
         buf1[(li << logn) + bitrev(t, logn)] = out;
       }
@@ -181,7 +194,7 @@ __global__ void __launch_bounds__(512) k_fft_pass(int kind, SolveArena<real> a, 
         const int li = contiguous ? (e >> logn) : (e & (nl - 1));
         const int t = contiguous ? (e & (len - 1)) : (e >> logC);
         const long long off = line_addr(line0 + li, t, ls, logn);
-        a.B[(size_t)m * S + g.offset + off] = buf1[(li << logn) + t];
+        a.B[(size_t)p * S + g.offset + off] = buf1[(li << logn) + t];
       }
       __syncthreads();
     }
@@ -197,8 +210,9 @@ __global__ void __launch_bounds__(512) k_fft_pass(int kind, SolveArena<real> a, 
       a.A[g.offset + off] = v;
     } else if (kind == FFT_INV_MID) {
       a.B[(size_t)J.comp * S + g.offset + off] = v;
-    } else {  // FFT_INV_LAST: the field is real
-      a.E[(size_t)J.comp * S + g.offset + off] = v.x;
+    } else {  // FFT_INV_LAST: real part -> component 2p, imaginary -> 2p + 1
+      a.E[(size_t)(2 * J.comp) * S + g.offset + off] = v.x;
+      if (2 * J.comp + 1 < a.dim) a.E[(size_t)(2 * J.comp + 1) * S + g.offset + off] = v.y;
     }
   }
 }

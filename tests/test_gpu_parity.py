@@ -117,7 +117,7 @@ def test_run_keys_counts_checksum(torch_cuda, prec):
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("d,n,tau,np_", [(2, 6, 1, 3 * 2048 + 99), (2, 7, 3, 20000), (3, 4, 1, 9000), (3, 5, 2, 15000),
-                                         (2, 8, 6, 30000), (3, 5, 4, 20000)])
+                                         (2, 8, 6, 30000), (3, 5, 4, 20000), (2, 10, 1, 20000)])
 def test_fields_at_init(torch_cuda, prec, d, n, tau, np_):
     if d == 2:
         wl = workloads.landau2d(n_particles=np_, n=n, tau=tau, seed=5 + n)
@@ -147,6 +147,25 @@ def test_fields_at_init(torch_cuda, prec, d, n, tau, np_):
     Eg = run.field()
     for m in range(d):
         assert nrmse(Eg[m], Ec[m]) < 20 * tol
+    run.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("d,n,tau,np_", [(2, 11, 2, 6000), (2, 12, 10, 3000), (3, 8, 6, 4000), (3, 2, 1, 500)])
+def test_restriction_line_lengths(torch_cuda, prec, d, n, tau, np_):
+    """Component-grid charges against the direct deposit of Proposition 1
+    at the longest and shortest lines the restriction supports (2^12 and
+    2^2 values per line)."""
+    if d == 2:
+        wl = workloads.landau2d(n_particles=np_, n=n, tau=tau, seed=7 + n)
+    else:
+        wl = workloads.twostream3d(n_particles=np_, n=n, tau=tau, seed=7 + n)
+    run, (u64, v64, q64) = make_run(wl, prec, torch_cuda)
+    u64 = O.wrap_unit(u64)
+    gq = run.grid_charges()
+    for l, c in O.combination_grids(d, n, tau):
+        ref = O.deposit_cic(u64, q64, l, wl.L)
+        assert nrmse(gq[l], ref) < TOL[prec], l
     run.close()
 
 
