@@ -895,6 +895,7 @@ class Engine final : public EngineBase {
     std::memset(&pp, 0, sizeof(pp));
     pp.qm = (real)cfg_.qm;
     pp.dt = (real)dt;
+    pp.ke_fac = (real)(0.5 / cfg_.qm);
     bool boris = false, eext = false;
     for (int m = 0; m < 3; ++m) {
       pp.dt_over_L[m] = m < D ? (real)(dt / cfg_.L[m]) : (real)0;

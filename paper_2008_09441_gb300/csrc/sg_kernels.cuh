@@ -166,6 +166,7 @@ struct LevelLists {
 template <typename real>
 struct PushParams {
   real qm, dt;
+  real ke_fac;    // 1 / (2 q/m): kinetic energy 0.5 m_p v.v with m_p = q_p / (q/m)
   real dt_over_L[3];
   real eext[3];   // E_ext,m = eext[m] * (u_m - 1/2)   (eext = Eext_lin * L)
   real tB[3];     // q/m * B * dt / 2 (Boris t vector)

@@ -23,10 +23,58 @@ int push_blocks(size_t np) {
   return (int)b;
 }
 
+// Kinetic-energy accumulator of one thread: FP32 path a float pair whose
+// low part collects the exact rounding error of every addition (two_sum);
+// FP64 path plain double.  Partials are reduced in FP64.
+template <typename real>
+struct KeAcc;
+template <>
+struct KeAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const ff s = two_sum(hi, x);
+    hi = s.hi;
+    lo += s.lo;
+  }
+  __device__ __forceinline__ double to_double() const { return (double)hi + (double)lo; }
+};
+template <>
+struct KeAcc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ double to_double() const { return v; }
+};
+
+// Cell and offset of the gather.  FP32: floor through the 1.5 * 2^23
+// rounding trick (no conversion instruction); a position exactly on a node
+// of odd index may land in the cell below with offset 1, which interpolates
+// the same node value with weight 1.  FP64: truncation.
+__device__ __forceinline__ void gather_cell(float s, int mask, int& c, float& f) {
+  const float t = (s - 0.5f) + 12582912.0f;
+  c = (__float_as_int(t) - 0x4B400000) & mask;
+  f = s - (t - 12582912.0f);
+}
+__device__ __forceinline__ void gather_cell(double s, int mask, int& c, double& f) {
+  int ci = (int)s;
+  ci = ci < 0 ? 0 : (ci > mask ? mask : ci);
+  c = ci;
+  f = s - (double)ci;
+}
+
+// Periodic wrap of a drifted position: u - floor(u), a rounded-up 1 mapped
+// to 0.  A drift of less than one box per step needs only a compare and an
+// add of +-1 (the same operation floor would select); larger ones take floor.
+template <typename real>
+__device__ __forceinline__ real wrap_drifted(real u) {
+  real w = u < (real)0 ? u + (real)1 : (u >= (real)1 ? u - (real)1 : u);
+  if (w < (real)0 || w >= (real)1) w = u - sg_floor(u);
+  return w >= (real)1 ? (real)0 : w;
+}
+
 // Advance one particle in registers.
 template <typename real, int D>
 __device__ __forceinline__ void push_one(real (&u)[D], real (&v)[D], real w, int n, const real* __restrict__ Ec,
-                                         size_t ND, const PushParams<real>& pp, Acc<real>& ke, bool& bad) {
+                                         size_t ND, const PushParams<real>& pp, KeAcc<real>& ke, bool& bad) {
   const int N = 1 << n;
   const int mask = N - 1;
   const real half = (real)0.5;
@@ -34,23 +82,19 @@ __device__ __forceinline__ void push_one(real (&u)[D], real (&v)[D], real w, int
   real f[D], E[D];
 #pragma unroll
   for (int m = 0; m < D; ++m) {
-    real s = u[m] * (real)N;
-    int ci = (int)s;
-    ci = ci < 0 ? 0 : (ci > mask ? mask : ci);
-    c[m] = ci;
-    f[m] = s - (real)ci;
+    gather_cell(u[m] * (real)N, mask, c[m], f[m]);
     E[m] = (real)0;
   }
 #pragma unroll
   for (int corner = 0; corner < (1 << D); ++corner) {
     real wgt = (real)1;
-    size_t node = 0, gs = 1;
+    unsigned node = 0, gs = 1;  // 2^{dn} <= 2^24 nodes
 #pragma unroll
     for (int m = 0; m < D; ++m) {
       int b = (corner >> m) & 1;
       wgt *= b ? f[m] : ((real)1 - f[m]);
-      node += (size_t)((c[m] + b) & mask) * gs;
-      gs *= (size_t)N;
+      node += (unsigned)((c[m] + b) & mask) * gs;
+      gs *= (unsigned)N;
     }
 #pragma unroll
     for (int m = 0; m < D; ++m) E[m] += wgt * __ldg(Ec + (size_t)m * ND + node);
@@ -93,11 +137,11 @@ __device__ __forceinline__ void push_one(real (&u)[D], real (&v)[D], real w, int
     bad |= !finite_r(vn);
     v[m] = vn;
   }
-  ke.add(half * (w / pp.qm) * dot);
+  ke.add(w * pp.ke_fac * dot);
   if (pp.drift) {
 #pragma unroll
     for (int m = 0; m < D; ++m) {
-      real un = wrap_unit(u[m] + v[m] * pp.dt_over_L[m]);
+      real un = wrap_drifted(u[m] + v[m] * pp.dt_over_L[m]);
       bad |= !finite_r(un);
       u[m] = un;
     }
@@ -126,13 +170,13 @@ __device__ __forceinline__ void count_tile(uint32_t* tile_count, uint32_t t, boo
 }
 
 template <typename real, int D>
-__global__ void __launch_bounds__(256) k_push(PArrays<real, D> p, size_t np, int n, const real* __restrict__ Ec,
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? (D == 2 ? 4 : 3) : 0) k_push(PArrays<real, D> p, size_t np, int n, const real* __restrict__ Ec,
                                               PushParams<real> pp, double* __restrict__ ke_partials,
                                               unsigned* status, SortFuse sf) {
   __shared__ double red[32];
   const int N = 1 << n;
   const size_t ND = (size_t)N * (D == 2 ? N : (size_t)N * N);
-  Acc<real> ke;
+  KeAcc<real> ke;
   bool bad = false;
   unsigned long long cks = 0;
   const size_t nvec = np >> 2;

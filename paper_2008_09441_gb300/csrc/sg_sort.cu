@@ -469,21 +469,33 @@ int launch_tile_hist(const uint32_t* keys, size_t np, uint32_t* tile_count, cuda
   return SG_OK;
 }
 
-// Scatter every particle to its tile's slots.  Same blocks as the count: the
-// block ranks its particles per tile with shared atomics, reserves one range
-// per distinct tile with a single global atomic, then moves each particle's
-// payload (loads issued before the stores).  Blocks whose keys span more
-// tiles than the shared counters reserve per warp group instead.  Within a
-// tile the order depends on the atomics: the step sort is a valid, not a
-// stable, counting sort by tile key.
+// Scatter every particle to its tile's slots.  Same blocks as the count.
+// When the block's keys span at most TB_SPAN tiles (the usual case: the
+// particles were tile-sorted a few steps earlier), the block ranks its
+// particles per tile with shared atomics, reserves one range per distinct
+// tile with a single global atomic, orders its payload by tile in shared
+// memory (a block-local counting sort), and writes it out as contiguous runs
+// per tile -- coalesced stores even when the particles have drifted over
+// many tiles.  Wider blocks reserve per warp group and store directly.
+// Within a tile the order depends on the atomics: the step sort is a valid,
+// not a stable, counting sort by tile key.
+template <typename real, int D>
+struct ScatterStage {
+  static constexpr size_t bytes = (size_t)TB_ITEMS * ((2 * D + 1) * sizeof(real) + 2 * sizeof(uint32_t));
+  static constexpr bool on = bytes <= 160 * 1024;
+};
+
 template <typename real, int D>
 __global__ void __launch_bounds__(TB_THREADS) k_tile_scatter(PArrays<real, D> src, PArrays<real, D> dst,
                                                              const uint32_t* __restrict__ keys, uint32_t* cursor,
                                                              size_t np) {
-  __shared__ uint32_t s_cnt[TB_SPAN];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t s_cnt[TB_SPAN];   // per tile: count, then the local start
+  __shared__ uint32_t s_base[TB_SPAN];  // per tile: the block's global base
+  __shared__ uint32_t s_wsum[TB_THREADS / 32];
   __shared__ uint32_t s_lo, s_hi;
   const size_t chunk = (size_t)blockIdx.x * TB_ITEMS;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t t[TB_PER_THREAD];
   load_keys(keys, np, chunk, t);
   if (threadIdx.x == 0) {
@@ -508,12 +520,72 @@ __global__ void __launch_bounds__(TB_THREADS) k_tile_scatter(PArrays<real, D> sr
       pos[k] = __shfl_sync(0xffffffffu, b, leader) + (uint32_t)__popc(peers & ((1u << lane) - 1u));
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < TB_SPAN; i += TB_THREADS)
-      if (s_cnt[i]) s_cnt[i] = atomicAdd(&cursor[lo + i], s_cnt[i]);  // block's base in the tile
-    __syncthreads();
+    // per tile: the block's global base (one atomic per non-empty tile) and
+    // the local start (exclusive scan of the counts, four tiles per thread)
+    static_assert(TB_SPAN == 4 * TB_THREADS, "four tiles per thread");
+    uint32_t cnt4[4], run = 0;
 #pragma unroll
-    for (int k = 0; k < TB_PER_THREAD; ++k)
-      if (t[k] != 0xFFFFFFFFu) pos[k] += s_cnt[t[k] - lo];
+    for (int j = 0; j < 4; ++j) {
+      const int i = 4 * threadIdx.x + j;
+      cnt4[j] = s_cnt[i];
+      if (cnt4[j]) s_base[i] = atomicAdd(&cursor[lo + i], cnt4[j]);
+      run += cnt4[j];
+    }
+    uint32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (int w = 0; w < warp; ++w) wbase += s_wsum[w];
+    uint32_t start = wbase + incl - run;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      s_cnt[4 * threadIdx.x + j] = start;
+      start += cnt4[j];
+    }
+    __syncthreads();
+    if constexpr (ScatterStage<real, D>::on) {
+      real* su = reinterpret_cast<real*>(smem_raw);  // [2D+1][TB_ITEMS]: u, v, w
+      uint32_t* spid = reinterpret_cast<uint32_t*>(su + (size_t)(2 * D + 1) * TB_ITEMS);
+      uint32_t* sdst = spid + TB_ITEMS;
+#pragma unroll
+      for (int k = 0; k < TB_PER_THREAD; ++k) {
+        const size_t i = chunk + (size_t)k * TB_THREADS + threadIdx.x;
+        if (i < np) {
+          const uint32_t ti = t[k] - lo;
+          const uint32_t L = s_cnt[ti] + pos[k];
+#pragma unroll
+          for (int m = 0; m < D; ++m) {
+            su[(size_t)m * TB_ITEMS + L] = __ldg(src.u[m] + i);
+            su[(size_t)(D + m) * TB_ITEMS + L] = __ldg(src.v[m] + i);
+          }
+          su[(size_t)(2 * D) * TB_ITEMS + L] = __ldg(src.w + i);
+          spid[L] = __ldg(src.pid + i);
+          sdst[L] = s_base[ti] + pos[k];
+        }
+      }
+      __syncthreads();
+      const int nvalid = (int)min((size_t)TB_ITEMS, np - chunk);
+      for (int j = threadIdx.x; j < nvalid; j += TB_THREADS) {
+        const uint32_t p = sdst[j];
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+          dst.u[m][p] = su[(size_t)m * TB_ITEMS + j];
+          dst.v[m][p] = su[(size_t)(D + m) * TB_ITEMS + j];
+        }
+        dst.w[p] = su[(size_t)(2 * D) * TB_ITEMS + j];
+        dst.pid[p] = spid[j];
+      }
+      return;
+    } else {
+#pragma unroll
+      for (int k = 0; k < TB_PER_THREAD; ++k)
+        if (t[k] != 0xFFFFFFFFu) pos[k] += s_base[t[k] - lo];
+    }
   } else {
 #pragma unroll
     for (int k = 0; k < TB_PER_THREAD; ++k) {
@@ -525,7 +597,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_tile_scatter(PArrays<real, D> sr
       pos[k] = __shfl_sync(0xffffffffu, base, leader) + (uint32_t)__popc(peers & ((1u << lane) - 1u));
     }
   }
-  // move the payload: loads of all items first, then the stores
+  // direct move: loads of a group of items first, then the stores
   constexpr int G = 4;
 #pragma unroll
   for (int g0 = 0; g0 < TB_PER_THREAD; g0 += G) {
@@ -563,7 +635,14 @@ template <typename real, int D>
 int launch_tile_scatter(const PArrays<real, D>& src, const PArrays<real, D>& dst, const uint32_t* keys,
                         uint32_t* cursor, size_t np, cudaStream_t s) {
   if (np == 0) return SG_OK;
-  k_tile_scatter<real, D><<<(unsigned)((np + TB_ITEMS - 1) / TB_ITEMS), TB_THREADS, 0, s>>>(src, dst, keys, cursor, np);
+  const size_t smem = ScatterStage<real, D>::on ? ScatterStage<real, D>::bytes : 0;
+  static bool attr_set = false;
+  if (!attr_set && smem > 48 * 1024) {
+    SG_CUDA(cudaFuncSetAttribute(k_tile_scatter<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
+  k_tile_scatter<real, D><<<(unsigned)((np + TB_ITEMS - 1) / TB_ITEMS), TB_THREADS, smem, s>>>(src, dst, keys,
+                                                                                              cursor, np);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
