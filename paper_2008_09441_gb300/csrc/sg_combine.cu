@@ -219,6 +219,15 @@ __device__ __forceinline__ void combine_finalize(const double* partials, int n_p
   }
 }
 
+// Lines per block of the warp-per-line kernel (one warp per line and
+// component) and the bytes of its per-warp row-term tables.
+template <int D>
+constexpr int combine_rows_per_block() { return D == 2 ? 4 : 2; }
+template <typename real, int D>
+__host__ __device__ constexpr size_t combine_table_bytes(int ngl) {
+  return ((size_t)combine_rows_per_block<D>() * D * ngl * sizeof(RowTerm<real, D>) + 15) / 16 * 16;
+}
+
 template <typename real, int D, int V>
 __global__ void __launch_bounds__(256) k_combine_warp(const GridDesc* __restrict__ grids, LevelLists ll, int lmin,
                                                       const real* __restrict__ E, size_t S, int n,
@@ -242,7 +251,13 @@ __global__ void __launch_bounds__(256) k_combine_warp(const GridDesc* __restrict
     for (int i = 0; i < 18; ++i) s_start[i] = ll.start[i];  // constant indices: no local copy
   }
   const int ngl = ll.start[17];
+  constexpr int RPB = combine_rows_per_block<D>();  // the block's lines: all D components of each
+  constexpr int DP = ec_stride<D>();
   RowTerm<real, D>* rt_tab = reinterpret_cast<RowTerm<real, D>*>(smem_raw) + (size_t)wib * ngl;
+  // [RPB][N][DP] with one padding word after every V nodes (a lane's run), so
+  // that the lanes' stores of one step fall in distinct banks
+  real* stage = reinterpret_cast<real*>(smem_raw + combine_table_bytes<real, D>(ngl));
+  const int row0 = blockIdx.x * RPB;
   for (int gi = lane; gi < ngl; gi += 32) rt_tab[gi] = row_term<real, D>(grids[ll.grid[gi]], n, y, z);
   __syncthreads();
   real energy = (real)0;
@@ -274,45 +289,51 @@ __global__ void __launch_bounds__(256) k_combine_warp(const GridDesc* __restrict
     }
     // register phase: 2^level / 32 consecutive values per lane
     if (level < n) CombLevels<real, D, 1, V>::run(T, level, n, lane, rt_tab, s_start, Em);
+    // hi parts to the block's node-interleaved stage, lo planes straight out
     const size_t o0 = (size_t)m * ND + (size_t)row * N;
-    if constexpr (sizeof(real) == 4) {
-      if constexpr (V >= 4) {
+    const int nb = (row - row0) * N;  // first node of this line in the block
+    real* srow = stage + (size_t)nb * DP + nb / V + m;  // node x at srow[x * DP + x / V]
+    const int per = N >= 32 ? V : 1;
+    if (N >= 32 || lane < N) {
+      if constexpr (sizeof(real) == 4) {
+        if constexpr (V >= 4) {
 #pragma unroll
-        for (int k = 0; k < V; k += 4) {
-          ff v[4];
+          for (int k = 0; k < V; k += 4) {
+            ff v[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            v[q] = T[k + q].normalised();
-            energy = fmaf(v[q].hi, v[q].hi, energy);
+            for (int q = 0; q < 4; ++q) {
+              v[q] = T[k + q].normalised();
+              energy = fmaf(v[q].hi, v[q].hi, energy);
+              srow[(size_t)(lane * V + k + q) * DP + lane] = v[q].hi;
+            }
+            *reinterpret_cast<float4*>(Elo + o0 + (size_t)lane * V + k) =
+                make_float4(v[0].lo, v[1].lo, v[2].lo, v[3].lo);
           }
-          const size_t o = o0 + (size_t)lane * V + k;
-          *reinterpret_cast<float4*>(Ehi + o) = make_float4(v[0].hi, v[1].hi, v[2].hi, v[3].hi);
-          *reinterpret_cast<float4*>(Elo + o) = make_float4(v[0].lo, v[1].lo, v[2].lo, v[3].lo);
-        }
-      } else {
-        const int per = N >= 32 ? V : 1;
-        if (N >= 32 || lane < N) {
+        } else {
 #pragma unroll
           for (int k = 0; k < V; ++k)
             if (k < per) {
               const ff v = T[k].normalised();
-              Ehi[o0 + (size_t)lane * per + k] = v.hi;
+              srow[(size_t)(lane * per + k) * DP + (lane * per + k) / V] = v.hi;
               Elo[o0 + (size_t)lane * per + k] = v.lo;
               energy = fmaf(v.hi, v.hi, energy);
             }
         }
-      }
-    } else {
-      const int per = N >= 32 ? V : 1;
-      if (N >= 32 || lane < N) {
+      } else {
 #pragma unroll
         for (int k = 0; k < V; ++k)
           if (k < per) {
-            Ehi[o0 + (size_t)lane * per + k] = T[k].v;
+            srow[(size_t)(lane * per + k) * DP + (lane * per + k) / V] = T[k].v;
             energy = fma(T[k].v, T[k].v, energy);
           }
       }
     }
+  }
+  __syncthreads();
+  {  // the block's RPB lines are contiguous nodes: coalesced stores of the stage
+    const int nreal = RPB * N * DP;
+    real* dst = Ehi + (size_t)row0 * N * DP;
+    for (int i = threadIdx.x; i < nreal; i += blockDim.x) dst[i] = stage[i + (i / DP) / V];
   }
   const double tot = warp_sum((double)energy);
   if (lane == 0 && row < rows) partials[task] = tot;
@@ -426,7 +447,7 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
     const int m = e2 >> n, x = e2 & (N - 1);
     const Acc<real> v = A[m * 2 * N + N + x];
     const size_t o = (size_t)m * ND + (size_t)row * N + x;
-    Ehi[o] = (real)v.hi();
+    Ehi[((size_t)row * N + x) * ec_stride<D>() + m] = (real)v.hi();
     if (Elo) Elo[o] = (float)v.lo();
     energy = fma((real)v.hi(), (real)v.hi(), energy);
   }
@@ -441,12 +462,18 @@ static int launch_combine_warp(const GridDesc* grids, const LevelLists& ll, int 
                                real* Ehi, float* Elo, double* energy_partials, const CombineFinal& fin,
                                cudaStream_t s) {
   const int N = 1 << n;
-  const long long tasks = (long long)(D == 2 ? N : N * N) * D;
-  const int warps = 8;
-  const unsigned blocks = (unsigned)((tasks + warps - 1) / warps);
-  const size_t smem = (size_t)warps * ll.start[17] * sizeof(RowTerm<real, D>);
-  k_combine_warp<real, D, V><<<blocks, 32 * warps, smem, s>>>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials,
-                                                              fin);
+  const long long rows = D == 2 ? N : (long long)N * N;
+  constexpr int RPB = combine_rows_per_block<D>();
+  const unsigned blocks = (unsigned)(rows / RPB);  // N >= 4: RPB divides the line count
+  const size_t smem = combine_table_bytes<real, D>(ll.start[17]) +
+                      ((size_t)RPB * N * ec_stride<D>() + (size_t)RPB * N / V) * sizeof(real);
+  static bool attr_set = false;
+  if (!attr_set && smem > 48 * 1024) {
+    SG_CUDA(cudaFuncSetAttribute(k_combine_warp<real, D, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  k_combine_warp<real, D, V><<<blocks, 32 * RPB * D, smem, s>>>(grids, ll, lmin, E, S, n, Ehi, Elo,
+                                                                energy_partials, fin);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }

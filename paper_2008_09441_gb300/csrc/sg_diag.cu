@@ -109,17 +109,25 @@ int launch_to_double(const real* src, double* dst, size_t n, cudaStream_t s) {
   return SG_OK;
 }
 
-__global__ void k_ff_to_double(const float* hi, const float* lo, double* dst, size_t n) {
-  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = (double)hi[i] + (lo ? (double)lo[i] : 0.0);
+template <typename real>
+__global__ void k_field_to_double(const real* hi, const float* lo, double* dst, size_t nd, int dim, int stride) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nd * (size_t)dim) return;
+  const size_t m = i / nd, node = i - m * nd;
+  dst[i] = (double)hi[node * (size_t)stride + m] + (lo ? (double)lo[i] : 0.0);
 }
 
-int launch_ff_to_double(const float* hi, const float* lo, double* dst, size_t n, cudaStream_t s) {
+template <typename real>
+int launch_field_to_double(const real* hi, const float* lo, double* dst, size_t nd, int dim, int stride,
+                           cudaStream_t s) {
+  const size_t n = nd * (size_t)dim;
   if (n == 0) return SG_OK;
-  k_ff_to_double<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(hi, lo, dst, n);
+  k_field_to_double<real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(hi, lo, dst, nd, dim, stride);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
+template int launch_field_to_double<float>(const float*, const float*, double*, size_t, int, int, cudaStream_t);
+template int launch_field_to_double<double>(const double*, const float*, double*, size_t, int, int, cudaStream_t);
 
 // ---------------------------------------------------------------- Algorithm 1 helpers (FP64)
 __global__ void k_real_to_cplx(const double* src, cplx<double>* dst, size_t n, double scale) {

@@ -97,7 +97,7 @@ class Engine final : public EngineBase {
 
     // ---- regular grid, combined field, twiddles
     SG_TRY(alloc((void**)&rho_reg_, ND_ * sizeof(real)));
-    SG_TRY(alloc((void**)&Ehi_, (size_t)D * ND_ * sizeof(real)));
+    SG_TRY(alloc((void**)&Ehi_, (size_t)ec_stride<D>() * ND_ * sizeof(real)));  // node-interleaved
     if (sizeof(real) == 4) SG_TRY(alloc((void**)&Elo_, (size_t)D * ND_ * sizeof(float)));
     nrows_ = (int)(ND_ / (size_t)N_);
     SG_TRY(alloc((void**)&fe_partials_, (size_t)nrows_ * D * sizeof(double)));  // per (line, component)
@@ -375,10 +375,7 @@ class Engine final : public EngineBase {
     if (cap < (size_t)D * ND_) return size_error("sg_pic_get_field");
     double* tmp = nullptr;
     SG_TRY(alloc((void**)&tmp, (size_t)D * ND_ * sizeof(double)));
-    if (sizeof(real) == 4)
-      SG_TRY(launch_ff_to_double((const float*)Ehi_, Elo_, tmp, (size_t)D * ND_, stream_));
-    else
-      SG_TRY(launch_to_double<real>(Ehi_, tmp, (size_t)D * ND_, stream_));
+    SG_TRY(launch_field_to_double<real>(Ehi_, Elo_, tmp, ND_, D, ec_stride<D>(), stream_));
     SG_CUDA(cudaMemcpyAsync(E, tmp, (size_t)D * ND_ * sizeof(double), cudaMemcpyDeviceToHost, stream_));
     SG_CUDA(cudaStreamSynchronize(stream_));
     free_one(tmp);

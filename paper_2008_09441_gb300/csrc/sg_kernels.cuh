@@ -163,6 +163,13 @@ struct LevelLists {
 
 
 // ---------------------------------------------------------------- push
+// The combined field the push gathers from is stored node-interleaved:
+// E_hi[node * ec_stride<D>() + m] (2D: (E_x, E_y); 3D: (E_x, E_y, E_z, pad)),
+// so one corner of the gather is one 8- or 16-byte load.  The low parts of
+// the FP32 path's float pairs are planes E_lo[m * N_c + node].
+template <int D>
+constexpr int ec_stride() { return D == 2 ? 2 : 4; }
+
 template <typename real>
 struct PushParams {
   real qm, dt;
@@ -245,7 +252,10 @@ int launch_grid_charges(const GridDesc* grids, int ngrids, const real* rho, cons
 
 template <typename real>
 int launch_to_double(const real* src, double* dst, size_t n, cudaStream_t s);
-int launch_ff_to_double(const float* hi, const float* lo, double* dst, size_t n, cudaStream_t s);
+// dst[m * nd + node] = E_hi[node * stride + m] (+ E_lo[m * nd + node] when lo != nullptr), FP64.
+template <typename real>
+int launch_field_to_double(const real* hi, const float* lo, double* dst, size_t nd, int dim, int stride,
+                           cudaStream_t s);
 
 // ---------------------------------------------------------------- tau estimator
 int launch_real_to_cplx(const double* src, cplx<double>* dst, size_t n, double scale, cudaStream_t s);

@@ -71,6 +71,27 @@ __device__ __forceinline__ real wrap_drifted(real u) {
   return w >= (real)1 ? (real)0 : w;
 }
 
+// The combined field at one node: one vector load from the node-interleaved
+// array.
+template <typename real, int D>
+__device__ __forceinline__ void load_node_field(const real* __restrict__ Ec, unsigned node, real (&e)[D]) {
+  if constexpr (sizeof(real) == 4 && D == 2) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(Ec) + node);
+    e[0] = t.x;
+    e[D - 1] = t.y;
+  } else if constexpr (sizeof(real) == 4) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(Ec) + node);
+    e[0] = t.x;
+    e[1 % D] = t.y;
+    e[D - 1] = t.z;
+  } else {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(Ec) + (size_t)node * (ec_stride<D>() / 2));
+    e[0] = (real)a.x;
+    e[1 % D] = (real)a.y;
+    if constexpr (D == 3) e[D - 1] = (real)__ldg(Ec + (size_t)node * ec_stride<D>() + 2);
+  }
+}
+
 // Advance one particle in registers.
 template <typename real, int D>
 __device__ __forceinline__ void push_one(real (&u)[D], real (&v)[D], real w, int n, const real* __restrict__ Ec,
@@ -96,8 +117,10 @@ __device__ __forceinline__ void push_one(real (&u)[D], real (&v)[D], real w, int
       node += (unsigned)((c[m] + b) & mask) * gs;
       gs *= (unsigned)N;
     }
+    real e[D];
+    load_node_field<real, D>(Ec, node, e);
 #pragma unroll
-    for (int m = 0; m < D; ++m) E[m] += wgt * __ldg(Ec + (size_t)m * ND + node);
+    for (int m = 0; m < D; ++m) E[m] += wgt * e[m];
   }
   if (pp.has_eext) {
 #pragma unroll
