@@ -258,8 +258,10 @@ __global__ void __launch_bounds__(256) k_combine_warp(const GridDesc* __restrict
   // that the lanes' stores of one step fall in distinct banks
   real* stage = reinterpret_cast<real*>(smem_raw + combine_table_bytes<real, D>(ngl));
   const int row0 = blockIdx.x * RPB;
+  pdl_trigger();
   for (int gi = lane; gi < ngl; gi += 32) rt_tab[gi] = row_term<real, D>(grids[ll.grid[gi]], n, y, z);
   __syncthreads();
+  pdl_wait();  // the solve's fields
   real energy = (real)0;
   if (row < rows) {
     CAcc<real> T[V];
@@ -472,8 +474,8 @@ static int launch_combine_warp(const GridDesc* grids, const LevelLists& ll, int 
     SG_CUDA(cudaFuncSetAttribute(k_combine_warp<real, D, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  k_combine_warp<real, D, V><<<blocks, 32 * RPB * D, smem, s>>>(grids, ll, lmin, E, S, n, Ehi, Elo,
-                                                                energy_partials, fin);
+  SG_CUDA(launch_pdl(k_combine_warp<real, D, V>, dim3(blocks), dim3(32 * RPB * D), smem, s, grids, ll, lmin, E, S, n,
+                     Ehi, Elo, energy_partials, fin));
   SG_CHECK_LAUNCH();
   return SG_OK;
 }

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 
 #include "../../include/sgpic.h"
 
@@ -50,6 +51,30 @@ unsigned long long launches_so_far();
     ::sg::count_launch(); \
     SG_CUDA(cudaGetLastError()); \
   } while (0)
+
+// Programmatic dependent launch (sm_90+).  A kernel launched with
+// launch_pdl may start while its predecessor in the stream drains; it must
+// call pdl_wait() before touching anything the predecessor writes (the wait
+// returns once the predecessor has completed and its writes are visible).
+// pdl_trigger() lets the successor start launching early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // device-side status bits (or-ed into a device word, read by diagnostics)
 enum : unsigned {

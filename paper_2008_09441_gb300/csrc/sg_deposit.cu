@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
   const int mask = N - 1;
   const size_t chunk = (size_t)blockIdx.x * DEP_CHUNK;
   const int lane = threadIdx.x & 31;
+  pdl_trigger();  // the restriction may start launching
 
   // ---- load the chunk: DEP_ITEMS / 4 vectors of four consecutive particles
   real ub[DEP_ITEMS][D], wb[DEP_ITEMS];
@@ -418,8 +419,10 @@ template <typename real, int VPL>
 __global__ void __launch_bounds__(256) k_restrict_warp(const LineJob* __restrict__ jobs, int njobs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* tile = reinterpret_cast<real*>(smem_raw);
-  const int jb = find_job(jobs, njobs);
+  pdl_trigger();
+  const int jb = find_job(jobs, njobs);  // job tables are written once, at set-up
   const LineJob* J = jobs + jb;
+  pdl_wait();
   const int lpb = blockDim.x >> 5;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int top = J->top, len = 1 << top;
@@ -550,7 +553,7 @@ int launch_restrict_pass(const LineJob* jobs_dev, int njobs, int nblocks, int li
                                    200 * 1024));                                                          \
       attr_set = true;                                                                                    \
     }                                                                                                     \
-    k_restrict_warp<real, V><<<nblocks, threads, smem_bytes, s>>>(jobs_dev, njobs);                       \
+    SG_CUDA(launch_pdl(k_restrict_warp<real, V>, dim3(nblocks), dim3(threads), smem_bytes, s, jobs_dev, njobs)); \
     break;                                                                                                \
   }
   switch (vpl) {

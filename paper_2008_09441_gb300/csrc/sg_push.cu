@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? (D == 2 ? 4 : 3) : 0)
   __shared__ double red[32];
   const int N = 1 << n;
   const size_t ND = (size_t)N * (D == 2 ? N : (size_t)N * N);
+  pdl_wait();  // the combined field (no-op when launched without the attribute)
   KeAcc<real> ke;
   bool bad = false;
   unsigned long long cks = 0;
@@ -279,7 +280,10 @@ template <typename real, int D>
 int launch_push(const PArrays<real, D>& p, size_t np, int n, const real* Ecomb, PushParams<real> pp,
                 double* ke_partials, unsigned* status, const SortFuse& sf, cudaStream_t s) {
   int blocks = push_blocks(np);
-  k_push<real, D><<<blocks, 256, 0, s>>>(p, np, n, Ecomb, pp, ke_partials, status, sf);
+  if (sf.keys)  // sort steps: memsets precede the push
+    k_push<real, D><<<blocks, 256, 0, s>>>(p, np, n, Ecomb, pp, ke_partials, status, sf);
+  else
+    SG_CUDA(launch_pdl(k_push<real, D>, dim3(blocks), dim3(256), 0, s, p, np, n, Ecomb, pp, ke_partials, status, sf));
   SG_CHECK_LAUNCH();
   return SG_OK;
 }

@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(512) k_fft_pass(int kind, SolveArena<real> a, 
                                                   int njobs) {
   extern __shared__ unsigned char smem_raw[];
   const int b = blockIdx.x;
-  const int j = find_job(jobs, njobs);
+  pdl_trigger();
+  const int j = find_job(jobs, njobs);  // job and grid tables are written once, at set-up
   const FftJob& J = jobs[j];
   const GridDesc g = a.grids[J.grid];
   const int logn = J.logn;
@@ -111,6 +112,7 @@ __global__ void __launch_bounds__(512) k_fft_pass(int kind, SolveArena<real> a, 
   cplx<real>* tws = reinterpret_cast<cplx<real>*>(smem_raw);
   const int ntw = 1 << (a.log_nmax - 1);
   for (int e = threadIdx.x; e < ntw; e += blockDim.x) tws[e] = a.tw[e];
+  pdl_wait();  // the previous pass's output
   cplx<real>* buf0 = tws + ntw;
   cplx<real>* buf1 = buf0 + C * len;
   int ls = 0;
@@ -226,7 +228,8 @@ int launch_fft_pass(int kind, const SolveArena<real>& a, const FftJob* jobs_dev,
     SG_CUDA(cudaFuncSetAttribute(k_fft_pass<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  k_fft_pass<real><<<nblocks, 512, smem_bytes + ((size_t)1 << (a.log_nmax - 1)) * sizeof(cplx<real>), s>>>(kind, a, jobs_dev, njobs);
+  SG_CUDA(launch_pdl(k_fft_pass<real>, dim3(nblocks), dim3(512),
+                     smem_bytes + ((size_t)1 << (a.log_nmax - 1)) * sizeof(cplx<real>), s, kind, a, jobs_dev, njobs));
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
