@@ -12,7 +12,7 @@ Every function works in float64 and follows the paper
 adaptive noise reduction strategy for particle-in-cell schemes",
 arXiv:2008.09441).  Section / equation names are the paper's.
 
-State conventions (readings of the paper, all listed in the design doc):
+State conventions (readings of the paper where it is silent):
 
 * Domain: periodic box [0, L_1) x ... x [0, L_d) (Section 5 opening).
   Positions are carried as fractions of the box, ``u_m = x_m / L_m`` in
@@ -381,16 +381,45 @@ def combined_field_regular(comps, n, d):
     return out
 
 
+def density_filter(rho_reg, n, tau, L):
+    """Sparse-grid filter of a regular-grid density (eq. sparse_filter,
+    Algorithm 2): rho_f = sum_i c_i P_i R_i rho~, with R_i and P_i of eq.
+    restriction and the grid set of Section 4.2."""
+    d = np.asarray(rho_reg).ndim
+    out = np.zeros_like(np.asarray(rho_reg, dtype=np.float64))
+    for l, c in combination_grids(d, n, tau):
+        out += c * prolong(restrict(rho_reg, n, l), n, l)
+    return out
+
+
+def filtered_field_regular(u, q, n, tau, L):
+    """Field of the paper's filter mode on the regular nodes: deposit on the
+    regular grid, filter the density (density_filter), one spectral solve
+    on the regular grid (Algorithm 2's field step)."""
+    d = np.asarray(u).shape[1]
+    rho = deposit_cic(u, q, (n,) * d, L)
+    rho_f = density_filter(rho, n, tau, L)
+    return rho, rho_f, solve_poisson_spectral(rho_f, L)
+
+
 class OracleRun:
     """Plain FP64 sparse-grid PIC run (deposit -> solve -> combine/gather ->
     push), the reference for the GPU hot path.
 
     Leapfrog start: v^{-1/2} from a backward half step at t = 0.
-    Diagnostics follow the GPU library's definitions (the design doc lists them).
+    Diagnostics: charge per grid and combined, field energy
+    0.5 h^d sum |E|^2 over the regular nodes (current and previous step),
+    time-centred kinetic energy, and the cell-count checksum.
     """
 
     def __init__(self, L, n, u, v, q, dt, qm=-1.0, tau=1, B=(0.0, 0.0, 0.0),
-                 eext_lin=(0.0, 0.0, 0.0)):
+                 eext_lin=(0.0, 0.0, 0.0), mode="combine"):
+        # mode "combine": sparse PIC, fields solved per component grid and
+        # combined (Section 4.1); "filter": the density is deposited on the
+        # regular grid, filtered (eq. sparse_filter) and solved once there
+        # (Algorithm 2).
+        assert mode in ("combine", "filter")
+        self.mode = mode
         self.L = [float(x) for x in L]
         self.n = int(n)
         self.u = wrap_unit(np.array(u, dtype=np.float64))
@@ -406,21 +435,41 @@ class OracleRun:
         self.kinetic_energy = 0.0
         self.field_energy_prev = 0.0
         self._fields()
-        E = field_at_particles(self.comps, self.u, self.L, self.eext)
+        E = self.field_at(self.u)
         self.v = kick_rotate(self.v, E, self.qm, -0.5 * self.dt, self.B)
 
     def _fields(self):
-        self.comps = component_fields(self.u, self.q, self.n, self.tau, self.L)
+        if self.mode == "combine":
+            self.comps = component_fields(self.u, self.q, self.n, self.tau, self.L)
+        else:  # component densities only (diagnostics), field on the regular grid
+            self.comps = []
+            rho, self.rho_filtered, self.E_regular = filtered_field_regular(self.u, self.q, self.n, self.tau,
+                                                                            self.L)
+            for l, c in combination_grids(self.d, self.n, self.tau):
+                self.comps.append((l, c, restrict(rho, self.n, l), None))
+
+    def field_at(self, u):
+        """The field the push sees at positions u (plus E_ext)."""
+        if self.mode == "combine":
+            return field_at_particles(self.comps, u, self.L, self.eext)
+        Ee = external_field(u, self.L, self.eext)
+        return [gather_cic(self.E_regular[m], u, (self.n,) * self.d) + Ee[m] for m in range(self.d)]
+
+    def regular_field(self):
+        """The field on the regular nodes (combined, or the filter mode's)."""
+        if self.mode == "combine":
+            return combined_field_regular(self.comps, self.n, self.d)
+        return self.E_regular
 
     def field_energy(self):
-        """0.5 h^d sum_j |E_comb(x~_j)|^2 over the regular nodes."""
-        Ec = combined_field_regular(self.comps, self.n, self.d)
+        """0.5 h^d sum_j |E(x~_j)|^2 over the regular nodes."""
+        Ec = self.regular_field()
         hd = float(np.prod([self.L[m] / 2 ** self.n for m in range(self.d)]))
         return 0.5 * hd * float(sum(np.sum(e * e) for e in Ec))
 
     def step(self, nsteps=1):
         for _ in range(nsteps):
-            E = field_at_particles(self.comps, self.u, self.L, self.eext)
+            E = self.field_at(self.u)
             vnew = kick_rotate(self.v, E, self.qm, self.dt, self.B)
             mass = self.q / self.qm
             self.kinetic_energy = 0.5 * float(np.sum(mass * sum(self.v[m] * vnew[m] for m in range(self.d))))

@@ -420,3 +420,77 @@ def test_estimator_threshold_drops_small_modes():
     # the small mixed mode (below eps) leaves no trace in beta
     assert c["beta"][0] == pytest.approx(0.0, abs=1e-9)
     assert c["kappa"][0] == pytest.approx(0.25 * kx * kx, rel=1e-10)
+
+
+# ------------------------------------------------------------ filter mode (eq. sparse_filter, Algorithm 2)
+
+
+@pytest.mark.parametrize("d,n", [(2, 5), (3, 3)])
+def test_filter_tau_n_is_identity(d, n):
+    """tau = n leaves the single regular grid: the filter is the identity."""
+    rng = np.random.default_rng(70 + d)
+    rho = rng.standard_normal((2 ** n,) * d)
+    assert np.allclose(O.density_filter(rho, n, n, [1.0] * d), rho, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("d,n,tau", [(2, 6, 1), (2, 5, 2), (3, 4, 1)])
+def test_filter_conserves_charge_and_constants(d, n, tau):
+    """Every P_i R_i conserves h^d sum rho and the coefficients sum to 1, so
+    the filter conserves the total charge and maps a constant to itself."""
+    rng = np.random.default_rng(80 + n)
+    rho = rng.standard_normal((2 ** n,) * d)
+    rf = O.density_filter(rho, n, tau, [1.0] * d)
+    assert abs(rf.sum() - rho.sum()) < 1e-11 * np.abs(rho).sum()
+    const = np.full((2 ** n,) * d, 3.25)
+    assert np.allclose(O.density_filter(const, n, tau, [1.0] * d), const, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("d,n,tau", [(2, 6, 1), (3, 4, 1)])
+def test_filter_is_self_adjoint(d, n, tau):
+    """R_i = (h^d / V_i) P_i^T makes each P_i R_i symmetric in the regular
+    grid's inner product, hence the whole filter: <a, F b> = <F a, b>."""
+    rng = np.random.default_rng(90 + d)
+    a = rng.standard_normal((2 ** n,) * d)
+    b = rng.standard_normal((2 ** n,) * d)
+    lhs = float(np.sum(a * O.density_filter(b, n, tau, [1.0] * d)))
+    rhs = float(np.sum(O.density_filter(a, n, tau, [1.0] * d) * b))
+    assert abs(lhs - rhs) < 1e-12 * (abs(lhs) + 1.0)
+
+
+@pytest.mark.parametrize("n,tau", [(6, 1), (7, 3)])
+def test_filter_passes_single_axis_densities(n, tau):
+    """2D: for rho(x) alone the y-restrictions are exact and the x parts
+    telescope, sum over a of P R_a with +1 minus the same with -1 leaves the
+    level-n term: a density varying along one axis passes unchanged."""
+    rng = np.random.default_rng(100 + n)
+    fx = rng.standard_normal(2 ** n)
+    rho_x = np.repeat(fx[:, None], 2 ** n, axis=1)  # [i_x, i_y]
+    rho_y = rho_x.T.copy()
+    for r in (rho_x, rho_y):
+        assert np.allclose(O.density_filter(r, n, tau, [1.0, 1.0]), r, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("d,n,tau", [(2, 6, 1), (2, 6, 4), (3, 4, 1)])
+def test_filter_annihilates_the_checkerboard(d, n, tau):
+    """Full weighting maps the Nyquist mode (-1)^i to zero, and every
+    component grid is restricted along at least one axis unless tau = n:
+    the (Nyquist, ..., Nyquist) checkerboard is filtered out entirely."""
+    idx = np.indices((2 ** n,) * d).sum(axis=0)
+    rho = np.where(idx % 2 == 0, 1.0, -1.0)
+    assert np.max(np.abs(O.density_filter(rho, n, tau, [1.0] * d))) < 1e-13
+
+
+def test_filter_mode_run_tau_n_equals_regular_pic():
+    """tau = n: the filter mode is regular PIC, and so is the combination
+    mode (one grid); the two runs must agree to rounding."""
+    rng = np.random.default_rng(5)
+    npart, n = 3000, 5
+    u = rng.random((npart, 2))
+    v = rng.standard_normal((npart, 2))
+    q = -np.full(npart, (4 * np.pi) ** 2 / npart)
+    a = O.OracleRun((4 * np.pi, 4 * np.pi), n, u, v, q, 0.05, tau=n, mode="combine")
+    b = O.OracleRun((4 * np.pi, 4 * np.pi), n, u, v, q, 0.05, tau=n, mode="filter")
+    a.step(3)
+    b.step(3)
+    assert np.max(np.abs(a.u - b.u)) < 1e-12
+    assert abs(a.field_energy() - b.field_energy()) < 1e-12 * a.field_energy()
