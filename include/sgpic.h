@@ -60,6 +60,8 @@ extern "C" {
 #define SG_TAU_ADAPTIVE (-1)          /* run Algorithm 1 (tauEstimator) every step */
 #define SG_TAU_CONST_PAPER 0          /* eq. grid_constants + eq. particle_constant */
 #define SG_TAU_CONST_EMPIRICAL 1      /* eq. empirical_constants */
+#define SG_MODE_COMBINE 0
+#define SG_MODE_FILTER 1
 
 typedef struct sg_pic sg_pic; /* opaque run handle; owns all its device memory */
 
@@ -97,6 +99,13 @@ typedef struct {
   int tau_constants;  /* SG_TAU_CONST_PAPER or SG_TAU_CONST_EMPIRICAL */
   int sort_every;     /* cell-key sort period in steps; 0 = library default (4) */
   void* stream;       /* cudaStream_t for all work of the run; NULL = own stream */
+  int mode;           /* SG_MODE_COMBINE (0): sparse PIC, a spectral solve on every
+                         component grid and the signed combination of their fields
+                         (Section 4.1); SG_MODE_FILTER (1): the paper's filter mode
+                         (eq. sparse_filter, Algorithm 2): the regular-grid density
+                         is filtered, rho_f = sum_i c_i P_i R_i rho~, and solved
+                         once on the regular grid.  Either way the push gathers
+                         from a field on the regular nodes. */
 } sg_params;
 
 typedef struct {
@@ -167,7 +176,8 @@ int sg_pic_get_field(sg_pic* h, double* E, size_t cap);
 int sg_pic_get_grid_charge(sg_pic* h, double* rho, size_t cap);
 
 /* Component fields E_i: for each grid in order, d blocks of 2^|l_i| values
- * (E_1 block, E_2 block, ...).  FP64 host buffer, cap in doubles. */
+ * (E_1 block, E_2 block, ...).  FP64 host buffer, cap in doubles.
+ * SG_ERR_STATE in SG_MODE_FILTER (no component fields are solved). */
 int sg_pic_get_grid_field(sg_pic* h, double* E, size_t cap);
 
 /* Regular-grid charge density rho~ of the current positions (the tau = n
@@ -196,7 +206,8 @@ int sg_pic_kernel_launches(sg_pic* h, unsigned long long* count);
 
 /* Device-event timing of the run's last sg_pic_step call, per stage
  * (0 gather-push, 1 sort, 2 deposit, 3 restrict, 4 solve, 5 combine) in
- * milliseconds, summed over that call's steps.  Enabled with
+ * milliseconds, summed over that call's steps; in SG_MODE_FILTER entry 4 is
+ * the density filter (sum_i c_i P_i R_i) and entry 5 the regular-grid solve.  Enabled with
  * sg_pic_set_profiling(h, 1), which replaces graph replay by direct launches
  * with events between the stages while on.  With cap >= 9, entries 6..8
  * report the init-time autotuner: the solve variant in use (0 per-axis

@@ -413,13 +413,18 @@ class OracleRun:
     """
 
     def __init__(self, L, n, u, v, q, dt, qm=-1.0, tau=1, B=(0.0, 0.0, 0.0),
-                 eext_lin=(0.0, 0.0, 0.0), mode="combine"):
+                 eext_lin=(0.0, 0.0, 0.0), mode="combine", alpha=0.01, pc_ref=5.0, tau_constants="paper"):
         # mode "combine": sparse PIC, fields solved per component grid and
         # combined (Section 4.1); "filter": the density is deposited on the
         # regular grid, filtered (eq. sparse_filter) and solved once there
-        # (Algorithm 2).
+        # (Algorithm 2).  tau = "adaptive": Algorithm 1 picks tau from the
+        # regular-grid density before every field evaluation (alpha, pc_ref,
+        # tau_constants are its parameters).
         assert mode in ("combine", "filter")
         self.mode = mode
+        self.adaptive = tau == "adaptive"
+        self.alpha, self.pc_ref, self.tau_constants = float(alpha), float(pc_ref), tau_constants
+        self.tau_history = []
         self.L = [float(x) for x in L]
         self.n = int(n)
         self.u = wrap_unit(np.array(u, dtype=np.float64))
@@ -428,7 +433,7 @@ class OracleRun:
         self.q = np.array(q, dtype=np.float64)
         self.dt = float(dt)
         self.qm = float(qm)
-        self.tau = int(tau)
+        self.tau = 1 if self.adaptive else int(tau)
         self.B = [float(b) for b in B]
         self.eext = [float(e) for e in eext_lin]
         self.step_count = 0
@@ -439,6 +444,11 @@ class OracleRun:
         self.v = kick_rotate(self.v, E, self.qm, -0.5 * self.dt, self.B)
 
     def _fields(self):
+        if self.adaptive:
+            rho = deposit_cic(self.u, self.q, (self.n,) * self.d, self.L)
+            self.tau = tau_estimator(rho, len(self.q), self.L[0], self.alpha, self.pc_ref,
+                                     float(np.sum(self.q)), self.tau_constants)[0]
+            self.tau_history.append(self.tau)
         if self.mode == "combine":
             self.comps = component_fields(self.u, self.q, self.n, self.tau, self.L)
         else:  # component densities only (diagnostics), field on the regular grid

@@ -29,6 +29,7 @@ SG_TAU_CONST_PAPER = 0
 SG_TAU_CONST_EMPIRICAL = 1
 SG_REQ_QUEUED, SG_REQ_RUNNING, SG_REQ_DONE, SG_REQ_FAILED = 0, 1, 2, 3
 SG_SERVE_BATCHED, SG_SERVE_PLAIN = 0, 1
+SG_MODE_COMBINE, SG_MODE_FILTER = 0, 1
 
 
 class sg_domain(C.Structure):
@@ -49,7 +50,7 @@ class sg_params(C.Structure):
     _fields_ = [("precision", C.c_int), ("tau", C.c_int), ("dt", C.c_double), ("qm", C.c_double),
                 ("B", C.c_double * 3), ("Eext_lin", C.c_double * 3), ("alpha", C.c_double),
                 ("pc_ref", C.c_double), ("tau_constants", C.c_int), ("sort_every", C.c_int),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("mode", C.c_int)]
 
 
 class sg_diag(C.Structure):

@@ -105,6 +105,9 @@ int sg_pic_init(const sg_domain* domain, int level_n, int dim, int shape_order, 
   cfg.pc_ref = params->pc_ref;
   cfg.tau_constants = params->tau_constants;
   cfg.sort_every = params->sort_every;
+  if (params->mode != SG_MODE_COMBINE && params->mode != SG_MODE_FILTER)
+    return invalid("sg_pic_init: mode must be SG_MODE_COMBINE or SG_MODE_FILTER");
+  cfg.mode = params->mode;
 
   sg_pic* h = new (std::nothrow) sg_pic;
   if (!h) return SG_ERR_OOM;

@@ -223,12 +223,16 @@ __device__ __forceinline__ void combine_finalize(const double* partials, int n_p
 // component) and the bytes of its per-warp row-term tables.
 template <int D>
 constexpr int combine_rows_per_block() { return D == 2 ? 4 : 2; }
-template <typename real, int D>
+template <typename real, int D, int NC>
 __host__ __device__ constexpr size_t combine_table_bytes(int ngl) {
-  return ((size_t)combine_rows_per_block<D>() * D * ngl * sizeof(RowTerm<real, D>) + 15) / 16 * 16;
+  return ((size_t)combine_rows_per_block<D>() * NC * ngl * sizeof(RowTerm<real, D>) + 15) / 16 * 16;
 }
+// Stride of the output between nodes: NC = D fields are stored
+// node-interleaved (ec_stride), a single density plainly.
+template <int D, int NC>
+constexpr int combine_out_stride() { return NC == 1 ? 1 : ec_stride<D>(); }
 
-template <typename real, int D, int V>
+template <typename real, int D, int V, int NC>
 __global__ void __launch_bounds__(256) k_combine_warp(const GridDesc* __restrict__ grids, LevelLists ll, int lmin,
                                                       const real* __restrict__ E, size_t S, int n,
                                                       real* __restrict__ Ehi, float* __restrict__ Elo,
@@ -241,7 +245,7 @@ __global__ void __launch_bounds__(256) k_combine_warp(const GridDesc* __restrict
   const int wib = threadIdx.x >> 5;
   const int task = blockIdx.x * (blockDim.x >> 5) + wib;  // (row, component)
   const int lane = threadIdx.x & 31;
-  const int m = task % D, row = task / D;
+  const int m = task % NC, row = task / NC;
   const int y = row & (N - 1);
   const int z = D == 3 ? (row >> n) : 0;
   const real* Em = E + (size_t)m * S;
@@ -251,12 +255,12 @@ __global__ void __launch_bounds__(256) k_combine_warp(const GridDesc* __restrict
     for (int i = 0; i < 18; ++i) s_start[i] = ll.start[i];  // constant indices: no local copy
   }
   const int ngl = ll.start[17];
-  constexpr int RPB = combine_rows_per_block<D>();  // the block's lines: all D components of each
-  constexpr int DP = ec_stride<D>();
+  constexpr int RPB = combine_rows_per_block<D>();  // the block's lines: all NC components of each
+  constexpr int DP = combine_out_stride<D, NC>();
   RowTerm<real, D>* rt_tab = reinterpret_cast<RowTerm<real, D>*>(smem_raw) + (size_t)wib * ngl;
   // [RPB][N][DP] with one padding word after every V nodes (a lane's run), so
   // that the lanes' stores of one step fall in distinct banks
-  real* stage = reinterpret_cast<real*>(smem_raw + combine_table_bytes<real, D>(ngl));
+  real* stage = reinterpret_cast<real*>(smem_raw + combine_table_bytes<real, D, NC>(ngl));
   const int row0 = blockIdx.x * RPB;
   pdl_trigger();
   for (int gi = lane; gi < ngl; gi += 32) rt_tab[gi] = row_term<real, D>(grids[ll.grid[gi]], n, y, z);
@@ -308,8 +312,9 @@ __global__ void __launch_bounds__(256) k_combine_warp(const GridDesc* __restrict
               energy = fmaf(v[q].hi, v[q].hi, energy);
               srow[(size_t)(lane * V + k + q) * DP + lane] = v[q].hi;
             }
-            *reinterpret_cast<float4*>(Elo + o0 + (size_t)lane * V + k) =
-                make_float4(v[0].lo, v[1].lo, v[2].lo, v[3].lo);
+            if (Elo)
+              *reinterpret_cast<float4*>(Elo + o0 + (size_t)lane * V + k) =
+                  make_float4(v[0].lo, v[1].lo, v[2].lo, v[3].lo);
           }
         } else {
 #pragma unroll
@@ -317,7 +322,7 @@ __global__ void __launch_bounds__(256) k_combine_warp(const GridDesc* __restrict
             if (k < per) {
               const ff v = T[k].normalised();
               srow[(size_t)(lane * per + k) * DP + (lane * per + k) / V] = v.hi;
-              Elo[o0 + (size_t)lane * per + k] = v.lo;
+              if (Elo) Elo[o0 + (size_t)lane * per + k] = v.lo;
               energy = fmaf(v.hi, v.hi, energy);
             }
         }
@@ -340,18 +345,18 @@ __global__ void __launch_bounds__(256) k_combine_warp(const GridDesc* __restrict
   const double tot = warp_sum((double)energy);
   if (lane == 0 && row < rows) partials[task] = tot;
   if (!fin.active) return;
-  combine_finalize(partials, rows * D, fin, red);
+  combine_finalize(partials, rows * NC, fin, red);
 }
 
 // ---------------------------------------------------------------- block-per-line combination (lines > 1024)
 
-template <typename real, int D>
+template <typename real, int D, int NC>
 __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ grids, LevelLists ll, int lmin,
                                                  const real* __restrict__ E, size_t S, int n, real* __restrict__ Ehi,
                                                  float* __restrict__ Elo, double* __restrict__ partials,
                                                  const CombineFinal fin) {
   extern __shared__ unsigned char smem_raw[];
-  Acc<real>* A = reinterpret_cast<Acc<real>*>(smem_raw);  // [D][2N], level l of comp m at m*2N + [2^l, 2^(l+1))
+  Acc<real>* A = reinterpret_cast<Acc<real>*>(smem_raw);  // [NC][2N], level l of comp m at m*2N + [2^l, 2^(l+1))
   __shared__ double red[32];
   const int N = 1 << n;
   const size_t ND = (size_t)N * (D == 2 ? N : (size_t)N * N);
@@ -410,11 +415,11 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
   for (int e = threadIdx.x + (1 << lmin); e < 2 * N; e += blockDim.x) {
     const int l = 31 - __clz(e);
     const int kx = e - (1 << l);
-    Acc<real> acc[D];
+    Acc<real> acc[NC];
     for (int gi = s_start[l]; gi < s_start[l + 1]; ++gi) {
       const real c = s_c[gi];
 #pragma unroll
-      for (int m = 0; m < D; ++m) {
+      for (int m = 0; m < NC; ++m) {
         const real* base = E + (size_t)m * S + kx;
         real val = s_w[gi][0] * base[s_off[gi][0]];
 #pragma unroll
@@ -423,13 +428,13 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
       }
     }
 #pragma unroll
-    for (int m = 0; m < D; ++m) A[m * 2 * N + e] = acc[m];
+    for (int m = 0; m < NC; ++m) A[m * 2 * N + e] = acc[m];
   }
   __syncthreads();
   for (int l = lmin; l < n; ++l) {
     const int cnt = 2 << l;  // size of level l+1
     const int half = 1 << l;
-    for (int e2 = threadIdx.x; e2 < D * cnt; e2 += blockDim.x) {
+    for (int e2 = threadIdx.x; e2 < NC * cnt; e2 += blockDim.x) {
       const int m = e2 >> (l + 1), e = e2 & (cnt - 1);
       Acc<real>* Am = A + m * 2 * N;
       const int k = e >> 1;
@@ -445,11 +450,11 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
   // field energy: each thread sums the squares of its few nodes in the run's
   // precision; the block and the step reduce the partials in FP64
   real energy = (real)0;
-  for (int e2 = threadIdx.x; e2 < D * N; e2 += blockDim.x) {
+  for (int e2 = threadIdx.x; e2 < NC * N; e2 += blockDim.x) {
     const int m = e2 >> n, x = e2 & (N - 1);
     const Acc<real> v = A[m * 2 * N + N + x];
     const size_t o = (size_t)m * ND + (size_t)row * N + x;
-    Ehi[((size_t)row * N + x) * ec_stride<D>() + m] = (real)v.hi();
+    Ehi[((size_t)row * N + x) * combine_out_stride<D, NC>() + m] = (real)v.hi();
     if (Elo) Elo[o] = (float)v.lo();
     energy = fma((real)v.hi(), (real)v.hi(), energy);
   }
@@ -459,7 +464,7 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
   combine_finalize(partials, (int)gridDim.x, fin, red);
 }
 
-template <typename real, int D, int V>
+template <typename real, int D, int V, int NC>
 static int launch_combine_warp(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n,
                                real* Ehi, float* Elo, double* energy_partials, const CombineFinal& fin,
                                cudaStream_t s) {
@@ -467,57 +472,66 @@ static int launch_combine_warp(const GridDesc* grids, const LevelLists& ll, int 
   const long long rows = D == 2 ? N : (long long)N * N;
   constexpr int RPB = combine_rows_per_block<D>();
   const unsigned blocks = (unsigned)(rows / RPB);  // N >= 4: RPB divides the line count
-  const size_t smem = combine_table_bytes<real, D>(ll.start[17]) +
-                      ((size_t)RPB * N * ec_stride<D>() + (size_t)RPB * N / V) * sizeof(real);
+  const size_t smem = combine_table_bytes<real, D, NC>(ll.start[17]) +
+                      ((size_t)RPB * N * combine_out_stride<D, NC>() + (size_t)RPB * N / V) * sizeof(real);
   static bool attr_set = false;
   if (!attr_set && smem > 48 * 1024) {
-    SG_CUDA(cudaFuncSetAttribute(k_combine_warp<real, D, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    SG_CUDA(cudaFuncSetAttribute(k_combine_warp<real, D, V, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
     attr_set = true;
   }
-  SG_CUDA(launch_pdl(k_combine_warp<real, D, V>, dim3(blocks), dim3(32 * RPB * D), smem, s, grids, ll, lmin, E, S, n,
-                     Ehi, Elo, energy_partials, fin));
+  SG_CUDA(launch_pdl(k_combine_warp<real, D, V, NC>, dim3(blocks), dim3(32 * RPB * NC), smem, s, grids, ll, lmin, E,
+                     S, n, Ehi, Elo, energy_partials, fin));
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
 
-template <typename real, int D>
-int launch_combine(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n, real* Ehi,
-                   float* Elo, double* energy_partials, const CombineFinal& fin, cudaStream_t s) {
+template <typename real, int D, int NC>
+static int launch_combine_nc(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n,
+                             real* Ehi, float* Elo, double* energy_partials, const CombineFinal& fin,
+                             cudaStream_t s) {
   const int N = 1 << n;
   switch (N) {  // lines of up to 1024 nodes: warp per line, values in registers
     case 4:
     case 8:
     case 16:
     case 32:
-      return launch_combine_warp<real, D, 1>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 1, NC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     case 64:
-      return launch_combine_warp<real, D, 2>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 2, NC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     case 128:
-      return launch_combine_warp<real, D, 4>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 4, NC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     case 256:
-      return launch_combine_warp<real, D, 8>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 8, NC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     case 512:
-      return launch_combine_warp<real, D, 16>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 16, NC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     case 1024:
-      return launch_combine_warp<real, D, 32>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 32, NC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     default:
       break;
   }
   unsigned rows = (unsigned)(D == 2 ? N : N * N);
-  size_t smem = (size_t)D * 2 * N * sizeof(Acc<real>);
+  size_t smem = (size_t)NC * 2 * N * sizeof(Acc<real>);
   static bool attr_set = false;
   if (!attr_set) {
-    SG_CUDA(cudaFuncSetAttribute(k_combine<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    SG_CUDA(cudaFuncSetAttribute(k_combine<real, D, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  k_combine<real, D><<<rows, 256, smem, s>>>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin);
+  k_combine<real, D, NC><<<rows, 256, smem, s>>>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
 
+template <typename real, int D>
+int launch_combine(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n, real* Ehi,
+                   float* Elo, double* energy_partials, const CombineFinal& fin, cudaStream_t s, int ncomp) {
+  if (ncomp == 1) return launch_combine_nc<real, D, 1>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+  return launch_combine_nc<real, D, D>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+}
+
 #define SG_INST_COMB(real, D)                                                                                   \
   template int launch_combine<real, D>(const GridDesc*, const LevelLists&, int, const real*, size_t, int, real*, \
-                                       float*, double*, const CombineFinal&, cudaStream_t);
+                                       float*, double*, const CombineFinal&, cudaStream_t, int);
 SG_INST_COMB(float, 2)
 SG_INST_COMB(float, 3)
 SG_INST_COMB(double, 2)

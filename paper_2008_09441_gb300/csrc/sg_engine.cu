@@ -114,6 +114,20 @@ class Engine final : public EngineBase {
       SG_CUDA(cudaMemcpyAsync(tw_, tw.data(), tw.size() * sizeof(cplx<real>), cudaMemcpyHostToDevice, stream_));
       SG_CUDA(cudaStreamSynchronize(stream_));
     }
+    filter_ = cfg.mode == SG_MODE_FILTER;
+    if (filter_) {
+      SG_TRY(alloc((void**)&rho_f_, ND_ * sizeof(real)));
+      SG_TRY(alloc((void**)&regA_, ND_ * sizeof(cplx<real>)));
+      SG_TRY(alloc((void**)&regB_, ND_ * sizeof(cplx<real>)));
+      std::vector<real> kt((size_t)D * N_);
+      for (int m = 0; m < D; ++m)
+        for (int i = 0; i < N_; ++i)
+          kt[(size_t)m * N_ + i] = (real)(2.0 * M_PI / cfg_.L[m] * (double)(i < N_ / 2 ? i : i - N_));
+      SG_TRY(alloc((void**)&ktab_, kt.size() * sizeof(real)));
+      SG_CUDA(cudaMemcpyAsync(ktab_, kt.data(), kt.size() * sizeof(real), cudaMemcpyHostToDevice, stream_));
+      reg_blocks_ = (int)std::min<size_t>(152 * 8, (ND_ + 255) / 256);
+      SG_TRY(alloc((void**)&reg_partials_, (size_t)2 * reg_blocks_ * sizeof(double)));
+    }
 
     // ---- charges: sum_p q_p in FP64 (fixed during the run)
     {
@@ -138,9 +152,24 @@ class Engine final : public EngineBase {
     SG_TRY(build_grid_set(tau_));
     // Initial state: sort, fields at t = 0, backward half kick.
     SG_TRY(enqueue_sort());
-    SG_TRY(enqueue_fields());
-    SG_TRY(tune_solve());
-    SG_TRY(enqueue_combine(false));
+    if (adaptive_) {  // Algorithm 1 on the initial density picks the first tau
+      SG_TRY(enqueue_deposit());
+      int t = tau_;
+      const int st = select_tau(&t, nullptr, nullptr, 0);
+      if (st == SG_OK && t != tau_) {
+        SG_CUDA(cudaStreamSynchronize(stream_));
+        SG_TRY(build_grid_set(t));
+      } else if (st != SG_OK && st != SG_ERR_RANGE) {
+        return st;
+      }
+      SG_TRY(enqueue_restrict_solve_combine());
+    } else {
+      SG_TRY(enqueue_fields());
+    }
+    if (!filter_) {  // pick the solve variant, then recompute with it
+      SG_TRY(tune_solve());
+      SG_TRY(enqueue_combine(false));
+    }
     SG_TRY(enqueue_push(-0.5 * cfg_.dt, false, nullptr));
     SG_CUDA(cudaStreamSynchronize(stream_));
     step_ = 0;
@@ -307,6 +336,7 @@ class Engine final : public EngineBase {
     SG_CUDA(cudaStreamSynchronize(stream_));
     SG_TRY(build_grid_set(tau));
     SG_TRY(enqueue_restrict());
+    if (filter_) return enqueue_filter_field(nullptr);
     SG_TRY(tune_solve());
     SG_TRY(enqueue_combine(true, nullptr));
     return SG_OK;
@@ -388,6 +418,10 @@ class Engine final : public EngineBase {
   }
 
   int get_grid_field(double* E, size_t cap) override {
+    if (filter_) {
+      set_error("sg_pic_get_grid_field: the filter mode solves no component fields");
+      return SG_ERR_STATE;
+    }
     if (cap < (size_t)D * S_) return size_error("sg_pic_get_grid_field");
     std::vector<double> all((size_t)D * S_);
     SG_TRY(copy_to_host_double(E_arena_, all.data(), (size_t)D * S_));
@@ -1024,10 +1058,34 @@ class Engine final : public EngineBase {
     fin.dd = dd_;
     fin.counter = comb_counter_;
     return launch_combine<real, D>(grids_dev_, levels_, lmin_, E_arena_, S_, n_, Ehi_, Elo_, fe_partials_, fin,
-                                   stream_);
+                                   stream_, D);
+  }
+
+  // Filter mode (Algorithm 2): rho_f = sum_i c_i P_i R_i rho~ on the regular
+  // nodes (the combination kernel on the component densities), then one
+  // spectral solve there; closes the step's FP64 bookkeeping.
+  int enqueue_filter_density() {
+    CombineFinal off;
+    std::memset(&off, 0, sizeof(off));
+    return launch_combine<real, D>(grids_dev_, levels_, lmin_, rho_arena_, S_, n_, rho_f_, nullptr, fe_partials_, off,
+                                   stream_, 1);
+  }
+  int enqueue_regular_solve(const double* ke) {
+    SG_TRY(launch_regular_solve<real>(rho_f_, regA_, regB_, ktab_, tw_, D, n_, Ehi_, Elo_, ec_stride<D>(),
+                                      reg_partials_, reg_blocks_, stream_));
+    return launch_finalize_step(reg_partials_, reg_blocks_ * ((D + 1) / 2), ke, ke ? nke_ : 0, fe_scale(), dd_,
+                                stream_);
+  }
+  int enqueue_filter_field(const double* ke) {
+    SG_TRY(enqueue_filter_density());
+    return enqueue_regular_solve(ke);
   }
 
   int enqueue_restrict_solve_combine(const double* ke = nullptr) {
+    if (filter_) {
+      SG_TRY(enqueue_restrict());
+      return enqueue_filter_field(ke);
+    }
     SG_TRY(enqueue_restrict());
     SG_TRY(enqueue_solve());
     return enqueue_combine(true, ke);
@@ -1091,9 +1149,15 @@ class Engine final : public EngineBase {
     SG_CUDA(cudaEventRecord(ev_[3], stream_));
     SG_TRY(enqueue_restrict());
     SG_CUDA(cudaEventRecord(ev_[4], stream_));
-    SG_TRY(enqueue_solve());
-    SG_CUDA(cudaEventRecord(ev_[5], stream_));
-    SG_TRY(enqueue_combine(true, ke_partials_));
+    if (filter_) {  // 4: the density filter, 5: the regular-grid solve
+      SG_TRY(enqueue_filter_density());
+      SG_CUDA(cudaEventRecord(ev_[5], stream_));
+      SG_TRY(enqueue_regular_solve(ke_partials_));
+    } else {
+      SG_TRY(enqueue_solve());
+      SG_CUDA(cudaEventRecord(ev_[5], stream_));
+      SG_TRY(enqueue_combine(true, ke_partials_));
+    }
     SG_CUDA(cudaEventRecord(ev_[6], stream_));
     SG_CUDA(cudaEventSynchronize(ev_[6]));
     for (int i = 0; i < 6; ++i) {
@@ -1151,6 +1215,14 @@ class Engine final : public EngineBase {
   double* ke_partials_ = nullptr;
   double* fe_partials_ = nullptr;
   unsigned* comb_counter_ = nullptr;
+  // filter mode (Algorithm 2): filtered density, regular-grid transform buffers
+  bool filter_ = false;
+  real* rho_f_ = nullptr;
+  cplx<real>* regA_ = nullptr;
+  cplx<real>* regB_ = nullptr;
+  real* ktab_ = nullptr;
+  double* reg_partials_ = nullptr;
+  int reg_blocks_ = 0;
   int nke_ = 0, nrows_ = 0;
 
   real* rho_reg_ = nullptr;

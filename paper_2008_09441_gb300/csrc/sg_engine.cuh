@@ -30,6 +30,7 @@ struct EngineConfig {
   double alpha = 0.01, pc_ref = 5;
   int tau_constants = SG_TAU_CONST_PAPER;
   int sort_every = 0;
+  int mode = SG_MODE_COMBINE;
   int win_cap = 4096;  // deposit window capacity in regular nodes (64-bit accumulators)
 };
 

@@ -145,6 +145,14 @@ int launch_solve_small(const SolveArena<real>& a, int ngrids, int max_size, cuda
 template <typename real>
 constexpr int small_solve_max() { return sizeof(real) == 4 ? 4096 : 2048; }
 
+// The filter mode's regular-grid solve: rho_f -> E on the regular nodes
+// (E_hi node-interleaved with `stride`, FP32 low planes zeroed), per-block
+// field-energy partials at partials[pair * blocks + block] (ceil(dim/2) pairs).
+template <typename real>
+int launch_regular_solve(const real* rho_f, cplx<real>* A, cplx<real>* B, const real* ktab, const cplx<real>* tw,
+                         int dim, int n, real* Ehi, float* Elo, int stride, double* partials, int blocks,
+                         cudaStream_t s);
+
 // Generic in-place complex FFT of a whole N^D array (regular grid) along one
 // axis, forward or inverse (unnormalised), in the given precision.
 template <typename real>
@@ -244,7 +252,7 @@ struct CombineFinal {
 template <typename real, int D>
 int launch_combine(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n,
                    real* Ehi, float* Elo, double* energy_partials, const CombineFinal& fin,
-                   cudaStream_t s);
+                   cudaStream_t s, int ncomp);  // ncomp = D: the fields, interleaved; 1: a density, plain
 
 template <typename real>
 int launch_grid_charges(const GridDesc* grids, int ngrids, const real* rho, const double* vol,

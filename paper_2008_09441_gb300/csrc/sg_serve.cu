@@ -145,6 +145,7 @@ static int admit(sg_server* s, bool* changed, int* failed) {
     cfg.pc_ref = q.params.pc_ref;
     cfg.tau_constants = q.params.tau_constants;
     cfg.sort_every = q.params.sort_every;
+    cfg.mode = q.params.mode;
     sg_particles hp;
     std::memset(&hp, 0, sizeof(hp));
     hp.n = q.particles.n;
@@ -280,6 +281,8 @@ int sg_serve_submit(sg_server* s, const sg_request* req, unsigned long long* tic
   if (!s || !req || !ticket) return serr("sg_serve_submit: NULL argument");
   const sg_particles& p = req->particles;
   if (p.on_device) return serr("sg_serve_submit: particle arrays must be host memory", SG_ERR_UNSUPPORTED);
+  if (req->params.mode != SG_MODE_COMBINE && req->params.mode != SG_MODE_FILTER)
+    return serr("sg_serve_submit: mode must be SG_MODE_COMBINE or SG_MODE_FILTER");
   if (req->dim != 2 && req->dim != 3) return serr("sg_serve_submit: dim must be 2 or 3");
   if (req->nsteps < 0) return serr("sg_serve_submit: nsteps < 0");
   if (req->params.tau == SG_TAU_ADAPTIVE) return serr("sg_serve_submit: adaptive tau is not served", SG_ERR_UNSUPPORTED);

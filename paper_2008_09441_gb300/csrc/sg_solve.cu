@@ -400,6 +400,111 @@ int launch_fft_array_axis(cplx<real>* data, int D, int logn, int axis, bool inve
   return SG_OK;
 }
 
+// ---------------------------------------------------------------- filter mode: the regular-grid solve
+//
+// Algorithm 2's field step on the 2^{dn} regular nodes: F(rho_f) (a complex
+// copy transformed along every axis), then per pair of field components
+// B = E^_a + i E^_b with E^_m = -i k_m rho^ / |k|^2 (k = 0 and the Nyquist
+// plane of axis m -> 0, the component-grid rules), the inverse transform
+// along every axis, and the real / imaginary parts as E_a / E_b.
+
+template <typename real>
+__global__ void k_regular_pack(const real* __restrict__ rho, cplx<real>* __restrict__ a, size_t nd) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += (size_t)gridDim.x * blockDim.x)
+    a[i] = {rho[i], (real)0};
+}
+
+// ktab[m * N + i] = 2 pi / L_m * (i < N/2 ? i : i - N), in the run's precision.
+template <typename real>
+__global__ void k_regular_spectral(const cplx<real>* __restrict__ A, cplx<real>* __restrict__ B, int dim, int n,
+                                   const real* __restrict__ ktab, int pair, real norm) {
+  const int N = 1 << n, mask = N - 1;
+  const size_t nd = (size_t)1 << (dim * n);
+  const int ma = 2 * pair, mb = 2 * pair + 1;  // mb == dim: no second component
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += (size_t)gridDim.x * blockDim.x) {
+    real k2 = 0, ka = 0, kb = 0;
+    bool nyq_a = false, nyq_b = false;
+    for (int q = 0; q < dim; ++q) {
+      const int idx = (int)(i >> (q * n)) & mask;
+      const real kq = ktab[q * N + idx];
+      k2 += kq * kq;
+      if (q == ma) {
+        ka = kq;
+        nyq_a = idx == (N >> 1);
+      }
+      if (q == mb) {
+        kb = kq;
+        nyq_b = idx == (N >> 1);
+      }
+    }
+    const cplx<real> r = A[i];
+    cplx<real> out = {(real)0, (real)0};
+    if (k2 != (real)0) {
+      const real inv = norm / k2;
+      if (!nyq_a) {  // -i k_a rho^ / |k|^2
+        const real fa = ka * inv;
+        out.x += r.y * fa;
+        out.y -= r.x * fa;
+      }
+      if (mb < dim && !nyq_b) {  // + i (-i k_b rho^ / |k|^2)
+        const real fb = kb * inv;
+        out.x += r.x * fb;
+        out.y += r.y * fb;
+      }
+    }
+    B[i] = out;
+  }
+}
+
+// E_hi[node * stride + 2p (+1)] from the pair's inverse transform; the FP32
+// path's low planes of these components are zero.  Per-block partials of
+// sum |E|^2 at partials[pair * gridDim.x + block].
+template <typename real>
+__global__ void __launch_bounds__(256) k_regular_field_out(const cplx<real>* __restrict__ B, real* __restrict__ Ehi,
+                                                           float* __restrict__ Elo, int dim, int stride, size_t nd,
+                                                           int pair, double* __restrict__ partials) {
+  __shared__ double red[32];
+  const int ma = 2 * pair, mb = 2 * pair + 1;
+  real energy = (real)0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += (size_t)gridDim.x * blockDim.x) {
+    const cplx<real> v = B[i];
+    Ehi[i * stride + ma] = v.x;
+    energy = fma(v.x, v.x, energy);
+    if (Elo) Elo[(size_t)ma * nd + i] = 0.f;
+    if (mb < dim) {
+      Ehi[i * stride + mb] = v.y;
+      energy = fma(v.y, v.y, energy);
+      if (Elo) Elo[(size_t)mb * nd + i] = 0.f;
+    }
+  }
+  const double tot = block_sum_double((double)energy, red);
+  if (threadIdx.x == 0) partials[(size_t)pair * gridDim.x + blockIdx.x] = tot;
+}
+
+template <typename real>
+int launch_regular_solve(const real* rho_f, cplx<real>* A, cplx<real>* B, const real* ktab, const cplx<real>* tw,
+                         int dim, int n, real* Ehi, float* Elo, int stride, double* partials, int blocks,
+                         cudaStream_t s) {
+  const size_t nd = (size_t)1 << (dim * n);
+  k_regular_pack<real><<<blocks, 256, 0, s>>>(rho_f, A, nd);
+  SG_CHECK_LAUNCH();
+  for (int ax = 0; ax < dim; ++ax) SG_TRY(launch_fft_array_axis<real>(A, dim, n, ax, false, tw, n, s));
+  const real norm = (real)(1.0 / (double)nd);
+  for (int p = 0; 2 * p < dim; ++p) {
+    k_regular_spectral<real><<<blocks, 256, 0, s>>>(A, B, dim, n, ktab, p, norm);
+    SG_CHECK_LAUNCH();
+    for (int ax = 0; ax < dim; ++ax) SG_TRY(launch_fft_array_axis<real>(B, dim, n, ax, true, tw, n, s));
+    k_regular_field_out<real><<<blocks, 256, 0, s>>>(B, Ehi, Elo, dim, stride, nd, p, partials);
+    SG_CHECK_LAUNCH();
+  }
+  return SG_OK;
+}
+template int launch_regular_solve<float>(const float*, cplx<float>*, cplx<float>*, const float*, const cplx<float>*,
+                                         int, int, float*, float*, int, double*, int, cudaStream_t);
+template int launch_regular_solve<double>(const double*, cplx<double>*, cplx<double>*, const double*,
+                                          const cplx<double>*, int, int, double*, float*, int, double*, int,
+                                          cudaStream_t);
+
 template int launch_fft_pass<float>(int, const SolveArena<float>&, const FftJob*, int, int, int, cudaStream_t);
 template int launch_fft_pass<double>(int, const SolveArena<double>&, const FftJob*, int, int, int, cudaStream_t);
 template int launch_fft_array_axis<float>(cplx<float>*, int, int, int, bool, const cplx<float>*, int, cudaStream_t);

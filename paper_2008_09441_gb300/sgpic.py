@@ -48,8 +48,12 @@ def _on_device(x):
     return 1 if (_is_torch(x) and x.is_cuda) else 0
 
 
+_MODES = {"combine": L.SG_MODE_COMBINE, "filter": L.SG_MODE_FILTER}
+
+
 def make_params(precision=L.SG_FP32, tau=1, dt=0.05, qm=-1.0, B=(0.0, 0.0, 0.0), eext_lin=(0.0, 0.0, 0.0),
-                alpha=0.01, pc_ref=5.0, tau_constants=L.SG_TAU_CONST_PAPER, sort_every=0, stream=None):
+                alpha=0.01, pc_ref=5.0, tau_constants=L.SG_TAU_CONST_PAPER, sort_every=0, stream=None,
+                mode=L.SG_MODE_COMBINE):
     p = L.sg_params()
     p.precision = precision
     p.tau = tau
@@ -63,6 +67,7 @@ def make_params(precision=L.SG_FP32, tau=1, dt=0.05, qm=-1.0, B=(0.0, 0.0, 0.0),
     p.tau_constants = tau_constants
     p.sort_every = sort_every
     p.stream = stream
+    p.mode = _MODES.get(mode, mode)
     return p
 
 
@@ -140,7 +145,7 @@ class Run:
 
     def __init__(self, L_box, n, u, v, w, dt, *, tau=1, qm=-1.0, precision="fp32", B=(0.0, 0.0, 0.0),
                  eext_lin=(0.0, 0.0, 0.0), alpha=0.01, pc_ref=5.0, tau_constants="paper", sort_every=0,
-                 stream=None):
+                 stream=None, mode="combine"):
         self.d = len(L_box)
         self.n = n
         self.precision = L.SG_FP32 if precision in ("fp32", L.SG_FP32) else L.SG_FP64
@@ -164,7 +169,7 @@ class Run:
         parts.w = _ptr(wcol).value
         tc = L.SG_TAU_CONST_PAPER if tau_constants == "paper" else L.SG_TAU_CONST_EMPIRICAL
         self.params = make_params(self.precision, tau, dt, qm, B, eext_lin, alpha, pc_ref, tc, sort_every,
-                                  stream)
+                                  stream, mode)
         self._keep = (ucols, vcols, wcol)
         self.h = sg_pic_init(dom, n, d, 1, parts, self.params)
         self._keep = None
@@ -328,7 +333,7 @@ class Server:
         self.meta = {}
 
     def submit(self, L_box, n, u, v, w, dt, nsteps, *, tau=1, qm=-1.0, precision="fp32", B=(0.0, 0.0, 0.0),
-               eext_lin=(0.0, 0.0, 0.0), sort_every=0):
+               eext_lin=(0.0, 0.0, 0.0), sort_every=0, mode="combine"):
         d = len(L_box)
         prec = L.SG_FP32 if precision in ("fp32", L.SG_FP32) else L.SG_FP64
         dt_np = _DT[prec]
@@ -347,7 +352,8 @@ class Server:
             req.particles.u[m] = _ptr(ucols[m]).value
             req.particles.v[m] = _ptr(vcols[m]).value
         req.particles.w = _ptr(wcol).value
-        req.params = make_params(prec, tau, dt, qm, B, eext_lin, 0.01, 5.0, L.SG_TAU_CONST_PAPER, sort_every, None)
+        req.params = make_params(prec, tau, dt, qm, B, eext_lin, 0.01, 5.0, L.SG_TAU_CONST_PAPER, sort_every, None,
+                                 mode)
         req.nsteps = int(nsteps)
         t = C.c_ulonglong()
         check(lib().sg_serve_submit(self.h, C.byref(req), C.byref(t)), "sg_serve_submit")
