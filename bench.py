@@ -267,6 +267,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--particles", type=int, default=4194304)
     ap.add_argument("--sort-every", type=int, default=0)
+    ap.add_argument("--mode", default="combine", choices=["combine", "filter"],
+                    help="combine: solves on every component grid, fields combined (the default line); "
+                         "filter: the paper's filter mode (eq. sparse_filter, Algorithm 2)")
     ap.add_argument("--ref-particles", type=int, default=1 << 16)
     ap.add_argument("--ref-budget-s", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -301,7 +304,7 @@ def main():
     q = torch.from_numpy(wl.q.astype(np.float32)).to(dev)
     sort_every = args.sort_every if args.sort_every > 0 else 4  # the library default
     run = Run(wl.L, n, u, v, q, wl.dt, tau=wl.tau, precision="fp32", sort_every=sort_every,
-              stream=stream.cuda_stream)
+              stream=stream.cuda_stream, mode=args.mode)
     del u, v, q
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     np_ = wl.n_particles
@@ -375,7 +378,8 @@ def main():
         from paper_2008_09441_gb300 import _lib as L
         import ctypes as C
         t0 = time.perf_counter()
-        r2 = Run(wl.L, n, hu, hv, hq, wl.dt, tau=wl.tau, precision="fp32", sort_every=sort_every, stream=stream.cuda_stream)
+        r2 = Run(wl.L, n, hu, hv, hq, wl.dt, tau=wl.tau, precision="fp32", sort_every=sort_every,
+                 stream=stream.cuda_stream, mode=args.mode)
         diag_bytes = 0
         for _ in range(args.steps):  # a user monitoring the run: step, then read the FP64 diagnostics
             r2.step(1)
@@ -417,6 +421,8 @@ def main():
                "config": {"workload": f"{WORKLOAD}: 2D Landau damping, n=10, tau=1, 19 component grids, "
                                       f"{np_} FP32 particles, dt=0.05",
                           "particles_per_gpu": np_, "sort_every": sort_every, "l2": "flushed before every step",
+                          "mode": args.mode + (" (stage 'solve' = density filter, 'combine' = regular-grid solve)"
+                                               if args.mode == "filter" else ""),
                           "combine": "float-float (48-bit) accumulation, FP64 diagnostics",
                           "parallelism": f"{world} independent replicas"},
                "latency_ms": {"p50": p50, "p99": p99},
