@@ -357,7 +357,11 @@ template <typename real>
 __global__ void __launch_bounds__(256) k_fft_array(cplx<real>* data, int D, int logn, int axis, int inverse,
                                                    const cplx<real>* __restrict__ tw, int log_nmax, int C) {
   extern __shared__ unsigned char smem_raw[];
-  cplx<real>* buf = reinterpret_cast<cplx<real>*>(smem_raw);
+  // twiddles staged in shared memory, then the lines
+  cplx<real>* tws = reinterpret_cast<cplx<real>*>(smem_raw);
+  const int ntw = 1 << (log_nmax - 1);
+  for (int e = threadIdx.x; e < ntw; e += blockDim.x) tws[e] = tw[e];
+  cplx<real>* buf = tws + ntw;
   const int len = 1 << logn;
   const long long line0 = (long long)blockIdx.x * C;  // C is a power of two dividing the line count
   const int nl = C;
@@ -370,7 +374,7 @@ __global__ void __launch_bounds__(256) k_fft_array(cplx<real>* data, int D, int 
     buf[(li << logn) + bitrev(t, logn)] = data[line_addr(line0 + li, t, ls, logn)];
   }
   __syncthreads();
-  fft_smem<real>(buf, nl, logn, inverse != 0, tw, log_nmax);
+  fft_smem<real>(buf, nl, logn, inverse != 0, tws, log_nmax);
   for (int e = threadIdx.x; e < (nl << logn); e += blockDim.x) {
     const int li = contiguous ? (e >> logn) : (e & (nl - 1));
     const int t = contiguous ? (e & (len - 1)) : (e >> logC);
@@ -384,11 +388,11 @@ int launch_fft_array_axis(cplx<real>* data, int D, int logn, int axis, bool inve
   const int len = 1 << logn;
   int C = 2048 / len;
   if (C < 1) C = 1;
-  if (axis > 0 && C < 8) C = 8;  // wider column blocks for coalescing
+  if (axis > 0 && C < 4) C = 4;  // column blocks: 32-byte row pieces (complex float), more blocks than SMs
   long long lines = 1;
   for (int m = 0; m < D - 1; ++m) lines *= len;
   if (C > lines) C = (int)lines;
-  size_t smem = (size_t)C * len * sizeof(cplx<real>);
+  size_t smem = ((size_t)C * len + ((size_t)1 << (log_nmax - 1))) * sizeof(cplx<real>);
   static bool attr_set = false;
   if (!attr_set) {
     SG_CUDA(cudaFuncSetAttribute(k_fft_array<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
