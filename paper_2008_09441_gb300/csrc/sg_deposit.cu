@@ -9,6 +9,8 @@
 // instead of 2^d * n_c scattered adds per particle.
 #include <limits.h>
 
+#include <algorithm>
+
 #include "sg_kernels.cuh"
 
 namespace sg {
@@ -17,11 +19,11 @@ namespace sg {
 //
 // FP32 path: 32-bit fixed point, so the window uses native integer shared
 // atomics and its sums do not depend on the order of the adds.  The scale is
-// the power of two 2^(19 - E) with max_p |q_p| / V < 2^E over the chunk: one
-// contribution is below 2^19 in magnitude, and DEP_CHUNK = 2^11 of them stay
-// below 2^30, so no node overflows.  A contribution is rounded once, to
-// 2^-19 of the chunk's largest charge (the same resolution a float has for
-// a sum of 2^5 such charges).  Because |x| < 2^22, x + 1.5 * 2^23 lands in
+// the power of two 2^(19 - E) with max_p |q_p| / V < 2^E over the run's
+// particles (set at upload): one contribution is below 2^19 in magnitude,
+// and DEP_CHUNK = 2^11 of them stay below 2^30, so no node overflows.  A
+// contribution is rounded once, to 2^-19 of the largest charge (the same
+// resolution a float has for a sum of 2^5 such charges).  Because |x| < 2^22, x + 1.5 * 2^23 lands in
 // [2^23, 2^24), where the float spacing is 1: its low mantissa bits are
 // round-to-nearest-even(x), with no conversion instruction.
 //
@@ -65,268 +67,223 @@ __device__ __forceinline__ void cell_frac(double s, int mask, int& c, double& f)
 
 // ---------------------------------------------------------------- deposit
 //
-// Each block takes DEP_CHUNK consecutive particles (consecutive in tile-key
-// order after a sort, so they occupy a compact block of cells).  All of them
-// are loaded first (16-byte vector loads); the chunk's middle particle fixes
-// the anchor cell and the periodic bounding box of the chunk's cells sizes a
-// window of regular nodes in shared memory, accumulated with WinAcc.  The
-// window is then added to the global grid row by row (coalesced atomics,
-// zero nodes skipped).  Corners outside a window clamped to the
-// shared-memory capacity add directly to the global grid.
+// Persistent blocks walk chunks of DEP_CHUNK consecutive particles
+// (consecutive in tile-key order after a sort, so a chunk covers a compact
+// group of cells).  Per chunk every thread reads the chunk's middle particle
+// and takes its cell as the anchor of a fixed window of side^d regular nodes
+// centred on it; its four particles (16-byte vector loads) add their CIC
+// weights into the window when all 2^d corners fall inside, else straight to
+// the global grid.  The window's touched box is then added to the global
+// grid row by row (coalesced atomics, zero nodes skipped) and cleared for the
+// next chunk: two block barriers per chunk, no reductions before the adds.
+//
+// FP32: WinAcc fixed point with the run's scale 2^(19 - E), max_p |q_p|/V <
+// 2^E (set at upload; charges do not change), so a window of at most 2^11
+// particles cannot overflow.  FP64: plain double, scale 1.
 template <typename real, int D>
 __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, size_t np, int n,
-                                                         real inv_cell_vol, real* __restrict__ rho, int side) {
+                                                         real inv_cell_vol, real* __restrict__ rho, int side,
+                                                         real scale, real inv_scale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using W = WinAcc<real>;
   using T = typename W::T;
   T* win = reinterpret_cast<T*>(smem_raw);
-  __shared__ int s_anchor[D], s_min[D], s_max[D];
-  __shared__ unsigned s_qmax;
+  __shared__ int s_box[2][2 * D];  // per chunk parity: lo[D], hi[D] of the touched window
   const int N = 1 << n;
   const int mask = N - 1;
-  const size_t chunk = (size_t)blockIdx.x * DEP_CHUNK;
   const int lane = threadIdx.x & 31;
-  pdl_trigger();  // the restriction may start launching
-
-  // ---- load the chunk: DEP_ITEMS / 4 vectors of four consecutive particles
-  real ub[DEP_ITEMS][D], wb[DEP_ITEMS];
-#pragma unroll
-  for (int j = 0; j < DEP_ITEMS / 4; ++j) {
-    const size_t i0 = chunk + ((size_t)j * DEP_THREADS + threadIdx.x) * 4;
-    if (i0 + 4 <= np) {
-#pragma unroll
-      for (int m = 0; m < D; ++m) {
-        V4<real> t = ld4(p.u[m] + i0);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) ub[4 * j + k][m] = t.x[k];
-      }
-      V4<real> t = ld4(p.w + i0);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) wb[4 * j + k] = t.x[k];
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const bool ok = i0 + k < np;
-#pragma unroll
-        for (int m = 0; m < D; ++m) ub[4 * j + k][m] = ok ? p.u[m][i0 + k] : (real)0;
-        wb[4 * j + k] = ok ? p.w[i0 + k] : (real)0;
-      }
-    }
-  }
-  // ---- anchor: the cell of the chunk's middle (or last) particle
-  {
-    size_t mid = chunk + DEP_CHUNK / 2;
-    if (mid >= np) mid = np - 1;
-    const int rel = (int)(mid - chunk);
-    const int holder = (rel & (DEP_THREADS * 4 - 1)) >> 2;
-    if ((int)threadIdx.x == holder) {
-      const int item = 4 * (rel / (DEP_THREADS * 4)) + (rel & 3);
-#pragma unroll
-      for (int it = 0; it < DEP_ITEMS; ++it)
-        if (it == item) {
-#pragma unroll
-          for (int m = 0; m < D; ++m) s_anchor[m] = cell_of(ub[it][m], n, N);
-        }
-    }
-    if (threadIdx.x < D) {
-      s_min[threadIdx.x] = INT_MAX;
-      s_max[threadIdx.x] = INT_MIN;
-    }
-    if (threadIdx.x == 0) s_qmax = 0u;
-  }
-  __syncthreads();
-
-  int c[DEP_ITEMS][D];
-  real f[DEP_ITEMS][D];
-  real q[DEP_ITEMS];
-  int dmin[D], dmax[D];
-  int anchor[D];
-#pragma unroll
-  for (int m = 0; m < D; ++m) {
-    dmin[m] = INT_MAX;
-    dmax[m] = INT_MIN;
-    anchor[m] = s_anchor[m];
-  }
-  unsigned qbits = 0u;  // max |q| as float bits (order-preserving for >= 0)
-#pragma unroll
-  for (int it = 0; it < DEP_ITEMS; ++it) {
-    const size_t i = chunk + ((size_t)(it >> 2) * DEP_THREADS + threadIdx.x) * 4 + (it & 3);
-    if (i < np) {
-#pragma unroll
-      for (int m = 0; m < D; ++m) {
-        cell_frac(ub[it][m] * (real)N, mask, c[it][m], f[it][m]);
-        const int dd = ((c[it][m] - anchor[m] + (N >> 1)) & mask) - (N >> 1);
-        dmin[m] = min(dmin[m], dd);
-        dmax[m] = max(dmax[m], dd);
-      }
-      q[it] = wb[it] * inv_cell_vol;
-      if (W::fixed) qbits = max(qbits, __float_as_uint(fabsf((float)q[it])));
-    } else {
-      q[it] = (real)0;
-#pragma unroll
-      for (int m = 0; m < D; ++m) {
-        c[it][m] = anchor[m];
-        f[it][m] = (real)0;
-      }
-    }
-  }
-#pragma unroll
-  for (int m = 0; m < D; ++m) {
-    dmin[m] = __reduce_min_sync(0xffffffffu, dmin[m]);
-    dmax[m] = __reduce_max_sync(0xffffffffu, dmax[m]);
-  }
-  if (W::fixed) qbits = __reduce_max_sync(0xffffffffu, qbits);
-  if (lane == 0) {
-#pragma unroll
-    for (int m = 0; m < D; ++m) {
-      atomicMin(&s_min[m], dmin[m]);
-      atomicMax(&s_max[m], dmax[m]);
-    }
-    if (W::fixed) atomicMax(&s_qmax, qbits);
-  }
-  __syncthreads();
-
-  // ---- window and fixed-point scale (every thread derives the same values)
-  int org[D], ext[D];
+  const int half = side >> 1;
   int nwin = 1;
 #pragma unroll
-  for (int m = 0; m < D; ++m) {
-    int lo = s_min[m];
-    int e = s_max[m] - lo + 2;  // +1 node for the upper corner
-    if (e >= N) {               // the window spans the whole axis
-      e = N;
-      lo = -(N >> 1);
-    }
-    if (e > side) {  // clamp around the anchor; outliers add to global
-      e = side;
-      lo = -(side >> 1);
-    }
-    org[m] = (anchor[m] + lo) & mask;
-    ext[m] = e;
-    nwin *= e;
-  }
-  real scale = (real)1, inv_scale = (real)1;
-  if (W::fixed) {
-    // max |q| < 2^E with E = (biased exponent) - 126; scale 2^(19 - E),
-    // kept inside the normal float range.
-    const int E = (int)(s_qmax >> 23) - 126;
-    const int k = max(-126, min(127, 19 - E));
-    scale = (real)__int_as_float((127 + k) << 23);
-    inv_scale = (real)__int_as_float((127 - k) << 23);
-  }
+  for (int m = 0; m < D; ++m) nwin *= side;
+  pdl_trigger();  // the restriction may start launching
   {
     uint4* w4 = reinterpret_cast<uint4*>(smem_raw);
     const int n4 = (int)((nwin * sizeof(T) + 15) / 16);
     for (int i = threadIdx.x; i < n4; i += DEP_THREADS) w4[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (threadIdx.x < 2 * D) {
+      s_box[0][threadIdx.x] = threadIdx.x < D ? INT_MAX : INT_MIN;
+      s_box[1][threadIdx.x] = threadIdx.x < D ? INT_MAX : INT_MIN;
+    }
   }
-  __syncthreads();
-
+  const size_t nchunks = (np + DEP_CHUNK - 1) / DEP_CHUNK;
+  int par = 0;
+  for (size_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x, par ^= 1) {
+    const size_t chunk = ch * DEP_CHUNK;
+    // ---- this thread's particles: DEP_ITEMS / 4 vectors of four
+    real ub[DEP_ITEMS][D], qb[DEP_ITEMS];
 #pragma unroll
-  for (int it = 0; it < DEP_ITEMS; ++it) {
-    if (q[it] == (real)0) continue;
-    // fast path: all 2^d corners inside the window (the common case)
-    int lc[D];
-    bool fast = true;
+    for (int j = 0; j < DEP_ITEMS / 4; ++j) {
+      const size_t i0 = chunk + ((size_t)j * DEP_THREADS + threadIdx.x) * 4;
+      if (i0 + 4 <= np) {
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+          const V4<real> t = ld4(p.u[m] + i0);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) ub[4 * j + k][m] = t.x[k];
+        }
+        const V4<real> t = ld4(p.w + i0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qb[4 * j + k] = t.x[k] * inv_cell_vol;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const bool ok = i0 + k < np;
+#pragma unroll
+          for (int m = 0; m < D; ++m) ub[4 * j + k][m] = ok ? p.u[m][i0 + k] : (real)0;
+          qb[4 * j + k] = ok ? p.w[i0 + k] * inv_cell_vol : (real)0;
+        }
+      }
+    }
+    // ---- anchor: the cell of the chunk's middle (or last) particle, read by every thread
+    int anchor[D];
+    {
+      size_t mid = chunk + DEP_CHUNK / 2;
+      if (mid >= np) mid = np - 1;
+#pragma unroll
+      for (int m = 0; m < D; ++m) anchor[m] = cell_of(__ldg(p.u[m] + mid), n, N);
+    }
+    __syncthreads();  // the previous chunk's flush has cleared the window
+    if (threadIdx.x < 2 * D) s_box[par ^ 1][threadIdx.x] = threadIdx.x < D ? INT_MAX : INT_MIN;
+    int lo[D], hi[D];
 #pragma unroll
     for (int m = 0; m < D; ++m) {
-      lc[m] = (c[it][m] - org[m]) & mask;
-      fast &= lc[m] + 1 < ext[m];
-    }
-    if (fast) {
-      const real qs = q[it] * scale;
-      const real wx0 = (real)1 - f[it][0], wx1 = f[it][0];
-      if (D == 2) {
-        const int base = lc[0] + ext[0] * lc[1 % D];
-        const real a = qs * ((real)1 - f[it][1 % D]), b = qs * f[it][1 % D];
-        atomicAdd(&win[base], W::quantize_fma(a, wx0));
-        atomicAdd(&win[base + 1], W::quantize_fma(a, wx1));
-        atomicAdd(&win[base + ext[0]], W::quantize_fma(b, wx0));
-        atomicAdd(&win[base + ext[0] + 1], W::quantize_fma(b, wx1));
-      } else {
-        const int sy = ext[0], sz = ext[0] * ext[1 % D];
-        const int base = lc[0] + sy * lc[1 % D] + sz * lc[(D - 1)];
-        const real wy[2] = {(real)1 - f[it][1 % D], f[it][1 % D]};
-        const real wz[2] = {(real)1 - f[it][D - 1], f[it][D - 1]};
-#pragma unroll
-        for (int kz = 0; kz < 2; ++kz)
-#pragma unroll
-          for (int ky = 0; ky < 2; ++ky) {
-            const real a = qs * wz[kz] * wy[ky];
-            const int o = base + kz * sz + ky * sy;
-            atomicAdd(&win[o], W::quantize_fma(a, wx0));
-            atomicAdd(&win[o + 1], W::quantize_fma(a, wx1));
-          }
-      }
-      continue;
+      lo[m] = INT_MAX;
+      hi[m] = INT_MIN;
     }
 #pragma unroll
-    for (int corner = 0; corner < (1 << D); ++corner) {
-      real wgt = q[it];
-      int loc = 0, glob = 0, lstride = 1, gstride = 1;
-      bool inside = true;
+    for (int it = 0; it < DEP_ITEMS; ++it) {
+      if (qb[it] == (real)0) continue;
+      int c[D], l[D];
+      real f[D];
+      bool fast = true;
 #pragma unroll
       for (int m = 0; m < D; ++m) {
-        const int b = (corner >> m) & 1;
-        wgt *= b ? f[it][m] : ((real)1 - f[it][m]);
-        const int g = (c[it][m] + b) & mask;
-        const int l = (g - org[m]) & mask;
-        inside &= l < ext[m];
-        loc += l * lstride;
-        lstride *= ext[m];
-        glob += g * gstride;
-        gstride *= N;
+        cell_frac(ub[it][m] * (real)N, mask, c[m], f[m]);
+        l[m] = (c[m] - anchor[m] + half) & mask;
+        fast &= l[m] + 1 < side;
       }
-      if (inside) {
-        atomicAdd(&win[loc], W::quantize_fma(wgt, scale));
-      } else {
-        atomicAdd(&rho[glob], wgt);
+      if (fast) {
+        const real qs = qb[it] * scale;
+        const real wx0 = (real)1 - f[0], wx1 = f[0];
+        if (D == 2) {
+          const int base = l[0] + side * l[1 % D];
+          const real a = qs * ((real)1 - f[1 % D]), b = qs * f[1 % D];
+          atomicAdd(&win[base], W::quantize_fma(a, wx0));
+          atomicAdd(&win[base + 1], W::quantize_fma(a, wx1));
+          atomicAdd(&win[base + side], W::quantize_fma(b, wx0));
+          atomicAdd(&win[base + side + 1], W::quantize_fma(b, wx1));
+        } else {
+          const int sz = side * side;
+          const int base = l[0] + side * l[1 % D] + sz * l[D - 1];
+          const real wy[2] = {(real)1 - f[1 % D], f[1 % D]};
+          const real wz[2] = {(real)1 - f[D - 1], f[D - 1]};
+#pragma unroll
+          for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+            for (int ky = 0; ky < 2; ++ky) {
+              const real a = qs * wz[kz] * wy[ky];
+              const int o = base + kz * sz + ky * side;
+              atomicAdd(&win[o], W::quantize_fma(a, wx0));
+              atomicAdd(&win[o + 1], W::quantize_fma(a, wx1));
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+          lo[m] = min(lo[m], l[m]);
+          hi[m] = max(hi[m], l[m] + 1);
+        }
+      } else {  // a corner outside the window: all corners to the global grid
+#pragma unroll 1
+        for (int corner = 0; corner < (1 << D); ++corner) {
+          real wgt = qb[it];
+          size_t g = 0, gs = 1;
+#pragma unroll
+          for (int m = 0; m < D; ++m) {
+            const int bb = (corner >> m) & 1;
+            wgt *= bb ? f[m] : ((real)1 - f[m]);
+            g += (size_t)((c[m] + bb) & mask) * gs;
+            gs *= (size_t)N;
+          }
+          atomicAdd(&rho[g], wgt);
+        }
       }
     }
-  }
-  __syncthreads();
-  // ---- flush: one warp per window row, lanes along x (coalesced atomics)
-  const int rows = nwin / ext[0];
-  for (int r = threadIdx.x >> 5; r < rows; r += DEP_THREADS / 32) {
-    size_t grow;
-    if (D == 2) {
-      grow = (size_t)((org[1 % D] + r) & mask) * N;
-    } else {
-      const int ry = r % ext[1 % D], rz = r / ext[1 % D];
-      grow = ((size_t)((org[D - 1] + rz) & mask) * N + ((org[1 % D] + ry) & mask)) * N;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      lo[m] = __reduce_min_sync(0xffffffffu, lo[m]);
+      hi[m] = __reduce_max_sync(0xffffffffu, hi[m]);
     }
-    const T* wrow = win + (size_t)r * ext[0];
-    for (int x = lane; x < ext[0]; x += 32) {
-      const T sv = wrow[x];
-      if (sv != (T)0) atomicAdd(&rho[grow + ((org[0] + x) & mask)], W::value(sv, inv_scale));
+    if (lane == 0) {
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        atomicMin(&s_box[par][m], lo[m]);
+        atomicMax(&s_box[par][D + m], hi[m]);
+      }
+    }
+    __syncthreads();  // the chunk's window is complete
+    int blo[D], bhi[D];
+    bool any = true;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      blo[m] = s_box[par][m];
+      bhi[m] = s_box[par][D + m];
+      any &= blo[m] <= bhi[m];
+    }
+    if (any) {  // the touched box, one warp per row, lanes along x: add and clear
+      const int ny = bhi[1 % D] - blo[1 % D] + 1;
+      const int nrows = D == 2 ? ny : ny * (bhi[D - 1] - blo[D - 1] + 1);
+      for (int r = threadIdx.x >> 5; r < nrows; r += DEP_THREADS / 32) {
+        const int ly = blo[1 % D] + (D == 2 ? r : r % ny);
+        const int lz = D == 2 ? 0 : blo[D - 1] + r / ny;
+        const size_t gy = (size_t)((anchor[1 % D] - half + ly) & mask);
+        const size_t grow = D == 2 ? gy * N : ((size_t)((anchor[D - 1] - half + lz) & mask) * N + gy) * N;
+        T* wrow = win + ((size_t)lz * side + ly) * side;
+        for (int x = blo[0] + lane; x <= bhi[0]; x += 32) {
+          const T v = wrow[x];
+          if (v != (T)0) {
+            atomicAdd(&rho[grow + ((anchor[0] - half + x) & mask)], W::value(v, inv_scale));
+            wrow[x] = (T)0;
+          }
+        }
+      }
     }
   }
 }
 
 template <typename real, int D>
 int launch_deposit(const PArrays<real, D>& p, size_t np, int n, real inv_cell_vol, real* rho, int win_cap_nodes,
-                   cudaStream_t s) {
+                   real scale, real inv_scale, cudaStream_t s) {
   if (np == 0) return SG_OK;
-  unsigned blocks = (unsigned)((np + DEP_CHUNK - 1) / DEP_CHUNK);
   using T = typename WinAcc<real>::T;
   const long long cap = (long long)win_cap_nodes * 8 / (long long)sizeof(T);  // same bytes for either type
-  int side = 1;  // largest side with side^D <= capacity
+  int side = 2;  // largest even side with side^D <= capacity
   while (true) {
     long long nxt = 1;
-    for (int m = 0; m < D; ++m) nxt *= (side + 1);
+    for (int m = 0; m < D; ++m) nxt *= (side + 2);
     if (nxt > cap) break;
-    ++side;
+    side += 2;
   }
   long long nodes = 1;
   for (int m = 0; m < D; ++m) nodes *= side;
   const size_t smem = ((size_t)nodes * sizeof(T) + 15) / 16 * 16;  // zeroed in 16-byte words
-  static bool attr_set = false;
-  if (!attr_set) {
+  static int per_sm = 0;
+  if (!per_sm) {
     if (smem > 48 * 1024)
       SG_CUDA(cudaFuncSetAttribute(k_deposit<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     SG_CUDA(cudaFuncSetAttribute(k_deposit<real, D>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    attr_set = true;
+    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deposit<real, D>, DEP_THREADS, smem));
+    if (per_sm < 1) per_sm = 1;
   }
-  k_deposit<real, D><<<blocks, DEP_THREADS, smem, s>>>(p, np, n, inv_cell_vol, rho, side);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    SG_CUDA(cudaGetDevice(&dev));
+    SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const size_t nchunks = (np + DEP_CHUNK - 1) / DEP_CHUNK;
+  const unsigned blocks = (unsigned)std::min<size_t>(nchunks, (size_t)sms * per_sm);
+  k_deposit<real, D><<<blocks, DEP_THREADS, smem, s>>>(p, np, n, inv_cell_vol, rho, side, scale, inv_scale);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
@@ -574,8 +531,9 @@ int launch_restrict_pass(const LineJob* jobs_dev, int njobs, int nblocks, int li
   return SG_OK;
 }
 
-#define SG_INST_DEP(real, D)                                                                            \
-  template int launch_deposit<real, D>(const PArrays<real, D>&, size_t, int, real, real*, int, cudaStream_t);
+#define SG_INST_DEP(real, D)                                                                  \
+  template int launch_deposit<real, D>(const PArrays<real, D>&, size_t, int, real, real*, int, real, real, \
+                                       cudaStream_t);
 
 SG_INST_DEP(float, 2)
 SG_INST_DEP(float, 3)

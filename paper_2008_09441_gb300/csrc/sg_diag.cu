@@ -1,6 +1,8 @@
 // FP64 diagnostics reductions, conversions and the device halves of the
 // tauEstimator (Algorithm 1): thresholding and spectral-derivative products
 // of the regular-grid density's Fourier coefficients, and max-norms.
+#include <cstring>
+
 #include "sg_kernels.cuh"
 
 namespace sg {
@@ -128,6 +130,43 @@ int launch_field_to_double(const real* hi, const float* lo, double* dst, size_t 
 }
 template int launch_field_to_double<float>(const float*, const float*, double*, size_t, int, int, cudaStream_t);
 template int launch_field_to_double<double>(const double*, const float*, double*, size_t, int, int, cudaStream_t);
+
+// max |x| through the float bits' order (non-negative values)
+template <typename real>
+__global__ void k_max_abs(const real* __restrict__ x, size_t n, unsigned long long* out) {
+  unsigned long long mx = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double a = fabs((double)x[i]);
+    mx = max(mx, (unsigned long long)__double_as_longlong(a));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
+template <typename real>
+int max_abs_host(const real* x, size_t n, double* out, cudaStream_t s) {
+  unsigned long long* d = nullptr;
+  SG_CUDA(cudaMalloc((void**)&d, sizeof(unsigned long long)));
+  int st = SG_OK;
+  unsigned long long h = 0;
+  if (cudaMemsetAsync(d, 0, sizeof(h), s) != cudaSuccess) st = SG_ERR_CUDA;
+  if (st == SG_OK && n > 0) {
+    k_max_abs<real><<<152 * 4, 256, 0, s>>>(x, n, d);
+    if (cudaGetLastError() != cudaSuccess) st = SG_ERR_CUDA;
+    count_launch();
+  }
+  if (st == SG_OK && cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) st = SG_ERR_CUDA;
+  if (st == SG_OK && cudaStreamSynchronize(s) != cudaSuccess) st = SG_ERR_CUDA;
+  cudaFree(d);
+  if (st != SG_OK) {
+    set_error("max_abs: CUDA error");
+    return st;
+  }
+  std::memcpy(out, &h, sizeof(double));
+  return SG_OK;
+}
+template int max_abs_host<float>(const float*, size_t, double*, cudaStream_t);
+template int max_abs_host<double>(const double*, size_t, double*, cudaStream_t);
 
 // ---------------------------------------------------------------- Algorithm 1 helpers (FP64)
 __global__ void k_real_to_cplx(const double* src, cplx<double>* dst, size_t n, double scale) {

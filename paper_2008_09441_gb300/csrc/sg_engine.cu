@@ -1,6 +1,7 @@
 // Engine<real, D>: one sparse-grid PIC run on one GPU.
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <map>
 #include <set>
 
@@ -667,6 +668,24 @@ class Engine final : public EngineBase {
       SG_TRY(launch_wrap_check<real, D>(P_[cur_], np_, status_, stream_));
     }
     SG_CUDA(cudaStreamSynchronize(stream_));
+    return set_deposit_scale();
+  }
+
+  // Fixed-point scale of the deposit window (FP32 path): with
+  // max_p |q_p| / V < 2^E, contributions are scaled by 2^(19 - E), so each
+  // is below 2^19 and a window of at most 2^11 particles stays below 2^30.
+  // Charges do not change during a run; load() recomputes it.
+  int set_deposit_scale() {
+    dep_scale_ = 1.0;
+    if (sizeof(real) == 4 && np_ > 0) {
+      double qmax = 0;
+      SG_TRY(max_abs_host<real>(P_[cur_].w, np_, &qmax, stream_));
+      qmax *= (double)inv_cell_vol();
+      int E = 0;
+      if (qmax > 0) std::frexp(qmax, &E);  // qmax < 2^E
+      const int k = std::max(-126, std::min(127, 19 - E));
+      dep_scale_ = std::ldexp(1.0, k);
+    }
     return SG_OK;
   }
 
@@ -978,7 +997,8 @@ class Engine final : public EngineBase {
 
   int enqueue_deposit() {
     SG_CUDA(cudaMemsetAsync(rho_reg_, 0, ND_ * sizeof(real), stream_));
-    return launch_deposit<real, D>(P_[cur_], np_, n_, inv_cell_vol(), rho_reg_, cfg_.win_cap, stream_);
+    return launch_deposit<real, D>(P_[cur_], np_, n_, inv_cell_vol(), rho_reg_, cfg_.win_cap, (real)dep_scale_,
+                                   (real)(1.0 / dep_scale_), stream_);
   }
 
   int enqueue_restrict() {
@@ -1215,6 +1235,7 @@ class Engine final : public EngineBase {
   double* ke_partials_ = nullptr;
   double* fe_partials_ = nullptr;
   unsigned* comb_counter_ = nullptr;
+  double dep_scale_ = 1.0;  // FP32 deposit window: fixed-point scale (power of two)
   // filter mode (Algorithm 2): filtered density, regular-grid transform buffers
   bool filter_ = false;
   real* rho_f_ = nullptr;

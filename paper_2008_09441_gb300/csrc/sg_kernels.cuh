@@ -60,9 +60,14 @@ constexpr int DEP_THREADS = 512;
 constexpr int DEP_ITEMS = 4;
 constexpr int DEP_CHUNK = DEP_THREADS * DEP_ITEMS;
 
+// scale / inv_scale: the FP32 fixed-point scale of the window (WinAcc), 1 for FP64.
 template <typename real, int D>
 int launch_deposit(const PArrays<real, D>& p, size_t np, int n, real inv_cell_vol, real* rho,
-                   int win_cap_nodes, cudaStream_t s);
+                   int win_cap_nodes, real scale, real inv_scale, cudaStream_t s);
+
+// max_i |x_i| on the host (synchronises the stream; set-up use only).
+template <typename real>
+int max_abs_host(const real* x, size_t n, double* out, cudaStream_t s);
 
 // ---------------------------------------------------------------- line passes
 // The lines of one array along one axis, processed by one kernel launch
