@@ -894,7 +894,8 @@ class Engine final : public EngineBase {
           J.block_begin = blocks;
           J.comp = comp;
           blocks += (J.lines + C - 1) / C;
-          smem = std::max(smem, (int)(2 * C * len * sizeof(cplx<real>)));
+          const size_t padded = (size_t)C * len + (((size_t)C * len) >> 5);  // see fpad in the solve
+          smem = std::max(smem, (int)(2 * padded * sizeof(cplx<real>)));
           jobs.push_back(J);
         }
       }

@@ -24,6 +24,12 @@ __device__ __forceinline__ cplx<real> cmul(cplx<real> a, cplx<real> w) {
 // the two butterflies of stage s (span 2h) and the two of stage s+1 (span
 // 4h) in registers and stores them, halving the passes over shared memory and
 // the barriers; an odd last stage is a plain radix-2 pass.
+// Shared-memory index of element x of the line buffers: one padding element
+// after every 32, so that the bit-reversed stores (consecutive t land 2^(logn-5)
+// apart) and the large-span butterflies spread over the banks.
+__device__ __forceinline__ int fpad(int x) { return x + (x >> 5); }
+__host__ __device__ constexpr size_t fpad_size(size_t n) { return n + (n >> 5); }
+
 template <typename real>
 __device__ __forceinline__ void fft_smem(cplx<real>* buf, int nl, int logn, bool inverse,
                                          const cplx<real>* __restrict__ tw, int log_nmax) {
@@ -46,15 +52,16 @@ __device__ __forceinline__ void fft_smem(cplx<real>* buf, int nl, int logn, bool
         w2.y = -w2.y;
         w3.y = -w3.y;
       }
-      const cplx<real> a0 = buf[i0], a1 = buf[i0 + h], a2 = buf[i0 + 2 * h], a3 = buf[i0 + 3 * h];
+      const cplx<real> a0 = buf[fpad(i0)], a1 = buf[fpad(i0 + h)], a2 = buf[fpad(i0 + 2 * h)],
+                       a3 = buf[fpad(i0 + 3 * h)];
       const cplx<real> m1 = cmul(a1, w1), m3 = cmul(a3, w1);
       const cplx<real> b0 = {a0.x + m1.x, a0.y + m1.y}, b1 = {a0.x - m1.x, a0.y - m1.y};
       const cplx<real> b2 = {a2.x + m3.x, a2.y + m3.y}, b3 = {a2.x - m3.x, a2.y - m3.y};
       const cplx<real> n2 = cmul(b2, w2), n3 = cmul(b3, w3);
-      buf[i0] = {b0.x + n2.x, b0.y + n2.y};
-      buf[i0 + 2 * h] = {b0.x - n2.x, b0.y - n2.y};
-      buf[i0 + h] = {b1.x + n3.x, b1.y + n3.y};
-      buf[i0 + 3 * h] = {b1.x - n3.x, b1.y - n3.y};
+      buf[fpad(i0)] = {b0.x + n2.x, b0.y + n2.y};
+      buf[fpad(i0 + 2 * h)] = {b0.x - n2.x, b0.y - n2.y};
+      buf[fpad(i0 + h)] = {b1.x + n3.x, b1.y + n3.y};
+      buf[fpad(i0 + 3 * h)] = {b1.x - n3.x, b1.y - n3.y};
     }
     __syncthreads();
   }
@@ -70,11 +77,11 @@ __device__ __forceinline__ void fft_smem(cplx<real>* buf, int nl, int logn, bool
       int i1 = i0 + half;
       cplx<real> w = tw[pos << tshift];
       if (inverse) w.y = -w.y;
-      cplx<real> a = buf[i0], b = buf[i1];
+      cplx<real> a = buf[fpad(i0)], b = buf[fpad(i1)];
       real bx = b.x * w.x - b.y * w.y;
       real by = b.x * w.y + b.y * w.x;
-      buf[i0] = {a.x + bx, a.y + by};
-      buf[i1] = {a.x - bx, a.y - by};
+      buf[fpad(i0)] = {a.x + bx, a.y + by};
+      buf[fpad(i1)] = {a.x - bx, a.y - by};
     }
     __syncthreads();
   }
@@ -114,7 +121,7 @@ __global__ void __launch_bounds__(512) k_fft_pass(int kind, SolveArena<real> a, 
   for (int e = threadIdx.x; e < ntw; e += blockDim.x) tws[e] = a.tw[e];
   pdl_wait();  // the previous pass's output
   cplx<real>* buf0 = tws + ntw;
-  cplx<real>* buf1 = buf0 + C * len;
+  cplx<real>* buf1 = buf0 + fpad_size((size_t)C * len);
   int ls = 0;
   for (int m = 0; m < J.axis; ++m) ls += __ffs(J.dims[m]) - 1;
   const size_t S = a.S;
@@ -134,7 +141,7 @@ __global__ void __launch_bounds__(512) k_fft_pass(int kind, SolveArena<real> a, 
     } else {
       v = a.B[(size_t)J.comp * S + g.offset + off];
     }
-    buf0[(li << logn) + bitrev(t, logn)] = v;
+    buf0[fpad((li << logn) + bitrev(t, logn))] = v;
   }
   __syncthreads();
   const bool inverse = (kind == FFT_INV_MID || kind == FFT_INV_LAST);
@@ -172,7 +179,7 @@ __global__ void __launch_bounds__(512) k_fft_pass(int kind, SolveArena<real> a, 
             nyq_b = (idx[q] == (Nq >> 1));
           }
         }
-        const cplx<real> r = buf0[(li << logn) + t];
+        const cplx<real> r = buf0[fpad((li << logn) + t)];
         // E^_m = -i k_m rho^ / |k|^2 : (x + iy) -> (y, -x) * k_m / |k|^2
         cplx<real> out = {(real)0, (real)0};
         if (k2 != (real)0) {
@@ -188,7 +195,7 @@ __global__ void __launch_bounds__(512) k_fft_pass(int kind, SolveArena<real> a, 
             out.y += r.y * fb;
           }
         }
-        buf1[(li << logn) + bitrev(t, logn)] = out;
+        buf1[fpad((li << logn) + bitrev(t, logn))] = out;
       }
       __syncthreads();
       fft_smem<real>(buf1, nl, logn, true, tws, a.log_nmax);
@@ -196,7 +203,7 @@ __global__ void __launch_bounds__(512) k_fft_pass(int kind, SolveArena<real> a, 
         const int li = contiguous ? (e >> logn) : (e & (nl - 1));
         const int t = contiguous ? (e & (len - 1)) : (e >> logC);
         const long long off = line_addr(line0 + li, t, ls, logn);
-        a.B[(size_t)p * S + g.offset + off] = buf1[(li << logn) + t];
+        a.B[(size_t)p * S + g.offset + off] = buf1[fpad((li << logn) + t)];
       }
       __syncthreads();
     }
@@ -207,7 +214,7 @@ __global__ void __launch_bounds__(512) k_fft_pass(int kind, SolveArena<real> a, 
     const int li = contiguous ? (e >> logn) : (e & (nl - 1));
     const int t = contiguous ? (e & (len - 1)) : (e >> logC);
     const long long off = line_addr(line0 + li, t, ls, logn);
-    const cplx<real> v = buf0[(li << logn) + t];
+    const cplx<real> v = buf0[fpad((li << logn) + t)];
     if (kind == FFT_FWD_FIRST || kind == FFT_FWD_MID) {
       a.A[g.offset + off] = v;
     } else if (kind == FFT_INV_MID) {
@@ -371,14 +378,14 @@ __global__ void __launch_bounds__(256) k_fft_array(cplx<real>* data, int D, int 
   for (int e = threadIdx.x; e < (nl << logn); e += blockDim.x) {
     const int li = contiguous ? (e >> logn) : (e & (nl - 1));
     const int t = contiguous ? (e & (len - 1)) : (e >> logC);
-    buf[(li << logn) + bitrev(t, logn)] = data[line_addr(line0 + li, t, ls, logn)];
+    buf[fpad((li << logn) + bitrev(t, logn))] = data[line_addr(line0 + li, t, ls, logn)];
   }
   __syncthreads();
   fft_smem<real>(buf, nl, logn, inverse != 0, tws, log_nmax);
   for (int e = threadIdx.x; e < (nl << logn); e += blockDim.x) {
     const int li = contiguous ? (e >> logn) : (e & (nl - 1));
     const int t = contiguous ? (e & (len - 1)) : (e >> logC);
-    data[line_addr(line0 + li, t, ls, logn)] = buf[(li << logn) + t];
+    data[line_addr(line0 + li, t, ls, logn)] = buf[fpad((li << logn) + t)];
   }
 }
 
@@ -392,7 +399,7 @@ int launch_fft_array_axis(cplx<real>* data, int D, int logn, int axis, bool inve
   long long lines = 1;
   for (int m = 0; m < D - 1; ++m) lines *= len;
   if (C > lines) C = (int)lines;
-  size_t smem = ((size_t)C * len + ((size_t)1 << (log_nmax - 1))) * sizeof(cplx<real>);
+  size_t smem = (fpad_size((size_t)C * len) + ((size_t)1 << (log_nmax - 1))) * sizeof(cplx<real>);
   static bool attr_set = false;
   if (!attr_set) {
     SG_CUDA(cudaFuncSetAttribute(k_fft_array<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
