@@ -322,11 +322,15 @@ def main():
     clocks.start()
     l0 = run.kernel_launches()
     wall0 = time.perf_counter()
+    # An NVTX range marks the timed steps, so that a profiler's launch list can
+    # be restricted to them (ncu --nvtx --nvtx-include "sg_timed_steps/").
+    torch.cuda.nvtx.range_push("sg_timed_steps")
     for k in range(args.steps):
         flush.zero_()
         starts[k].record(stream)
         run.step(1)
         ends[k].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     barrier(pg)
