@@ -17,8 +17,14 @@ State conventions (readings of the paper where it is silent):
 * Domain: periodic box [0, L_1) x ... x [0, L_d) (Section 5 opening).
   Positions are carried as fractions of the box, ``u_m = x_m / L_m`` in
   [0, 1); velocities are physical.
-* Grids are node-centred: node ``k`` of a level-``l`` axis sits at
-  ``x_k = k L / 2^l`` (the case in which Proposition 1 is exact).
+* Grids are node-centred by default: node ``k`` of a level-``l`` axis sits
+  at ``x_k = k L / 2^l`` (the case in which Proposition 1 is exact).  With
+  ``centring="cell"`` node ``k`` sits at the cell centre
+  ``x_k = (k + 1/2) L / 2^l`` (the paper's own choice, Section 4.3); then
+  the component densities are the two-step ones, R_i applied to the
+  regular-grid deposit, whose effective shape is Appendix A's W_c, and the
+  field reaches the particles through the same two-step shape (P_i onto
+  the regular grid, then the regular-grid CIC gather).
   Grid arrays are indexed ``[i_1, i_2(, i_3)]``, i.e. array axis m is
   coordinate axis m.
 * Particle charge ``q_p`` is per particle (weighted particles); the mass is
@@ -125,14 +131,25 @@ def count_checksum(counts):
 # --------------------------------------------------------------------------
 
 
-def _cic_corners(u, l):
+def _node_offset(centring):
+    """Position of node 0 in cells: 0 for node-centred grids, 1/2 for
+    cell-centred ones."""
+    if centring not in ("node", "cell"):
+        raise ValueError("centring must be 'node' or 'cell'")
+    return 0.5 if centring == "cell" else 0.0
+
+
+def _cic_corners(u, l, centring="node"):
     """For each of the 2^d corners: (tuple of node-index arrays, weight array).
 
     W_m(zeta) = max(0, 1 - |zeta| / h_m) evaluated at the two nodes that
-    bracket the particle along each axis (Section 4.1, eq. restriction)."""
+    bracket the particle along each axis (Section 4.1, eq. restriction).
+    Node k of a level-l axis sits at (k + o) h_l, o = 0 (node-centred) or
+    1/2 (cell-centred), periodically."""
     u = np.asarray(u, dtype=np.float64)
     d = u.shape[1]
-    s = [u[:, m] * float(2 ** l[m]) for m in range(d)]
+    o = _node_offset(centring)
+    s = [u[:, m] * float(2 ** l[m]) - o for m in range(d)]
     j = [np.floor(s[m]).astype(np.int64) for m in range(d)]
     f = [s[m] - j[m] for m in range(d)]
     out = []
@@ -149,67 +166,75 @@ def cell_volume(l, L):
     return float(np.prod([L[m] / 2 ** l[m] for m in range(len(l))]))
 
 
-def deposit_cic(u, q, l, L):
-    """Direct CIC charge deposition onto a node-centred grid of levels ``l``.
+def deposit_cic(u, q, l, L, centring="node"):
+    """Direct CIC charge deposition onto a grid of levels ``l``.
 
     rho(x_k) = (1 / V) sum_p q_p prod_m W_m(x_{k,m} - x_{p,m}), V the cell
     volume: eq. rho_hf (Appendix A) generalised to d dimensions and to
     per-particle charges.  This is the sparse-PIC direct deposit onto a
-    component grid (Section 4.1)."""
+    component grid (Section 4.1), and, at levels (n, ..., n), the regular-grid
+    deposit of the two-step approach."""
     shape = tuple(2 ** lm for lm in l)
     rho = np.zeros(shape, dtype=np.float64)
     V = cell_volume(l, L)
     q = np.asarray(q, dtype=np.float64)
-    for idx, w in _cic_corners(u, l):
+    for idx, w in _cic_corners(u, l, centring):
         np.add.at(rho, idx, q * w / V)
     return rho
 
 
-def restriction_matrix_1d(n, l):
+def _periodic_distance(a, b, N):
+    """|a - b| on a circle of circumference N (a, b in fine-cell units)."""
+    dist = (a - b) % N
+    return min(dist, N - dist)
+
+
+def restriction_matrix_1d(n, l, centring="node"):
     """R along one axis from the level-n grid to level l (eq. restriction):
-    entry [k, j] = (h / h_l) W(x_k - x~_j) with periodic distance."""
+    entry [k, j] = (h / h_l) W(x_k - x~_j) with periodic distance; node k of
+    level l at (k + o) h_l, node j of level n at (j + o) h, o = 0 or 1/2."""
     N, M = 2 ** n, 2 ** l
     r = N // M  # regular cells per coarse cell
+    o = _node_offset(centring)
     R = np.zeros((M, N), dtype=np.float64)
     for k in range(M):
         for j in range(N):
-            dist = (j - k * r) % N
-            dist = min(dist, N - dist)  # periodic distance in fine cells
+            dist = _periodic_distance(j + o, (k + o) * r, N)  # in fine cells
             R[k, j] = max(0.0, 1.0 - dist / r) / r
     return R
 
 
-def restrict(rho_reg, n, l):
+def restrict(rho_reg, n, l, centring="node"):
     """R_i rho~: transfer from the regular grid to component grid l using
     R_i = (h^d / V_i) prod_m W_m (eq. restriction).  The operator is a tensor
     product of 1D operators; applied axis by axis with a dense matrix."""
     out = np.asarray(rho_reg, dtype=np.float64)
     for m, lm in enumerate(l):
-        R = restriction_matrix_1d(n, lm)
+        R = restriction_matrix_1d(n, lm, centring)
         out = np.moveaxis(np.tensordot(R, np.moveaxis(out, m, 0), axes=(1, 0)), 0, m)
     return out
 
 
-def prolongation_matrix_1d(n, l):
+def prolongation_matrix_1d(n, l, centring="node"):
     """P along one axis from level l to the level-n nodes (eq. restriction):
     entry [j, k] = W(x~_j - x_k) with the coarse spacing h_l."""
     N, M = 2 ** n, 2 ** l
     r = N // M
+    o = _node_offset(centring)
     P = np.zeros((N, M), dtype=np.float64)
     for j in range(N):
         for k in range(M):
-            dist = (j - k * r) % N
-            dist = min(dist, N - dist)
+            dist = _periodic_distance(j + o, (k + o) * r, N)
             P[j, k] = max(0.0, 1.0 - dist / r)
     return P
 
 
-def prolong(field, n, l):
+def prolong(field, n, l, centring="node"):
     """P_i: linear interpolation of a level-l nodal field onto the level-n
     nodes (eq. restriction), axis by axis."""
     out = np.asarray(field, dtype=np.float64)
     for m, lm in enumerate(l):
-        P = prolongation_matrix_1d(n, lm)
+        P = prolongation_matrix_1d(n, lm, centring)
         out = np.moveaxis(np.tensordot(P, np.moveaxis(out, m, 0), axes=(1, 0)), 0, m)
     return out
 
@@ -271,18 +296,20 @@ def potential_spectral(rho, L):
 # --------------------------------------------------------------------------
 
 
-def gather_cic(field, u, l):
+def gather_cic(field, u, l, centring="node"):
     """CIC interpolation of a level-l nodal field to the particles."""
     out = np.zeros(np.asarray(u).shape[0], dtype=np.float64)
-    for idx, w in _cic_corners(u, l):
+    for idx, w in _cic_corners(u, l, centring):
         out += w * field[idx]
     return out
 
 
-def regular_node_positions(n, d):
-    """Fractional positions j / 2^n of all level-n nodes, in array order."""
+def regular_node_positions(n, d, centring="node"):
+    """Fractional positions (j + o) / 2^n of all level-n nodes, in array
+    order (o = 0 node-centred, 1/2 cell-centred)."""
     N = 2 ** n
-    axes = np.meshgrid(*[np.arange(N) / N for _ in range(d)], indexing="ij")
+    o = _node_offset(centring)
+    axes = np.meshgrid(*[(np.arange(N) + o) / N for _ in range(d)], indexing="ij")
     return np.stack([a.ravel() for a in axes], axis=1)
 
 
@@ -345,60 +372,72 @@ def drift(u, v, dt, L):
 # --------------------------------------------------------------------------
 
 
-def component_fields(u, q, n, tau, L):
-    """Deposit directly on every component grid and solve each
-    (sparse PIC of Section 4.1 with the grid set of Section 4.2).
-    Returns a list of (l, c, rho_l, [E_l,m])."""
+def component_fields(u, q, n, tau, L, centring="node"):
+    """Component densities and fields (sparse PIC of Section 4.1 with the
+    grid set of Section 4.2).  Node-centred: deposit directly on every
+    component grid.  Cell-centred: the two-step densities R_i rho~ of the
+    regular-grid deposit rho~ (Appendix A: their shape W_c is a shape
+    function of its own, no longer the direct deposit).  Each density is
+    solved on its grid.  Returns a list of (l, c, rho_l, [E_l,m])."""
     d = np.asarray(u).shape[1]
     out = []
+    rho_reg = deposit_cic(u, q, (n,) * d, L, "cell") if centring == "cell" else None
     for l, c in combination_grids(d, n, tau):
-        rho = deposit_cic(u, q, l, L)
+        if centring == "cell":
+            rho = restrict(rho_reg, n, l, "cell")
+        else:
+            rho = deposit_cic(u, q, l, L)
         E = solve_poisson_spectral(rho, L)
         out.append((l, c, rho, E))
     return out
 
 
-def field_at_particles(comps, u, L, eext_lin):
-    """E(x_p) = sum_i c_i I_i[E_i](x_p) + E_ext(x_p): the signed combination of
-    the component fields gathered with the CIC shape from each component grid
-    (no regular grid involved)."""
+def field_at_particles(comps, u, L, eext_lin, centring="node", n=None):
+    """E(x_p) = sum_i c_i I_i[E_i](x_p) + E_ext(x_p).  Node-centred: each
+    component field gathered with the CIC shape straight from its grid (no
+    regular grid involved).  Cell-centred: the same two-step shape as the
+    deposit, sum_k W_c(x_k - x_p) E_i(x_k) = regular-grid CIC gather of
+    P_i E_i (Appendix A's W_c, used in both directions)."""
     d = np.asarray(u).shape[1]
     E = [np.zeros(np.asarray(u).shape[0]) for _ in range(d)]
     for l, c, _, El in comps:
         for m in range(d):
-            E[m] += c * gather_cic(El[m], u, l)
+            if centring == "cell":
+                E[m] += c * gather_cic(prolong(El[m], n, l, "cell"), u, (n,) * d, "cell")
+            else:
+                E[m] += c * gather_cic(El[m], u, l)
     Ee = external_field(u, L, eext_lin)
     return [E[m] + Ee[m] for m in range(d)]
 
 
-def combined_field_regular(comps, n, d):
+def combined_field_regular(comps, n, d, centring="node"):
     """E_comb = sum_i c_i P_i E_i on the regular nodes (eq. sparse_filter with
     the same c_i and P_i, applied to the component fields)."""
     out = [np.zeros((2 ** n,) * d) for _ in range(d)]
     for l, c, _, El in comps:
         for m in range(d):
-            out[m] += c * prolong(El[m], n, l)
+            out[m] += c * prolong(El[m], n, l, centring)
     return out
 
 
-def density_filter(rho_reg, n, tau, L):
+def density_filter(rho_reg, n, tau, L, centring="node"):
     """Sparse-grid filter of a regular-grid density (eq. sparse_filter,
     Algorithm 2): rho_f = sum_i c_i P_i R_i rho~, with R_i and P_i of eq.
     restriction and the grid set of Section 4.2."""
     d = np.asarray(rho_reg).ndim
     out = np.zeros_like(np.asarray(rho_reg, dtype=np.float64))
     for l, c in combination_grids(d, n, tau):
-        out += c * prolong(restrict(rho_reg, n, l), n, l)
+        out += c * prolong(restrict(rho_reg, n, l, centring), n, l, centring)
     return out
 
 
-def filtered_field_regular(u, q, n, tau, L):
+def filtered_field_regular(u, q, n, tau, L, centring="node"):
     """Field of the paper's filter mode on the regular nodes: deposit on the
     regular grid, filter the density (density_filter), one spectral solve
     on the regular grid (Algorithm 2's field step)."""
     d = np.asarray(u).shape[1]
-    rho = deposit_cic(u, q, (n,) * d, L)
-    rho_f = density_filter(rho, n, tau, L)
+    rho = deposit_cic(u, q, (n,) * d, L, centring)
+    rho_f = density_filter(rho, n, tau, L, centring)
     return rho, rho_f, solve_poisson_spectral(rho_f, L)
 
 
@@ -413,15 +452,19 @@ class OracleRun:
     """
 
     def __init__(self, L, n, u, v, q, dt, qm=-1.0, tau=1, B=(0.0, 0.0, 0.0),
-                 eext_lin=(0.0, 0.0, 0.0), mode="combine", alpha=0.01, pc_ref=5.0, tau_constants="paper"):
+                 eext_lin=(0.0, 0.0, 0.0), mode="combine", alpha=0.01, pc_ref=5.0, tau_constants="paper",
+                 centring="node"):
         # mode "combine": sparse PIC, fields solved per component grid and
         # combined (Section 4.1); "filter": the density is deposited on the
         # regular grid, filtered (eq. sparse_filter) and solved once there
         # (Algorithm 2).  tau = "adaptive": Algorithm 1 picks tau from the
         # regular-grid density before every field evaluation (alpha, pc_ref,
-        # tau_constants are its parameters).
+        # tau_constants are its parameters).  centring "node" | "cell": where
+        # the grid nodes sit (module docstring).
         assert mode in ("combine", "filter")
+        _node_offset(centring)
         self.mode = mode
+        self.centring = centring
         self.adaptive = tau == "adaptive"
         self.alpha, self.pc_ref, self.tau_constants = float(alpha), float(pc_ref), tau_constants
         self.tau_history = []
@@ -445,30 +488,30 @@ class OracleRun:
 
     def _fields(self):
         if self.adaptive:
-            rho = deposit_cic(self.u, self.q, (self.n,) * self.d, self.L)
+            rho = deposit_cic(self.u, self.q, (self.n,) * self.d, self.L, self.centring)
             self.tau = tau_estimator(rho, len(self.q), self.L[0], self.alpha, self.pc_ref,
                                      float(np.sum(self.q)), self.tau_constants)[0]
             self.tau_history.append(self.tau)
         if self.mode == "combine":
-            self.comps = component_fields(self.u, self.q, self.n, self.tau, self.L)
+            self.comps = component_fields(self.u, self.q, self.n, self.tau, self.L, self.centring)
         else:  # component densities only (diagnostics), field on the regular grid
             self.comps = []
             rho, self.rho_filtered, self.E_regular = filtered_field_regular(self.u, self.q, self.n, self.tau,
-                                                                            self.L)
+                                                                            self.L, self.centring)
             for l, c in combination_grids(self.d, self.n, self.tau):
-                self.comps.append((l, c, restrict(rho, self.n, l), None))
+                self.comps.append((l, c, restrict(rho, self.n, l, self.centring), None))
 
     def field_at(self, u):
         """The field the push sees at positions u (plus E_ext)."""
         if self.mode == "combine":
-            return field_at_particles(self.comps, u, self.L, self.eext)
+            return field_at_particles(self.comps, u, self.L, self.eext, self.centring, self.n)
         Ee = external_field(u, self.L, self.eext)
-        return [gather_cic(self.E_regular[m], u, (self.n,) * self.d) + Ee[m] for m in range(self.d)]
+        return [gather_cic(self.E_regular[m], u, (self.n,) * self.d, self.centring) + Ee[m] for m in range(self.d)]
 
     def regular_field(self):
         """The field on the regular nodes (combined, or the filter mode's)."""
         if self.mode == "combine":
-            return combined_field_regular(self.comps, self.n, self.d)
+            return combined_field_regular(self.comps, self.n, self.d, self.centring)
         return self.E_regular
 
     def field_energy(self):
