@@ -270,6 +270,10 @@ def main():
     ap.add_argument("--mode", default="combine", choices=["combine", "filter"],
                     help="combine: solves on every component grid, fields combined (the default line); "
                          "filter: the paper's filter mode (eq. sparse_filter, Algorithm 2)")
+    ap.add_argument("--solve-variant", default="auto", choices=["auto", "passes", "one-block"],
+                    help="component-grid solve: timed choice at init (default), or fixed; a profiler's "
+                         "serialised launches distort the timed choice, so profile with the variant the "
+                         "plain run chose")
     ap.add_argument("--ref-particles", type=int, default=1 << 16)
     ap.add_argument("--ref-budget-s", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -305,6 +309,8 @@ def main():
     sort_every = args.sort_every if args.sort_every > 0 else 4  # the library default
     run = Run(wl.L, n, u, v, q, wl.dt, tau=wl.tau, precision="fp32", sort_every=sort_every,
               stream=stream.cuda_stream, mode=args.mode)
+    if args.solve_variant != "auto":
+        run.set_solve_variant(args.solve_variant)
     del u, v, q
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     np_ = wl.n_particles
@@ -384,6 +390,8 @@ def main():
         t0 = time.perf_counter()
         r2 = Run(wl.L, n, hu, hv, hq, wl.dt, tau=wl.tau, precision="fp32", sort_every=sort_every,
                  stream=stream.cuda_stream, mode=args.mode)
+        if args.solve_variant != "auto":
+            r2.set_solve_variant(args.solve_variant)
         diag_bytes = 0
         for _ in range(args.steps):  # a user monitoring the run: step, then read the FP64 diagnostics
             r2.step(1)

@@ -62,6 +62,8 @@ extern "C" {
 #define SG_TAU_CONST_EMPIRICAL 1      /* eq. empirical_constants */
 #define SG_MODE_COMBINE 0
 #define SG_MODE_FILTER 1
+#define SG_NODE_CENTRED 0 /* node k of a level-l axis at x_k = k L / 2^l */
+#define SG_CELL_CENTRED 1 /* node k at the cell centre x_k = (k + 1/2) L / 2^l */
 
 typedef struct sg_pic sg_pic; /* opaque run handle; owns all its device memory */
 
@@ -106,6 +108,13 @@ typedef struct {
                          is filtered, rho_f = sum_i c_i P_i R_i rho~, and solved
                          once on the regular grid.  Either way the push gathers
                          from a field on the regular nodes. */
+  int centring;       /* SG_NODE_CENTRED (0): nodes at x_k = k h, where Proposition 1
+                         makes the two-step deposit the direct one; SG_CELL_CENTRED
+                         (1): nodes at cell centres (the paper's choice, Section 4.3),
+                         component densities R_i rho~ with the two-step shape W_c of
+                         Appendix A, and the gather through the same shape (P_i to
+                         the regular grid, then CIC).  Any other value:
+                         SG_ERR_INVALID. */
 } sg_params;
 
 typedef struct {
@@ -214,6 +223,20 @@ int sg_pic_kernel_launches(sg_pic* h, unsigned long long* count);
  * passes, 1 one block per grid) and the two timings (ms) it compared. */
 int sg_pic_set_profiling(sg_pic* h, int on);
 int sg_pic_stage_times(sg_pic* h, double* ms, int cap);
+
+/* Solve variant of the combination mode: SG_SOLVE_AUTO (-1, the default:
+ * both variants timed at init and at every grid-set change, the faster
+ * kept), SG_SOLVE_PASSES (0: batched FFT passes per axis over all
+ * component grids) or SG_SOLVE_ONE_BLOCK (1: one block solves one whole
+ * component grid in shared memory).  Both compute the same fields.  A fixed
+ * variant stays through later grid-set changes.  Returns SG_ERR_INVALID for
+ * another value and SG_ERR_UNSUPPORTED for SG_SOLVE_ONE_BLOCK when a
+ * component grid exceeds the one-block size; synchronises the run's
+ * stream.  No effect on the filter mode's regular-grid solve. */
+#define SG_SOLVE_AUTO (-1)
+#define SG_SOLVE_PASSES 0
+#define SG_SOLVE_ONE_BLOCK 1
+int sg_pic_set_solve_variant(sg_pic* h, int variant);
 
 void sg_pic_destroy(sg_pic* h);
 

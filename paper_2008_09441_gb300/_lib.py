@@ -30,6 +30,8 @@ SG_TAU_CONST_EMPIRICAL = 1
 SG_REQ_QUEUED, SG_REQ_RUNNING, SG_REQ_DONE, SG_REQ_FAILED = 0, 1, 2, 3
 SG_SERVE_BATCHED, SG_SERVE_PLAIN = 0, 1
 SG_MODE_COMBINE, SG_MODE_FILTER = 0, 1
+SG_NODE_CENTRED, SG_CELL_CENTRED = 0, 1
+SG_SOLVE_AUTO, SG_SOLVE_PASSES, SG_SOLVE_ONE_BLOCK = -1, 0, 1
 
 
 class sg_domain(C.Structure):
@@ -50,7 +52,7 @@ class sg_params(C.Structure):
     _fields_ = [("precision", C.c_int), ("tau", C.c_int), ("dt", C.c_double), ("qm", C.c_double),
                 ("B", C.c_double * 3), ("Eext_lin", C.c_double * 3), ("alpha", C.c_double),
                 ("pc_ref", C.c_double), ("tau_constants", C.c_int), ("sort_every", C.c_int),
-                ("stream", C.c_void_p), ("mode", C.c_int)]
+                ("stream", C.c_void_p), ("mode", C.c_int), ("centring", C.c_int)]
 
 
 class sg_diag(C.Structure):
@@ -90,6 +92,7 @@ SIGNATURES = {
     "sg_pic_device_particles": (C.c_int, [_P, C.POINTER(sg_particles_out)]),
     "sg_pic_kernel_launches": (C.c_int, [_P, C.POINTER(C.c_ulonglong)]),
     "sg_pic_set_profiling": (C.c_int, [_P, C.c_int]),
+    "sg_pic_set_solve_variant": (C.c_int, [_P, C.c_int]),
     "sg_pic_stage_times": (C.c_int, [_P, _P, C.c_int]),
     "sg_pic_destroy": (None, [_P]),
     "sg_strerror": (C.c_char_p, [C.c_int]),

@@ -108,6 +108,9 @@ int sg_pic_init(const sg_domain* domain, int level_n, int dim, int shape_order, 
   if (params->mode != SG_MODE_COMBINE && params->mode != SG_MODE_FILTER)
     return invalid("sg_pic_init: mode must be SG_MODE_COMBINE or SG_MODE_FILTER");
   cfg.mode = params->mode;
+  if (params->centring != SG_NODE_CENTRED && params->centring != SG_CELL_CENTRED)
+    return invalid("sg_pic_init: centring must be SG_NODE_CENTRED or SG_CELL_CENTRED");
+  cfg.cell = params->centring == SG_CELL_CENTRED;
 
   sg_pic* h = new (std::nothrow) sg_pic;
   if (!h) return SG_ERR_OOM;
@@ -222,6 +225,11 @@ int sg_pic_kernel_launches(sg_pic* h, unsigned long long* count) {
 int sg_pic_set_profiling(sg_pic* h, int on) {
   SG_H(h);
   return h->e->set_profiling(on);
+}
+
+int sg_pic_set_solve_variant(sg_pic* h, int variant) {
+  SG_H(h);
+  return h->e->set_solve_variant(variant);
 }
 
 int sg_pic_stage_times(sg_pic* h, double* ms, int cap) {

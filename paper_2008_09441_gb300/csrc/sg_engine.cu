@@ -552,6 +552,24 @@ class Engine final : public EngineBase {
     return SG_OK;
   }
 
+  // Fix the solve variant (0 per-axis passes, 1 one block per grid) or
+  // return to autotuning (-1); kept across grid-set changes.
+  int set_solve_variant(int variant) override {
+    if (variant < -1 || variant > 1) {
+      set_error("sg_pic_set_solve_variant: variant must be -1, 0 or 1");
+      return SG_ERR_INVALID;
+    }
+    if (variant == 1 && !small_solve_fits()) {
+      set_error("sg_pic_set_solve_variant: a component grid is too large for the one-block solve");
+      return SG_ERR_UNSUPPORTED;
+    }
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    invalidate_graphs();
+    force_mode_ = variant;
+    if (filter_) return SG_OK;  // the filter mode runs no component solves
+    return tune_solve();
+  }
+
   int stage_times(double* ms, int cap) override {
     for (int i = 0; i < 6 && i < cap; ++i) ms[i] = stage_ms_[i];
     // autotuner record: chosen solve variant and the timings it compared
@@ -1026,8 +1044,7 @@ class Engine final : public EngineBase {
       for (int g = 0; g < ngrids_; ++g) SG_TRY(launch_solve_small<real>(a, 1, gdesc_[g].size, stream_, g));
       return SG_OK;
     }
-    if (small_ok && (solve_mode_ == 1 || (solve_mode_ == -1 && force_mode_ < 0)))
-      return launch_solve_small<real>(a, ngrids_, maxsize, stream_);
+    if (small_ok && solve_mode_ == 1) return launch_solve_small<real>(a, ngrids_, maxsize, stream_);
     for (auto& P : fpasses_) SG_TRY(launch_fft_pass<real>(P.kind, a, P.dev, P.njobs, P.nblocks, P.smem, stream_));
     return SG_OK;
   }
@@ -1036,11 +1053,19 @@ class Engine final : public EngineBase {
   // per-axis passes on this grid set (both read the component densities and
   // write the component fields, so repeating them is harmless) and keep the
   // faster.  Runs at init and whenever the grid set changes.
-  int tune_solve() {
+  bool small_solve_fits() const {
     int maxsize = 0;
     for (auto& g : gdesc_) maxsize = std::max(maxsize, g.size);
-    if (maxsize > small_solve_max<real>()) {
+    return maxsize <= small_solve_max<real>();
+  }
+
+  int tune_solve() {
+    if (!small_solve_fits()) {
       solve_mode_ = 0;
+      return SG_OK;
+    }
+    if (force_mode_ >= 0) {  // fixed by the caller: no timing
+      solve_mode_ = force_mode_;
       return SG_OK;
     }
     cudaEvent_t e0, e1;
@@ -1258,7 +1283,7 @@ class Engine final : public EngineBase {
   LevelLists levels_{};
   bool per_grid_ = false;
   int solve_mode_ = -1;  // -1 untuned, 0 per-axis passes, 1 one block per grid
-  int force_mode_ = -1;
+  int force_mode_ = -1;  // solve variant fixed by the caller, -1 autotuned
   float solve_ms_[2] = {0, 0};
   GridDesc* grids_dev_ = nullptr;
   double* charges_dev_ = nullptr;

@@ -31,6 +31,7 @@ struct EngineConfig {
   int tau_constants = SG_TAU_CONST_PAPER;
   int sort_every = 0;
   int mode = SG_MODE_COMBINE;
+  bool cell = false;  // cell-centred grids (nodes at (k + 1/2) h)
   int win_cap = 4096;  // deposit window capacity in regular nodes (64-bit accumulators)
 };
 
@@ -53,6 +54,7 @@ class EngineBase {
   virtual int load(const void* buf, size_t size) = 0;
   virtual int device_particles(sg_particles_out* out) = 0;
   virtual int set_profiling(int on) = 0;
+  virtual int set_solve_variant(int variant) = 0;
   virtual int stage_times(double* ms, int cap) = 0;
   virtual unsigned long long kernel_launches() const = 0;
   virtual size_t device_bytes() const = 0;

@@ -146,6 +146,7 @@ static int admit(sg_server* s, bool* changed, int* failed) {
     cfg.tau_constants = q.params.tau_constants;
     cfg.sort_every = q.params.sort_every;
     cfg.mode = q.params.mode;
+    cfg.cell = q.params.centring == SG_CELL_CENTRED;
     sg_particles hp;
     std::memset(&hp, 0, sizeof(hp));
     hp.n = q.particles.n;
@@ -283,6 +284,8 @@ int sg_serve_submit(sg_server* s, const sg_request* req, unsigned long long* tic
   if (p.on_device) return serr("sg_serve_submit: particle arrays must be host memory", SG_ERR_UNSUPPORTED);
   if (req->params.mode != SG_MODE_COMBINE && req->params.mode != SG_MODE_FILTER)
     return serr("sg_serve_submit: mode must be SG_MODE_COMBINE or SG_MODE_FILTER");
+  if (req->params.centring != SG_NODE_CENTRED && req->params.centring != SG_CELL_CENTRED)
+    return serr("sg_serve_submit: centring must be SG_NODE_CENTRED or SG_CELL_CENTRED");
   if (req->dim != 2 && req->dim != 3) return serr("sg_serve_submit: dim must be 2 or 3");
   if (req->nsteps < 0) return serr("sg_serve_submit: nsteps < 0");
   if (req->params.tau == SG_TAU_ADAPTIVE) return serr("sg_serve_submit: adaptive tau is not served", SG_ERR_UNSUPPORTED);

@@ -49,11 +49,12 @@ def _on_device(x):
 
 
 _MODES = {"combine": L.SG_MODE_COMBINE, "filter": L.SG_MODE_FILTER}
+_CENTRINGS = {"node": L.SG_NODE_CENTRED, "cell": L.SG_CELL_CENTRED}
 
 
 def make_params(precision=L.SG_FP32, tau=1, dt=0.05, qm=-1.0, B=(0.0, 0.0, 0.0), eext_lin=(0.0, 0.0, 0.0),
                 alpha=0.01, pc_ref=5.0, tau_constants=L.SG_TAU_CONST_PAPER, sort_every=0, stream=None,
-                mode=L.SG_MODE_COMBINE):
+                mode=L.SG_MODE_COMBINE, centring=L.SG_NODE_CENTRED):
     p = L.sg_params()
     p.precision = precision
     p.tau = tau
@@ -68,6 +69,7 @@ def make_params(precision=L.SG_FP32, tau=1, dt=0.05, qm=-1.0, B=(0.0, 0.0, 0.0),
     p.sort_every = sort_every
     p.stream = stream
     p.mode = _MODES.get(mode, mode)
+    p.centring = _CENTRINGS.get(centring, centring)
     return p
 
 
@@ -145,7 +147,7 @@ class Run:
 
     def __init__(self, L_box, n, u, v, w, dt, *, tau=1, qm=-1.0, precision="fp32", B=(0.0, 0.0, 0.0),
                  eext_lin=(0.0, 0.0, 0.0), alpha=0.01, pc_ref=5.0, tau_constants="paper", sort_every=0,
-                 stream=None, mode="combine"):
+                 stream=None, mode="combine", centring="node"):
         self.d = len(L_box)
         self.n = n
         self.precision = L.SG_FP32 if precision in ("fp32", L.SG_FP32) else L.SG_FP64
@@ -169,7 +171,7 @@ class Run:
         parts.w = _ptr(wcol).value
         tc = L.SG_TAU_CONST_PAPER if tau_constants == "paper" else L.SG_TAU_CONST_EMPIRICAL
         self.params = make_params(self.precision, tau, dt, qm, B, eext_lin, alpha, pc_ref, tc, sort_every,
-                                  stream, mode)
+                                  stream, mode, centring)
         self._keep = (ucols, vcols, wcol)
         self.h = sg_pic_init(dom, n, d, 1, parts, self.params)
         self._keep = None
@@ -296,6 +298,11 @@ class Run:
     def set_profiling(self, on=True):
         check(lib().sg_pic_set_profiling(self.h, 1 if on else 0), "sg_pic_set_profiling")
 
+    def set_solve_variant(self, variant="auto"):
+        """'auto' (timed choice), 'passes' or 'one-block' (sg_pic_set_solve_variant)."""
+        v = {"auto": L.SG_SOLVE_AUTO, "passes": L.SG_SOLVE_PASSES, "one-block": L.SG_SOLVE_ONE_BLOCK}.get(variant, variant)
+        check(lib().sg_pic_set_solve_variant(self.h, v), "sg_pic_set_solve_variant")
+
     def stage_times(self):
         ms = np.zeros(6)
         check(lib().sg_pic_stage_times(self.h, ms.ctypes.data, 6), "sg_pic_stage_times")
@@ -333,7 +340,7 @@ class Server:
         self.meta = {}
 
     def submit(self, L_box, n, u, v, w, dt, nsteps, *, tau=1, qm=-1.0, precision="fp32", B=(0.0, 0.0, 0.0),
-               eext_lin=(0.0, 0.0, 0.0), sort_every=0, mode="combine"):
+               eext_lin=(0.0, 0.0, 0.0), sort_every=0, mode="combine", centring="node"):
         d = len(L_box)
         prec = L.SG_FP32 if precision in ("fp32", L.SG_FP32) else L.SG_FP64
         dt_np = _DT[prec]
@@ -353,7 +360,7 @@ class Server:
             req.particles.v[m] = _ptr(vcols[m]).value
         req.particles.w = _ptr(wcol).value
         req.params = make_params(prec, tau, dt, qm, B, eext_lin, 0.01, 5.0, L.SG_TAU_CONST_PAPER, sort_every, None,
-                                 mode)
+                                 mode, centring)
         req.nsteps = int(nsteps)
         t = C.c_ulonglong()
         check(lib().sg_serve_submit(self.h, C.byref(req), C.byref(t)), "sg_serve_submit")

@@ -433,3 +433,29 @@ def test_stage_profiling_mode_same_results(torch_cuda):
         assert nrmse(x, y) < 1e-13
     r1.close()
     r2.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_fixed_solve_variants_agree(torch_cuda, prec):
+    """Both solve variants, fixed through sg_pic_set_solve_variant, give the
+    oracle's fields and the same trajectory; bad values are rejected."""
+    from paper_2008_09441_gb300 import SGError
+    wl = workloads.landau2d(n_particles=12000, n=7, tau=1, seed=171)
+    runs = []
+    for variant in ("passes", "one-block"):
+        run, (u64, v64, q64) = make_run(wl, prec, torch_cuda)
+        run.set_solve_variant(variant)
+        assert run.tuning()["solve_variant"] == ("per-axis-passes" if variant == "passes" else "one-block-per-grid")
+        run.step(3)
+        runs.append(run)
+    ref = O.OracleRun(wl.L, wl.n, u64, v64, q64, wl.dt, qm=wl.qm, tau=1)
+    ref.step(3)
+    for run in runs:
+        ug, vg, _ = run.particles()
+        assert nrmse_periodic(ug, ref.u) < TOL[prec] and nrmse(vg, ref.velocities()) < TOL[prec]
+    with pytest.raises(SGError):
+        runs[0].set_solve_variant(7)
+    runs[0].set_solve_variant("auto")
+    runs[0].step(1)
+    for run in runs:
+        run.close()
