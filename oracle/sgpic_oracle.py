@@ -184,24 +184,29 @@ def deposit_cic(u, q, l, L, centring="node"):
 
 
 def _periodic_distance(a, b, N):
-    """|a - b| on a circle of circumference N (a, b in fine-cell units)."""
-    dist = (a - b) % N
-    return min(dist, N - dist)
+    """|a - b| on a circle of circumference N (a, b in fine-cell units,
+    scalars or broadcasting arrays)."""
+    dist = np.mod(np.subtract(a, b), N)
+    return np.minimum(dist, N - dist)
+
+
+def _coarse_fine_distance(n, l, centring):
+    """[k, j]: periodic distance, in level-n cells, between node k of level l
+    at (k + o) h_l and node j of level n at (j + o) h (o = 0 or 1/2)."""
+    N, M = 2 ** n, 2 ** l
+    r = N // M
+    o = _node_offset(centring)
+    k = np.arange(M, dtype=np.float64)[:, None]
+    j = np.arange(N, dtype=np.float64)[None, :]
+    return _periodic_distance(j + o, (k + o) * r, N)
 
 
 def restriction_matrix_1d(n, l, centring="node"):
     """R along one axis from the level-n grid to level l (eq. restriction):
     entry [k, j] = (h / h_l) W(x_k - x~_j) with periodic distance; node k of
     level l at (k + o) h_l, node j of level n at (j + o) h, o = 0 or 1/2."""
-    N, M = 2 ** n, 2 ** l
-    r = N // M  # regular cells per coarse cell
-    o = _node_offset(centring)
-    R = np.zeros((M, N), dtype=np.float64)
-    for k in range(M):
-        for j in range(N):
-            dist = _periodic_distance(j + o, (k + o) * r, N)  # in fine cells
-            R[k, j] = max(0.0, 1.0 - dist / r) / r
-    return R
+    r = 2 ** (n - l)  # regular cells per coarse cell
+    return np.maximum(0.0, 1.0 - _coarse_fine_distance(n, l, centring) / r) / r
 
 
 def restrict(rho_reg, n, l, centring="node"):
@@ -210,6 +215,8 @@ def restrict(rho_reg, n, l, centring="node"):
     product of 1D operators; applied axis by axis with a dense matrix."""
     out = np.asarray(rho_reg, dtype=np.float64)
     for m, lm in enumerate(l):
+        if lm == n:
+            continue  # R = identity along this axis
         R = restriction_matrix_1d(n, lm, centring)
         out = np.moveaxis(np.tensordot(R, np.moveaxis(out, m, 0), axes=(1, 0)), 0, m)
     return out
@@ -218,15 +225,8 @@ def restrict(rho_reg, n, l, centring="node"):
 def prolongation_matrix_1d(n, l, centring="node"):
     """P along one axis from level l to the level-n nodes (eq. restriction):
     entry [j, k] = W(x~_j - x_k) with the coarse spacing h_l."""
-    N, M = 2 ** n, 2 ** l
-    r = N // M
-    o = _node_offset(centring)
-    P = np.zeros((N, M), dtype=np.float64)
-    for j in range(N):
-        for k in range(M):
-            dist = _periodic_distance(j + o, (k + o) * r, N)
-            P[j, k] = max(0.0, 1.0 - dist / r)
-    return P
+    r = 2 ** (n - l)
+    return np.maximum(0.0, 1.0 - _coarse_fine_distance(n, l, centring).T / r)
 
 
 def prolong(field, n, l, centring="node"):
@@ -234,8 +234,32 @@ def prolong(field, n, l, centring="node"):
     nodes (eq. restriction), axis by axis."""
     out = np.asarray(field, dtype=np.float64)
     for m, lm in enumerate(l):
+        if lm == n:
+            continue  # P = identity along this axis
         P = prolongation_matrix_1d(n, lm, centring)
         out = np.moveaxis(np.tensordot(P, np.moveaxis(out, m, 0), axes=(1, 0)), 0, m)
+    return out
+
+
+def prolong_at(field, n, l, idx, centring="node"):
+    """(P_i field)(x~_j) at the regular nodes j = idx[s] (an S x d integer
+    array) only: the rows j of the per-axis P (eq. restriction), each with at
+    most two non-zero entries (the bracketing coarse nodes)."""
+    idx = np.asarray(idx)
+    S, d = idx.shape
+    ks, ws = [], []
+    for m, lm in enumerate(l):
+        rows = prolongation_matrix_1d(n, lm, centring)[idx[:, m]]  # S x 2^lm
+        top = np.argsort(-rows, axis=1, kind="stable")[:, :2]
+        ks.append(top)
+        ws.append(np.take_along_axis(rows, top, axis=1))
+    out = np.zeros(S)
+    field = np.asarray(field, dtype=np.float64)
+    for corner in itertools.product((0, 1), repeat=d):
+        w = np.ones(S)
+        for m in range(d):
+            w = w * ws[m][:, corner[m]]
+        out += w * field[tuple(ks[m][:, corner[m]] for m in range(d))]
     return out
 
 

@@ -272,3 +272,14 @@ def test_cell_run_conserves_charge_on_every_grid(d, n, tau):
     dg = run.diagnostics()
     assert dg["charge_grid_max_abs_err"] < 1e-11 * abs(dg["charge_total"])
     assert abs(dg["charge_combined"] - dg["charge_total"]) < 1e-11 * abs(dg["charge_total"])
+
+
+@pytest.mark.parametrize("centring", ["node", "cell"])
+def test_prolong_at_equals_prolong(centring):
+    """prolong_at (rows of P at chosen regular nodes) == prolong, sampled."""
+    rng = np.random.default_rng(61)
+    n, l = 6, (3, 5)
+    E = rng.standard_normal((8, 32))
+    full = O.prolong(E, n, l, centring)
+    idx = rng.integers(0, 64, size=(300, 2))
+    np.testing.assert_allclose(O.prolong_at(E, n, l, idx, centring), full[idx[:, 0], idx[:, 1]], rtol=0, atol=1e-14)
