@@ -270,6 +270,9 @@ def main():
     ap.add_argument("--mode", default="combine", choices=["combine", "filter"],
                     help="combine: solves on every component grid, fields combined (the default line); "
                          "filter: the paper's filter mode (eq. sparse_filter, Algorithm 2)")
+    ap.add_argument("--centring", default="node", choices=["node", "cell"],
+                    help="node: nodes at k h (the default line); cell: nodes at cell centres with the "
+                         "two-step shape of Appendix A")
     ap.add_argument("--solve-variant", default="auto", choices=["auto", "passes", "one-block"],
                     help="component-grid solve: timed choice at init (default), or fixed; a profiler's "
                          "serialised launches distort the timed choice, so profile with the variant the "
@@ -308,7 +311,7 @@ def main():
     q = torch.from_numpy(wl.q.astype(np.float32)).to(dev)
     sort_every = args.sort_every if args.sort_every > 0 else 4  # the library default
     run = Run(wl.L, n, u, v, q, wl.dt, tau=wl.tau, precision="fp32", sort_every=sort_every,
-              stream=stream.cuda_stream, mode=args.mode)
+              stream=stream.cuda_stream, mode=args.mode, centring=args.centring)
     if args.solve_variant != "auto":
         run.set_solve_variant(args.solve_variant)
     del u, v, q
@@ -389,7 +392,7 @@ def main():
         import ctypes as C
         t0 = time.perf_counter()
         r2 = Run(wl.L, n, hu, hv, hq, wl.dt, tau=wl.tau, precision="fp32", sort_every=sort_every,
-                 stream=stream.cuda_stream, mode=args.mode)
+                 stream=stream.cuda_stream, mode=args.mode, centring=args.centring)
         if args.solve_variant != "auto":
             r2.set_solve_variant(args.solve_variant)
         diag_bytes = 0
@@ -435,6 +438,7 @@ def main():
                           "particles_per_gpu": np_, "sort_every": sort_every, "l2": "flushed before every step",
                           "mode": args.mode + (" (stage 'solve' = density filter, 'combine' = regular-grid solve)"
                                                if args.mode == "filter" else ""),
+                          "centring": args.centring,
                           "combine": "float-float (48-bit) accumulation, FP64 diagnostics",
                           "parallelism": f"{world} independent replicas"},
                "latency_ms": {"p50": p50, "p99": p99},

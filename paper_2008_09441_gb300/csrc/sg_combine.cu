@@ -76,27 +76,44 @@ struct RowTerm {
   real w[1 << (D - 1)];
 };
 
-template <typename real, int D>
+// The two level-lev nodes that bracket regular node y along one axis and
+// the weight of the second: node-centred, y / 2^r in coarse units (r = n -
+// lev); cell-centred, (y + 1/2) / 2^r - 1/2 = (2y + 1 - 2^r) / 2^(r+1), whose
+// floor may be -1 (wrapped).  Both weights are dyadic: exact.
+template <typename real, bool CELL>
+__device__ __forceinline__ void bracket(int y, int n, int lev, int& k0, int& k1, real& f) {
+  const int r = n - lev;
+  const int nl = 1 << lev;
+  if (!CELL) {
+    k0 = y >> r;
+    f = (real)(y & ((1 << r) - 1)) * ((real)1 / (real)(1 << r));
+  } else {
+    const int num = 2 * y + 1 - (1 << r);
+    const int fl = num >> (r + 1);  // arithmetic shift: floor
+    f = (real)(num - fl * (2 << r)) * ((real)1 / (real)(2 << r));
+    k0 = fl & (nl - 1);
+  }
+  k1 = (k0 + 1) & (nl - 1);
+}
+
+template <typename real, int D, bool CELL>
 __device__ __forceinline__ RowTerm<real, D> row_term(const GridDesc& g, int n, int y, int z) {
   RowTerm<real, D> t;
   const int nx = 1 << g.l[0];
-  const int ry = n - g.l[1];
   const int ny = 1 << g.l[1];
-  const int ky0 = y >> ry;
-  const int ky1 = (ky0 + 1) & (ny - 1);
+  int ky0, ky1;
+  real fy;
+  bracket<real, CELL>(y, n, g.l[1], ky0, ky1, fy);
   const real c = (real)g.coeff;
-  const real fy = (real)(y & ((1 << ry) - 1)) * ((real)1 / (real)(1 << ry));
   if (D == 2) {
     t.off[0] = g.offset + ky0 * nx;
     t.off[(1 << (D - 1)) - 1] = g.offset + ky1 * nx;
     t.w[0] = c * ((real)1 - fy);
     t.w[(1 << (D - 1)) - 1] = c * fy;
   } else {
-    const int rz = n - g.l[D - 1];
-    const int nz = 1 << g.l[D - 1];
-    const int kz0 = z >> rz;
-    const int kz1 = (kz0 + 1) & (nz - 1);
-    const real fz = (real)(z & ((1 << rz) - 1)) * ((real)1 / (real)(1 << rz));
+    int kz0, kz1;
+    real fz;
+    bracket<real, CELL>(z, n, g.l[D - 1], kz0, kz1, fz);
     constexpr int R = 1 << (D - 1);
     t.off[0] = g.offset + (kz0 * ny + ky0) * nx;
     t.off[1 % R] = g.offset + (kz0 * ny + ky1) * nx;
@@ -159,9 +176,70 @@ __device__ __forceinline__ CAcc<real> level_term1(const RowTerm<real, D>* rt_tab
   return acc;
 }
 
+// Cell-centred grids.  Linear interpolation through the centres of a
+// level-l line is the node-centred interpolant of the level-(l+1) line
+// whose odd nodes are the centres (g[2k+1] = E[k]) and whose even nodes are
+// the midpoints (g[2k] = (E[k-1] + E[k]) / 2); the regular centres are the
+// midpoints of the level-n nodes.  So the same Horner scheme runs with each
+// grid entering one level higher as g, and the regular-centre values are
+// (T[j] + T[j+1]) / 2 of its level-n result, plus the grids of x level n
+// at their own centres.
+
+// g of the grids of x level `level - 1` at Horner level `level`, index t.
+template <typename real, int D>
+__device__ __forceinline__ CAcc<real> cell_term1(const RowTerm<real, D>* rt_tab, const int* lstart, int level,
+                                                 const real* __restrict__ Em, int t) {
+  if (level < 1) return CAcc<real>::zero();
+  const int lc = level - 1, nc = 1 << lc;
+  if (t & 1) return level_term1<real, D>(rt_tab, lstart, lc, Em, t >> 1);
+  return CAcc<real>::avg(level_term1<real, D>(rt_tab, lstart, lc, Em, ((t >> 1) - 1) & (nc - 1)),
+                         level_term1<real, D>(rt_tab, lstart, lc, Em, t >> 1));
+}
+
+// Adds g of every grid of x level `level - 1` to the K >= 2 consecutive
+// values T[0..K) at Horner-level index x0.. (x0 a multiple of K): the
+// grid's K/2 centre values from x0/2 on (vector loads once K/2 >= 4) and
+// the one before, periodically.
+template <typename real, int D, int K>
+__device__ __forceinline__ void add_level_terms_cell(CAcc<real>* T, const RowTerm<real, D>* rt_tab,
+                                                     const int* lstart, int level, const real* __restrict__ Em,
+                                                     int x0) {
+  constexpr int R = 1 << (D - 1);
+  constexpr int H = K / 2;
+  const int lc = level - 1, nc = 1 << lc;
+  const int c0 = x0 >> 1, cm = (c0 - 1) & (nc - 1);
+  for (int gi = lstart[lc]; gi < lstart[lc + 1]; ++gi) {
+    const RowTerm<real, D> rt = rt_tab[gi];
+    real t[H + 1];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const real* row = Em + rt.off[r];
+      const real w = rt.w[r];
+      const real prev = row[cm];
+      t[0] = r == 0 ? w * prev : fma(w, prev, t[0]);
+      if constexpr (H >= 4) {
+#pragma unroll
+        for (int k = 0; k < H; k += 4) {
+          const V4<real> a = ld4(row + c0 + k);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) t[1 + k + q] = r == 0 ? w * a.x[q] : fma(w, a.x[q], t[1 + k + q]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < H; ++k) t[1 + k] = r == 0 ? w * row[c0 + k] : fma(w, row[c0 + k], t[1 + k]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      T[2 * j + 1] = CAcc<real>::add_term(T[2 * j + 1], t[j + 1]);
+      T[2 * j] = CAcc<real>::add_term(T[2 * j], (real)0.5 * (t[j] + t[j + 1]));
+    }
+  }
+}
+
 // One Horner step in the register phase: Vc values per lane -> 2 Vc, then
 // add the new level's terms; recurse up to level n (2 Vc <= VMAX).
-template <typename real, int D, int Vc, int VMAX>
+template <typename real, int D, int Vc, int VMAX, bool CELL>
 struct CombLevels {
   static __device__ __forceinline__ void run(CAcc<real>* T, int& level, int n, int lane,
                                              const RowTerm<real, D>* rt_tab, const int* lstart,
@@ -176,14 +254,16 @@ struct CombLevels {
       }
       ++level;
       constexpr int K = 2 * Vc;
-      if constexpr (K >= 4) {
+      if constexpr (CELL) {
+        add_level_terms_cell<real, D, K>(T, rt_tab, lstart, level, Em, lane * K);
+      } else if constexpr (K >= 4) {
         add_level_terms<real, D, K>(T, rt_tab, lstart, level, Em, lane * K);
       } else {
 #pragma unroll
         for (int k = 0; k < K; ++k)
           T[k] = CAcc<real>::add(T[k], level_term1<real, D>(rt_tab, lstart, level, Em, lane * K + k));
       }
-      if (level < n) CombLevels<real, D, 2 * Vc, VMAX>::run(T, level, n, lane, rt_tab, lstart, Em);
+      if (level < n) CombLevels<real, D, 2 * Vc, VMAX, CELL>::run(T, level, n, lane, rt_tab, lstart, Em);
     }
   }
 };
@@ -232,7 +312,7 @@ __host__ __device__ constexpr size_t combine_table_bytes(int ngl) {
 template <int D, int NC>
 constexpr int combine_out_stride() { return NC == 1 ? 1 : ec_stride<D>(); }
 
-template <typename real, int D, int V, int NC>
+template <typename real, int D, int V, int NC, bool CELL>
 __global__ void __launch_bounds__(256) k_combine_warp(const GridDesc* __restrict__ grids, LevelLists ll, int lmin,
                                                       const real* __restrict__ E, size_t S, int n,
                                                       real* __restrict__ Ehi, float* __restrict__ Elo,
@@ -263,22 +343,26 @@ __global__ void __launch_bounds__(256) k_combine_warp(const GridDesc* __restrict
   real* stage = reinterpret_cast<real*>(smem_raw + combine_table_bytes<real, D, NC>(ngl));
   const int row0 = blockIdx.x * RPB;
   pdl_trigger();
-  for (int gi = lane; gi < ngl; gi += 32) rt_tab[gi] = row_term<real, D>(grids[ll.grid[gi]], n, y, z);
+  for (int gi = lane; gi < ngl; gi += 32) rt_tab[gi] = row_term<real, D, CELL>(grids[ll.grid[gi]], n, y, z);
   __syncthreads();
   pdl_wait();  // the solve's fields
   real energy = (real)0;
   if (row < rows) {
     CAcc<real> T[V];
     // coarse phase: one value on 2^level lanes, up to 32 values; the terms
-    // of all coarse levels are read first (independent loads)
-    int level = min(lmin, min(n, 5));
+    // of all coarse levels are read first (independent loads).  Cell-centred
+    // grids enter one level higher.
+    int level = min(CELL ? lmin + 1 : lmin, min(n, 5));
     const int ltop = min(n, 5);
     CAcc<real> sc[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       const int l = level + j;
-      sc[j] = (l <= ltop && lane < (1 << l)) ? level_term1<real, D>(rt_tab, s_start, l, Em, lane)
-                                             : CAcc<real>::zero();
+      if (l <= ltop && lane < (1 << l))
+        sc[j] = CELL ? cell_term1<real, D>(rt_tab, s_start, l, Em, lane)
+                     : level_term1<real, D>(rt_tab, s_start, l, Em, lane);
+      else
+        sc[j] = CAcc<real>::zero();
     }
     T[0] = sc[0];
 #pragma unroll
@@ -294,7 +378,25 @@ __global__ void __launch_bounds__(256) k_combine_warp(const GridDesc* __restrict
       }
     }
     // register phase: 2^level / 32 consecutive values per lane
-    if (level < n) CombLevels<real, D, 1, V>::run(T, level, n, lane, rt_tab, s_start, Em);
+    if (level < n) CombLevels<real, D, 1, V, CELL>::run(T, level, n, lane, rt_tab, s_start, Em);
+    if constexpr (CELL) {  // to the regular centres, then the grids of x level n
+      if (N >= 32) {
+        const CAcc<real> right = T[0].shfl((lane + 1) & 31);
+#pragma unroll
+        for (int k = 0; k < V; ++k) T[k] = CAcc<real>::avg(T[k], k == V - 1 ? right : T[k + 1]);
+        if constexpr (V >= 4) {
+          add_level_terms<real, D, V>(T, rt_tab, s_start, n, Em, lane * V);
+        } else {
+#pragma unroll
+          for (int k = 0; k < V; ++k)
+            T[k] = CAcc<real>::add(T[k], level_term1<real, D>(rt_tab, s_start, n, Em, lane * V + k));
+        }
+      } else {
+        const CAcc<real> right = T[0].shfl((lane + 1) & (N - 1));
+        T[0] = CAcc<real>::avg(T[0], right);
+        if (lane < N) T[0] = CAcc<real>::add(T[0], level_term1<real, D>(rt_tab, s_start, n, Em, lane));
+      }
+    }
     // hi parts to the block's node-interleaved stage, lo planes straight out
     const size_t o0 = (size_t)m * ND + (size_t)row * N;
     const int nb = (row - row0) * N;  // first node of this line in the block
@@ -350,7 +452,7 @@ __global__ void __launch_bounds__(256) k_combine_warp(const GridDesc* __restrict
 
 // ---------------------------------------------------------------- block-per-line combination (lines > 1024)
 
-template <typename real, int D, int NC>
+template <typename real, int D, int NC, bool CELL>
 __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ grids, LevelLists ll, int lmin,
                                                  const real* __restrict__ E, size_t S, int n, real* __restrict__ Ehi,
                                                  float* __restrict__ Elo, double* __restrict__ partials,
@@ -379,22 +481,19 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
   for (int gi = threadIdx.x; gi < ngl; gi += blockDim.x) {
     const GridDesc g = grids[ll.grid[gi]];
     const int nx = 1 << g.l[0];
-    const int ry = n - g.l[1];
     const int ny = 1 << g.l[1];
-    const int ky0 = y >> ry;
-    const int ky1 = (ky0 + 1) & (ny - 1);
-    const real fy = (real)(y & ((1 << ry) - 1)) * ((real)1 / (real)(1 << ry));  // exact: power of two
+    int ky0, ky1;
+    real fy;
+    bracket<real, CELL>(y, n, g.l[1], ky0, ky1, fy);
     if (D == 2) {
       s_off[gi][0] = g.offset + ky0 * nx;
       s_off[gi][R - 1] = g.offset + ky1 * nx;
       s_w[gi][0] = (real)1 - fy;
       s_w[gi][R - 1] = fy;
     } else {
-      const int rz = n - g.l[D - 1];
-      const int nz = 1 << g.l[D - 1];
-      const int kz0 = z >> rz;
-      const int kz1 = (kz0 + 1) & (nz - 1);
-      const real fz = (real)(z & ((1 << rz) - 1)) * ((real)1 / (real)(1 << rz));
+      int kz0, kz1;
+      real fz;
+      bracket<real, CELL>(z, n, g.l[D - 1], kz0, kz1, fz);
       s_off[gi][0] = g.offset + (kz0 * ny + ky0) * nx;
       s_off[gi][1 % R] = g.offset + (kz0 * ny + ky1) * nx;
       s_off[gi][2 % R] = g.offset + (kz1 * ny + ky0) * nx;
@@ -408,30 +507,46 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
   }
   __syncthreads();
 
+  // the transverse interpolation of grid gi, component m, at x index kx
+  auto tval = [&](int gi, int m, int kx) {
+    const real* base = E + (size_t)m * S + kx;
+    real val = s_w[gi][0] * base[s_off[gi][0]];
+#pragma unroll
+    for (int r = 1; r < R; ++r) val = fma(s_w[gi][r], base[s_off[gi][r]], val);
+    return val;
+  };
   // every (level, x index) of the levels Horner reads: each grid's term in
   // the run's precision (one rounding per product, like the component field
   // itself), then an error-free addition into the accumulator, so the
-  // alternating-sign sum loses nothing to cancellation
-  for (int e = threadIdx.x + (1 << lmin); e < 2 * N; e += blockDim.x) {
+  // alternating-sign sum loses nothing to cancellation.  Cell-centred grids
+  // of x level l enter at level l+1 as centre values (odd) and midpoints
+  // (even), as in the warp kernel.
+  const int l0 = CELL ? min(lmin + 1, n) : lmin;
+  for (int e = threadIdx.x + (1 << l0); e < 2 * N; e += blockDim.x) {
     const int l = 31 - __clz(e);
     const int kx = e - (1 << l);
     Acc<real> acc[NC];
-    for (int gi = s_start[l]; gi < s_start[l + 1]; ++gi) {
+    const int lg = CELL ? l - 1 : l;
+    for (int gi = s_start[lg]; gi < s_start[lg + 1]; ++gi) {
       const real c = s_c[gi];
 #pragma unroll
       for (int m = 0; m < NC; ++m) {
-        const real* base = E + (size_t)m * S + kx;
-        real val = s_w[gi][0] * base[s_off[gi][0]];
-#pragma unroll
-        for (int r = 1; r < R; ++r) val = fma(s_w[gi][r], base[s_off[gi][r]], val);
-        acc[m].add(c * val);  // |c| is 1 or 2 (a power of two): exact
+        if (!CELL) {
+          acc[m].add(c * tval(gi, m, kx));  // |c| is 1 or 2 (a power of two): exact
+        } else if (kx & 1) {
+          acc[m].add(c * tval(gi, m, kx >> 1));
+        } else {
+          const int nc = 1 << lg;
+          acc[m].add((real)0.5 * c * tval(gi, m, ((kx >> 1) - 1) & (nc - 1)));
+          acc[m].add((real)0.5 * c * tval(gi, m, kx >> 1));
+        }
       }
     }
 #pragma unroll
     for (int m = 0; m < NC; ++m) A[m * 2 * N + e] = acc[m];
   }
   __syncthreads();
-  for (int l = lmin; l < n; ++l) {
+  for (int l = l0; l < n; ++l) {
     const int cnt = 2 << l;  // size of level l+1
     const int half = 1 << l;
     for (int e2 = threadIdx.x; e2 < NC * cnt; e2 += blockDim.x) {
@@ -452,7 +567,12 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
   real energy = (real)0;
   for (int e2 = threadIdx.x; e2 < NC * N; e2 += blockDim.x) {
     const int m = e2 >> n, x = e2 & (N - 1);
-    const Acc<real> v = A[m * 2 * N + N + x];
+    Acc<real> v = A[m * 2 * N + N + x];
+    if (CELL) {  // to the regular centres, then the grids of x level n
+      v.add_acc(A[m * 2 * N + N + ((x + 1) & (N - 1))]);
+      v.scale((real)0.5);
+      for (int gi = s_start[n]; gi < s_start[n + 1]; ++gi) v.add(s_c[gi] * tval(gi, m, x));
+    }
     const size_t o = (size_t)m * ND + (size_t)row * N + x;
     Ehi[((size_t)row * N + x) * combine_out_stride<D, NC>() + m] = (real)v.hi();
     if (Elo) Elo[o] = (float)v.lo();
@@ -464,7 +584,7 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
   combine_finalize(partials, (int)gridDim.x, fin, red);
 }
 
-template <typename real, int D, int V, int NC>
+template <typename real, int D, int V, int NC, bool CELL>
 static int launch_combine_warp(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n,
                                real* Ehi, float* Elo, double* energy_partials, const CombineFinal& fin,
                                cudaStream_t s) {
@@ -476,17 +596,17 @@ static int launch_combine_warp(const GridDesc* grids, const LevelLists& ll, int 
                       ((size_t)RPB * N * combine_out_stride<D, NC>() + (size_t)RPB * N / V) * sizeof(real);
   static bool attr_set = false;
   if (!attr_set && smem > 48 * 1024) {
-    SG_CUDA(cudaFuncSetAttribute(k_combine_warp<real, D, V, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SG_CUDA(cudaFuncSetAttribute(k_combine_warp<real, D, V, NC, CELL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024));
     attr_set = true;
   }
-  SG_CUDA(launch_pdl(k_combine_warp<real, D, V, NC>, dim3(blocks), dim3(32 * RPB * NC), smem, s, grids, ll, lmin, E,
+  SG_CUDA(launch_pdl(k_combine_warp<real, D, V, NC, CELL>, dim3(blocks), dim3(32 * RPB * NC), smem, s, grids, ll, lmin, E,
                      S, n, Ehi, Elo, energy_partials, fin));
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
 
-template <typename real, int D, int NC>
+template <typename real, int D, int NC, bool CELL>
 static int launch_combine_nc(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n,
                              real* Ehi, float* Elo, double* energy_partials, const CombineFinal& fin,
                              cudaStream_t s) {
@@ -496,17 +616,17 @@ static int launch_combine_nc(const GridDesc* grids, const LevelLists& ll, int lm
     case 8:
     case 16:
     case 32:
-      return launch_combine_warp<real, D, 1, NC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 1, NC, CELL>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     case 64:
-      return launch_combine_warp<real, D, 2, NC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 2, NC, CELL>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     case 128:
-      return launch_combine_warp<real, D, 4, NC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 4, NC, CELL>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     case 256:
-      return launch_combine_warp<real, D, 8, NC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 8, NC, CELL>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     case 512:
-      return launch_combine_warp<real, D, 16, NC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 16, NC, CELL>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     case 1024:
-      return launch_combine_warp<real, D, 32, NC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 32, NC, CELL>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     default:
       break;
   }
@@ -514,24 +634,30 @@ static int launch_combine_nc(const GridDesc* grids, const LevelLists& ll, int lm
   size_t smem = (size_t)NC * 2 * N * sizeof(Acc<real>);
   static bool attr_set = false;
   if (!attr_set) {
-    SG_CUDA(cudaFuncSetAttribute(k_combine<real, D, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    SG_CUDA(cudaFuncSetAttribute(k_combine<real, D, NC, CELL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  k_combine<real, D, NC><<<rows, 256, smem, s>>>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin);
+  k_combine<real, D, NC, CELL><<<rows, 256, smem, s>>>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
 
 template <typename real, int D>
 int launch_combine(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n, real* Ehi,
-                   float* Elo, double* energy_partials, const CombineFinal& fin, cudaStream_t s, int ncomp) {
-  if (ncomp == 1) return launch_combine_nc<real, D, 1>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
-  return launch_combine_nc<real, D, D>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+                   float* Elo, double* energy_partials, const CombineFinal& fin, cudaStream_t s, int ncomp,
+                   bool cell) {
+  if (cell) {
+    if (ncomp == 1)
+      return launch_combine_nc<real, D, 1, true>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+    return launch_combine_nc<real, D, D, true>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+  }
+  if (ncomp == 1) return launch_combine_nc<real, D, 1, false>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+  return launch_combine_nc<real, D, D, false>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
 }
 
 #define SG_INST_COMB(real, D)                                                                                   \
   template int launch_combine<real, D>(const GridDesc*, const LevelLists&, int, const real*, size_t, int, real*, \
-                                       float*, double*, const CombineFinal&, cudaStream_t, int);
+                                       float*, double*, const CombineFinal&, cudaStream_t, int, bool);
 SG_INST_COMB(float, 2)
 SG_INST_COMB(float, 3)
 SG_INST_COMB(double, 2)

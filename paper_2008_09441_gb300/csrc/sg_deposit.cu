@@ -48,10 +48,12 @@ struct WinAcc<double> {
   static __device__ __forceinline__ double value(T s, double) { return s; }
 };
 
-// Cell index and offset of a scaled coordinate s = u * 2^n in [0, 2^n).
+// Index of the node left of a scaled coordinate s = u * 2^n - shift in
+// [-1/2, 2^n) (shift = 1/2 on cell-centred grids, where node k sits at
+// u = (k + 1/2) / 2^n), wrapped periodically, and the offset from it.
 // FP32: floor through the same 1.5 * 2^23 rounding (ties at exact integers
-// may land on the cell below with offset 1, which deposits identical
-// weights on identical nodes); FP64: a plain truncation.
+// may land on the node below with offset 1, which deposits identical
+// weights on identical nodes); FP64: floor.
 __device__ __forceinline__ void cell_frac(float s, int mask, int& c, float& f) {
   const float t = (s - 0.5f) + 12582912.0f;
   const float fl = t - 12582912.0f;
@@ -59,10 +61,9 @@ __device__ __forceinline__ void cell_frac(float s, int mask, int& c, float& f) {
   f = s - fl;
 }
 __device__ __forceinline__ void cell_frac(double s, int mask, int& c, double& f) {
-  int ci = (int)s;
-  ci = ci < 0 ? 0 : (ci > mask ? mask : ci);
-  c = ci;
-  f = s - (double)ci;
+  const double fl = floor(s);
+  c = (int)fl & mask;
+  f = s - fl;
 }
 
 // ---------------------------------------------------------------- deposit
@@ -83,7 +84,7 @@ __device__ __forceinline__ void cell_frac(double s, int mask, int& c, double& f)
 template <typename real, int D>
 __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, size_t np, int n,
                                                          real inv_cell_vol, real* __restrict__ rho, int side,
-                                                         real scale, real inv_scale) {
+                                                         real scale, real inv_scale, real shift) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using W = WinAcc<real>;
   using T = typename W::T;
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
       bool fast = true;
 #pragma unroll
       for (int m = 0; m < D; ++m) {
-        cell_frac(ub[it][m] * (real)N, mask, c[m], f[m]);
+        cell_frac(ub[it][m] * (real)N - shift, mask, c[m], f[m]);
         l[m] = (c[m] - anchor[m] + half) & mask;
         fast &= l[m] + 1 < side;
       }
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
 
 template <typename real, int D>
 int launch_deposit(const PArrays<real, D>& p, size_t np, int n, real inv_cell_vol, real* rho, int win_cap_nodes,
-                   real scale, real inv_scale, cudaStream_t s) {
+                   real scale, real inv_scale, real shift, cudaStream_t s) {
   if (np == 0) return SG_OK;
   using T = typename WinAcc<real>::T;
   const long long cap = (long long)win_cap_nodes * 8 / (long long)sizeof(T);  // same bytes for either type
@@ -283,7 +284,7 @@ int launch_deposit(const PArrays<real, D>& p, size_t np, int n, real inv_cell_vo
   }
   const size_t nchunks = (np + DEP_CHUNK - 1) / DEP_CHUNK;
   const unsigned blocks = (unsigned)std::min<size_t>(nchunks, (size_t)sms * per_sm);
-  k_deposit<real, D><<<blocks, DEP_THREADS, smem, s>>>(p, np, n, inv_cell_vol, rho, side, scale, inv_scale);
+  k_deposit<real, D><<<blocks, DEP_THREADS, smem, s>>>(p, np, n, inv_cell_vol, rho, side, scale, inv_scale, shift);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
@@ -295,6 +296,23 @@ int launch_deposit(const PArrays<real, D>& p, size_t np, int n, real inv_cell_vo
 // (periodic), which is (h_l / h_{l-1}) sum_k' W_{l-1}(x_k - x_k') a[k'].
 // Composing the steps is exact because a coarse hat is linear between the
 // finer nodes (Appendix A).
+//
+// Cell-centred grids (node k at (k + 1/2) h): the coarse hat is no longer
+// linear between fine nodes and the steps do not compose; R from level n
+// to level l (r = 2^(n-l) fine cells per coarse cell) weights fine value j
+// by (1/r) max(0, 1 - |j + 1/2 - (k + 1/2) r| / r).  It still factors
+// into the same cascade: average neighbouring values onto the cell faces,
+// a[t] = (x[t-1] + x[t]) / 2 (the faces are the nodes of a node-centred
+// level-n line), apply full weighting n-l-1 times, and take the last step's
+// full weighting at the odd nodes instead of the even ones,
+// R_l x[k] = (a[2k] + 2 a[2k+1] + a[2k+2]) / 4.  (The cell-centred
+// prolongation is linear interpolation through the coarse centres; R is
+// (h / h_l) times its transpose, and the prolongation is the node-centred
+// one from level l+1, whose odd nodes are the coarse centres and even nodes
+// their midpoints, sampled at the fine centres, which are the midpoints of
+// the level-n nodes.)  So one register cascade serves every level again:
+// at each step the even full weighting carries the cascade and the odd one
+// is the output.
 //
 // Arrays keep their natural layout [outer][len][inner] (inner = the axes
 // already restricted, contiguous; len = the axis being restricted).  One
@@ -355,6 +373,33 @@ struct RjLevels<real, 1> {
   static __device__ __forceinline__ void run(real*, int&, int, const RjOut<real>&) {}
 };
 
+// Cell-centred cascade: v[0..V) are this lane's V consecutive face values of
+// the current level; emits the odd full weighting (the cell-centred
+// restriction to the next level down) and keeps the even one.
+template <typename real, int V>
+struct RjLevelsCell {
+  static __device__ __forceinline__ void run(real* v, int& level, int tmin, const RjOut<real>& e) {
+    const real left = __shfl_sync(0xffffffffu, v[V - 1], (e.lane + 31) & 31);
+    const real right = __shfl_sync(0xffffffffu, v[0], (e.lane + 1) & 31);
+    real ob[V / 2];
+#pragma unroll
+    for (int k = 0; k < V / 2; ++k) {  // in place: v[k] is written after its last read
+      const real am = (k == 0) ? left : v[2 * k - 1];
+      const real a0 = v[2 * k], a1 = v[2 * k + 1];
+      const real a2 = (k == V / 2 - 1) ? right : v[2 * k + 2];
+      ob[k] = (real)0.25 * a0 + (real)0.5 * a1 + (real)0.25 * a2;
+      v[k] = (real)0.25 * am + (real)0.5 * a0 + (real)0.25 * a1;
+    }
+    --level;
+    e.template emit<V / 2>(ob, level);
+    if (level > tmin) RjLevelsCell<real, V / 2>::run(v, level, tmin, e);
+  }
+};
+template <typename real>
+struct RjLevelsCell<real, 1> {
+  static __device__ __forceinline__ void run(real*, int&, int, const RjOut<real>&) {}
+};
+
 template <typename real, int VPL>
 __device__ __forceinline__ void rj_load_run(const real* p, real* v) {
   if (VPL >= 4 && sizeof(real) == 4) {
@@ -372,7 +417,7 @@ __device__ __forceinline__ void rj_load_run(const real* p, real* v) {
   }
 }
 
-template <typename real, int VPL>
+template <typename real, int VPL, bool CELL>
 __global__ void __launch_bounds__(256) k_restrict_warp(const LineJob* __restrict__ jobs, int njobs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* tile = reinterpret_cast<real*>(smem_raw);
@@ -478,9 +523,22 @@ __global__ void __launch_bounds__(256) k_restrict_warp(const LineJob* __restrict
   const int tmin = J->tmin;
   if (VPL > 1 || top >= 5) {
     e.template emit<VPL>(v, level);
-    if (level > tmin) RjLevels<real, VPL>::run(v, level, tmin, e);
-  } else if (((J->tmask >> level) & 1) && lane < len) {  // a line shorter than a warp
-    reinterpret_cast<real*>(J->dst[level])[((o << level) + lane) * (size_t)inner + i] = v[0];
+    if (CELL) {  // onto the faces: a[t] = (x[t-1] + x[t]) / 2, periodic over the whole line
+      const real left = __shfl_sync(0xffffffffu, v[VPL - 1], (lane + 31) & 31);
+#pragma unroll
+      for (int k = VPL - 1; k > 0; --k) v[k] = (real)0.5 * (v[k - 1] + v[k]);
+      v[0] = (real)0.5 * (left + v[0]);
+      if (level > tmin) RjLevelsCell<real, VPL>::run(v, level, tmin, e);
+    } else {
+      if (level > tmin) RjLevels<real, VPL>::run(v, level, tmin, e);
+    }
+  } else {  // a line shorter than a warp
+    if (((J->tmask >> level) & 1) && lane < len)
+      reinterpret_cast<real*>(J->dst[level])[((o << level) + lane) * (size_t)inner + i] = v[0];
+    if (CELL) {
+      const real left = __shfl_sync(0xffffffffu, v[0], (lane - 1) & (len - 1));
+      v[0] = (real)0.5 * (left + v[0]);
+    }
   }
   // one value per lane on m = 2^level lanes
   real a = v[0];
@@ -490,29 +548,42 @@ __global__ void __launch_bounds__(256) k_restrict_warp(const LineJob* __restrict
     const real am = __shfl_sync(0xffffffffu, a, (2 * k - 1) & (m - 1));
     const real a0 = __shfl_sync(0xffffffffu, a, (2 * k) & (m - 1));
     const real ap = __shfl_sync(0xffffffffu, a, (2 * k + 1) & (m - 1));
+    real out;
+    if (CELL) {
+      const real a2 = __shfl_sync(0xffffffffu, a, (2 * k + 2) & (m - 1));
+      out = (real)0.25 * a0 + (real)0.5 * ap + (real)0.25 * a2;
+    }
     a = (real)0.25 * am + (real)0.5 * a0 + (real)0.25 * ap;
+    if (!CELL) out = a;
     --level;
     if (((J->tmask >> level) & 1) && lane < h)
-      reinterpret_cast<real*>(J->dst[level])[((o << level) + lane) * (size_t)inner + i] = a;
+      reinterpret_cast<real*>(J->dst[level])[((o << level) + lane) * (size_t)inner + i] = out;
   }
 }
 
 template <typename real>
 int launch_restrict_pass(const LineJob* jobs_dev, int njobs, int nblocks, int lines_per_block, int vpl,
-                         int smem_bytes, cudaStream_t s) {
+                         int smem_bytes, bool cell, cudaStream_t s) {
   if (njobs == 0 || nblocks == 0) return SG_OK;
   const unsigned threads = 32u * (unsigned)lines_per_block;
-#define SG_RJ_CASE(V)                                                                                     \
-  case V: {                                                                                               \
-    static bool attr_set = false;                                                                         \
-    if (!attr_set) {                                                                                      \
-      SG_CUDA(cudaFuncSetAttribute(k_restrict_warp<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                   200 * 1024));                                                          \
-      attr_set = true;                                                                                    \
-    }                                                                                                     \
-    SG_CUDA(launch_pdl(k_restrict_warp<real, V>, dim3(nblocks), dim3(threads), smem_bytes, s, jobs_dev, njobs)); \
-    break;                                                                                                \
+#define SG_RJ_LAUNCH(V, C)                                                                                   \
+  {                                                                                                          \
+    static bool attr_set = false;                                                                            \
+    if (!attr_set) {                                                                                         \
+      SG_CUDA(cudaFuncSetAttribute(k_restrict_warp<real, V, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                   200 * 1024));                                                             \
+      attr_set = true;                                                                                       \
+    }                                                                                                        \
+    SG_CUDA(launch_pdl(k_restrict_warp<real, V, C>, dim3(nblocks), dim3(threads), smem_bytes, s, jobs_dev,   \
+                       njobs));                                                                              \
   }
+#define SG_RJ_CASE(V)            \
+  case V:                        \
+    if (cell)                    \
+      SG_RJ_LAUNCH(V, true)      \
+    else                         \
+      SG_RJ_LAUNCH(V, false)     \
+    break;
   switch (vpl) {
     SG_RJ_CASE(1)
     SG_RJ_CASE(2)
@@ -527,19 +598,20 @@ int launch_restrict_pass(const LineJob* jobs_dev, int njobs, int nblocks, int li
       return SG_ERR_UNSUPPORTED;
   }
 #undef SG_RJ_CASE
+#undef SG_RJ_LAUNCH
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
 
 #define SG_INST_DEP(real, D)                                                                  \
-  template int launch_deposit<real, D>(const PArrays<real, D>&, size_t, int, real, real*, int, real, real, \
+  template int launch_deposit<real, D>(const PArrays<real, D>&, size_t, int, real, real*, int, real, real, real, \
                                        cudaStream_t);
 
 SG_INST_DEP(float, 2)
 SG_INST_DEP(float, 3)
 SG_INST_DEP(double, 2)
 SG_INST_DEP(double, 3)
-template int launch_restrict_pass<float>(const LineJob*, int, int, int, int, int, cudaStream_t);
-template int launch_restrict_pass<double>(const LineJob*, int, int, int, int, int, cudaStream_t);
+template int launch_restrict_pass<float>(const LineJob*, int, int, int, int, int, bool, cudaStream_t);
+template int launch_restrict_pass<double>(const LineJob*, int, int, int, int, int, bool, cudaStream_t);
 
 }  // namespace sg

@@ -976,6 +976,7 @@ class Engine final : public EngineBase {
     pp.boris = boris ? 1 : 0;
     pp.has_eext = eext ? 1 : 0;
     pp.drift = drift ? 1 : 0;
+    pp.shift = cfg_.cell ? (real)0.5 : (real)0;
     SortFuse sf;
     if (fuse_sort) {
       SG_TRY(sort_reset());
@@ -1017,12 +1018,12 @@ class Engine final : public EngineBase {
   int enqueue_deposit() {
     SG_CUDA(cudaMemsetAsync(rho_reg_, 0, ND_ * sizeof(real), stream_));
     return launch_deposit<real, D>(P_[cur_], np_, n_, inv_cell_vol(), rho_reg_, cfg_.win_cap, (real)dep_scale_,
-                                   (real)(1.0 / dep_scale_), stream_);
+                                   (real)(1.0 / dep_scale_), cfg_.cell ? (real)0.5 : (real)0, stream_);
   }
 
   int enqueue_restrict() {
     for (auto& P : rpasses_)
-      SG_TRY(launch_restrict_pass<real>(P.dev, P.njobs, P.nblocks, P.lpb, P.vpl, P.smem, stream_));
+      SG_TRY(launch_restrict_pass<real>(P.dev, P.njobs, P.nblocks, P.lpb, P.vpl, P.smem, cfg_.cell, stream_));
     return SG_OK;
   }
 
@@ -1104,7 +1105,7 @@ class Engine final : public EngineBase {
     fin.dd = dd_;
     fin.counter = comb_counter_;
     return launch_combine<real, D>(grids_dev_, levels_, lmin_, E_arena_, S_, n_, Ehi_, Elo_, fe_partials_, fin,
-                                   stream_, D);
+                                   stream_, D, cfg_.cell);
   }
 
   // Filter mode (Algorithm 2): rho_f = sum_i c_i P_i R_i rho~ on the regular
@@ -1114,7 +1115,7 @@ class Engine final : public EngineBase {
     CombineFinal off;
     std::memset(&off, 0, sizeof(off));
     return launch_combine<real, D>(grids_dev_, levels_, lmin_, rho_arena_, S_, n_, rho_f_, nullptr, fe_partials_, off,
-                                   stream_, 1);
+                                   stream_, 1, cfg_.cell);
   }
   int enqueue_regular_solve(const double* ke) {
     SG_TRY(launch_regular_solve<real>(rho_f_, regA_, regB_, ktab_, tw_, D, n_, Ehi_, Elo_, ec_stride<D>(),

@@ -61,9 +61,10 @@ constexpr int DEP_ITEMS = 4;
 constexpr int DEP_CHUNK = DEP_THREADS * DEP_ITEMS;
 
 // scale / inv_scale: the FP32 fixed-point scale of the window (WinAcc), 1 for FP64.
+// shift: position of node 0 in cells (0 node-centred, 1/2 cell-centred).
 template <typename real, int D>
 int launch_deposit(const PArrays<real, D>& p, size_t np, int n, real inv_cell_vol, real* rho,
-                   int win_cap_nodes, real scale, real inv_scale, cudaStream_t s);
+                   int win_cap_nodes, real scale, real inv_scale, real shift, cudaStream_t s);
 
 // max_i |x_i| on the host (synchronises the stream; set-up use only).
 template <typename real>
@@ -107,10 +108,11 @@ __device__ __forceinline__ int find_job(const Job* __restrict__ jobs, int njobs)
 
 // Restriction along one axis of every job's lines (full weighting 1/4,
 // 1/2, 1/4 per level halving, the exact form of R along one axis for nested
-// node-centred grids), outputs in the natural layout.
+// node-centred grids; cell = true: R of cell-centred grids through the
+// face-averaged cascade), outputs in the natural layout.
 template <typename real>
 int launch_restrict_pass(const LineJob* jobs_dev, int njobs, int nblocks, int lines_per_block, int vpl,
-                         int smem_bytes, cudaStream_t s);
+                         int smem_bytes, bool cell, cudaStream_t s);
 
 // FFT passes over the component grids.
 enum FftKind { FFT_FWD_FIRST = 0, FFT_FWD_MID = 1, FFT_LAST = 2, FFT_INV_MID = 3, FFT_INV_LAST = 4 };
@@ -193,6 +195,7 @@ struct PushParams {
   int boris;
   int has_eext;
   int drift;      // 0: velocity only (initial half kick), 1: kick + drift
+  real shift;     // position of node 0 in cells: 0 node-centred, 1/2 cell-centred
 };
 
 // Sort work fused into the push on sort steps (keys == nullptr: none).
@@ -257,7 +260,8 @@ struct CombineFinal {
 template <typename real, int D>
 int launch_combine(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n,
                    real* Ehi, float* Elo, double* energy_partials, const CombineFinal& fin,
-                   cudaStream_t s, int ncomp);  // ncomp = D: the fields, interleaved; 1: a density, plain
+                   cudaStream_t s, int ncomp,  // ncomp = D: the fields, interleaved; 1: a density, plain
+                   bool cell);                 // cell-centred grids
 
 template <typename real>
 int launch_grid_charges(const GridDesc* grids, int ngrids, const real* rho, const double* vol,

@@ -45,20 +45,21 @@ struct KeAcc<double> {
   __device__ __forceinline__ double to_double() const { return v; }
 };
 
-// Cell and offset of the gather.  FP32: floor through the 1.5 * 2^23
-// rounding trick (no conversion instruction); a position exactly on a node
-// of odd index may land in the cell below with offset 1, which interpolates
-// the same node value with weight 1.  FP64: truncation.
+// Node left of the gather position s = u * 2^n - shift in [-1/2, 2^n)
+// (shift 1/2 on cell-centred grids), wrapped, and the offset from it.  FP32:
+// floor through the 1.5 * 2^23 rounding trick (no conversion instruction);
+// a position exactly on a node of odd index may land in the cell below
+// with offset 1, which interpolates the same node value with weight 1.
+// FP64: floor.
 __device__ __forceinline__ void gather_cell(float s, int mask, int& c, float& f) {
   const float t = (s - 0.5f) + 12582912.0f;
   c = (__float_as_int(t) - 0x4B400000) & mask;
   f = s - (t - 12582912.0f);
 }
 __device__ __forceinline__ void gather_cell(double s, int mask, int& c, double& f) {
-  int ci = (int)s;
-  ci = ci < 0 ? 0 : (ci > mask ? mask : ci);
-  c = ci;
-  f = s - (double)ci;
+  const double fl = floor(s);
+  c = (int)fl & mask;
+  f = s - fl;
 }
 
 // Periodic wrap of a drifted position: u - floor(u), a rounded-up 1 mapped
@@ -103,7 +104,7 @@ __device__ __forceinline__ void push_one(real (&u)[D], real (&v)[D], real w, int
   real f[D], E[D];
 #pragma unroll
   for (int m = 0; m < D; ++m) {
-    gather_cell(u[m] * (real)N, mask, c[m], f[m]);
+    gather_cell(u[m] * (real)N - pp.shift, mask, c[m], f[m]);
     E[m] = (real)0;
   }
 #pragma unroll
