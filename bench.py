@@ -23,7 +23,14 @@ import sys
 import threading
 import time
 
-import numpy as np
+# The oracle runs single-threaded wherever this file times it (the reference
+# arm here, the CPU baseline in a child process): numpy's BLAS threads are
+# pinned to one before numpy loads, so the reported core count is exact.
+_SINGLE_THREAD_ENV = {"OPENBLAS_NUM_THREADS": "1", "OMP_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+if "reference" in sys.argv:
+    os.environ.update(_SINGLE_THREAD_ENV)
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -154,7 +161,20 @@ def algorithmic_bytes(np_, n, d, real_bytes=4):
     return {"deposit": dep, "push": push}
 
 
-def cpu_baseline(sample_particles=1 << 18, steps=1):
+def cpu_baseline():
+    """cpu_baseline_sample in a child process with one BLAS thread."""
+    env = dict(os.environ, **_SINGLE_THREAD_ENV)
+    code = "import json, bench; print(json.dumps(bench.cpu_baseline_sample()))"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError("cpu baseline failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_sample(sample_particles=1 << 18, min_seconds=10.0, max_steps=50):
+    """The oracle as it stands on a bounded sample: steps of 2^18 particles
+    until about min_seconds of CPU work (at most max_steps)."""
     from oracle import sgpic_oracle as O
     from paper_2008_09441_gb300 import workloads
     wl = workloads.make(WORKLOAD, n_particles=sample_particles)
@@ -163,7 +183,10 @@ def cpu_baseline(sample_particles=1 << 18, steps=1):
     q = wl.q.astype(np.float32).astype(np.float64)
     run = O.OracleRun(wl.L, wl.n, u, v, q, wl.dt, tau=wl.tau)
     t0 = time.perf_counter()
-    run.step(steps)
+    steps = 0
+    while steps < max_steps and (steps == 0 or time.perf_counter() - t0 < min_seconds):
+        run.step(1)
+        steps += 1
     dt = time.perf_counter() - t0
     return {"value": sample_particles * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{steps} step(s) of {sample_particles} particles of the {WORKLOAD} workload "
