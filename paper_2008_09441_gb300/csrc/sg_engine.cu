@@ -890,7 +890,7 @@ class Engine final : public EngineBase {
     } else {
       seq = {{FFT_FWD_FIRST, 0}, {FFT_FWD_MID, 1}, {FFT_LAST, 2}, {FFT_INV_MID, 1}, {FFT_INV_LAST, 0}};
     }
-    const int CAPC = 1024;  // complex values per buffer: one butterfly per thread of 512 per stage
+    const int CAPC = FFT_BLOCK_VALUES;  // complex values per buffer (whole lines, at least one)
     for (auto& ka : seq) {
       const int kind = ka.first, axis = ka.second;
       const bool per_comp = (kind == FFT_INV_MID || kind == FFT_INV_LAST);

@@ -141,6 +141,10 @@ struct SolveArena {
   int dim;
 };
 
+// Complex values per block of a transform pass (whole lines, at least one
+// line per block); the block has half as many threads.
+constexpr int FFT_BLOCK_VALUES = 1024;
+
 template <typename real>
 int launch_fft_pass(int kind, const SolveArena<real>& a, const FftJob* jobs_dev, int njobs,
                     int nblocks, int smem_bytes, cudaStream_t s);

@@ -101,7 +101,7 @@ __device__ __forceinline__ int sfreq(int i, int N) { return i < (N >> 1) ? i : i
 // along axis > 0 consecutive threads take consecutive lines so that strided
 // columns are read together.
 template <typename real>
-__global__ void __launch_bounds__(512) k_fft_pass(int kind, SolveArena<real> a, const FftJob* __restrict__ jobs,
+__global__ void __launch_bounds__(FFT_BLOCK_VALUES / 2) k_fft_pass(int kind, SolveArena<real> a, const FftJob* __restrict__ jobs,
                                                   int njobs) {
   extern __shared__ unsigned char smem_raw[];
   const int b = blockIdx.x;
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(512) k_fft_pass(int kind, SolveArena<real> a, 
         bool nyq_a = false, nyq_b = false;
         for (int q = 0; q < D; ++q) {
           const int Nq = J.dims[q];
-          const real kq = (real)(g.kfac[q] * (double)sfreq(idx[q], Nq));
+          const real kq = (real)g.kfac[q] * (real)sfreq(idx[q], Nq);  // no FP64 on the FP32 path
           k2 += kq * kq;
           if (q == ma) {
             ka = kq;
@@ -235,7 +235,7 @@ int launch_fft_pass(int kind, const SolveArena<real>& a, const FftJob* jobs_dev,
     SG_CUDA(cudaFuncSetAttribute(k_fft_pass<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  SG_CUDA(launch_pdl(k_fft_pass<real>, dim3(nblocks), dim3(512),
+  SG_CUDA(launch_pdl(k_fft_pass<real>, dim3(nblocks), dim3(FFT_BLOCK_VALUES / 2),
                      smem_bytes + ((size_t)1 << (a.log_nmax - 1)) * sizeof(cplx<real>), s, kind, a, jobs_dev, njobs));
   SG_CHECK_LAUNCH();
   return SG_OK;
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(1024) k_solve_small(SolveArena<real> a, int ma
       bool nyq_m = false;
       for (int q = 0; q < D; ++q) {
         const int Nq = 1 << logs[q];
-        const real kq = (real)(g.kfac[q] * (double)sfreq(idx[q], Nq));
+        const real kq = (real)g.kfac[q] * (real)sfreq(idx[q], Nq);
         k2 += kq * kq;
         if (q == m) {
           km = kq;

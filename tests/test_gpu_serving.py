@@ -82,3 +82,38 @@ def test_admission_respects_budget():
     assert all(srv.poll(t)[0] == 2 for t in ts)
     assert max(seen) < 6  # the budget kept some requests queued
     srv.close()
+
+
+def test_modes_and_centrings_in_one_mix():
+    """Runs in the combination and filter modes on node- and cell-centred
+    grids share one batched server; each equals the same run alone."""
+    import torch
+    from paper_2008_09441_gb300 import Run
+    from paper_2008_09441_gb300.sgpic import Server
+    assert torch.cuda.is_available()
+    params = mix_params()[:4]
+    kinds = [("combine", "cell"), ("filter", "node"), ("filter", "cell"), ("combine", "node")]
+    wls = [workloads.serving_run_workload(p) for p in params]
+    srv = Server(hbm_budget_bytes=256 << 20, max_slots=4)
+    tickets = []
+    for p, wl, (mode, cen) in zip(params, wls, kinds):
+        tickets.append(srv.submit(wl.L, wl.n, wl.u.astype(np.float32), wl.v.astype(np.float32),
+                                  wl.q.astype(np.float32), wl.dt, p["steps"], mode=mode, centring=cen))
+    for _ in range(200):
+        srv.tick()
+        if all(srv.poll(t)[0] in (2, 3) for t in tickets):
+            break
+    for t, p, wl, (mode, cen) in zip(tickets, params, wls, kinds):
+        st, diag = srv.poll(t)
+        assert st == 2 and diag["step"] == p["steps"], (t, st)
+        um, vm, _ = srv.result(t)
+        run = Run(wl.L, wl.n, wl.u.astype(np.float32), wl.v.astype(np.float32), wl.q.astype(np.float32), wl.dt,
+                  mode=mode, centring=cen)
+        run.step(p["steps"])
+        ua, va, _ = run.particles()
+        du = um.astype(np.float64) - ua
+        du -= np.round(du)
+        assert np.sqrt(np.sum(du ** 2) / np.sum(ua.astype(np.float64) ** 2)) < 1e-5, (mode, cen)
+        assert nrmse(vm, va) < 1e-5, (mode, cen)
+        run.close()
+    srv.close()
