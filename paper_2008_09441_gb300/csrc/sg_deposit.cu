@@ -75,8 +75,13 @@ __device__ __forceinline__ void cell_frac(double s, int mask, int& c, double& f)
 // centred on it; its four particles (16-byte vector loads) add their CIC
 // weights into the window when all 2^d corners fall inside, else straight to
 // the global grid.  The window's touched box is then added to the global
-// grid row by row (coalesced atomics, zero nodes skipped) and cleared for the
-// next chunk: two block barriers per chunk, no reductions before the adds.
+// grid row by row and cleared for the next chunk: two block barriers per
+// chunk, no reductions before the adds.  FP32: the window's x origin is a
+// multiple of 4 and its side a multiple of 4, so each lane moves four
+// nodes with one 16-byte shared load and one vector global add
+// (red.global.add.v4.f32), skipping groups that are all zero; this matters
+// most a few steps after a sort, when the particles of a chunk have spread
+// and the touched box has grown.  FP64: one atomic add per non-zero node.
 //
 // FP32: WinAcc fixed point with the run's scale 2^(19 - E), max_p |q_p|/V <
 // 2^E (set at upload; charges do not change), so a window of at most 2^11
@@ -144,6 +149,13 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
 #pragma unroll
       for (int m = 0; m < D; ++m) anchor[m] = cell_of(__ldg(p.u[m] + mid), n, N);
     }
+    // window origin (global node of window index 0) per axis; along x a
+    // multiple of 4, so that 4 consecutive window nodes are 4 aligned global
+    // nodes (16-byte vector adds in the flush)
+    int origin[D];
+#pragma unroll
+    for (int m = 0; m < D; ++m) origin[m] = (anchor[m] - half) & mask;
+    origin[0] &= ~3;
     __syncthreads();  // the previous chunk's flush has cleared the window
     if (threadIdx.x < 2 * D) s_box[par ^ 1][threadIdx.x] = threadIdx.x < D ? INT_MAX : INT_MIN;
     int lo[D], hi[D];
@@ -161,7 +173,7 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
 #pragma unroll
       for (int m = 0; m < D; ++m) {
         cell_frac(ub[it][m] * (real)N - shift, mask, c[m], f[m]);
-        l[m] = (c[m] - anchor[m] + half) & mask;
+        l[m] = (c[m] - origin[m]) & mask;
         fast &= l[m] + 1 < side;
       }
       if (fast) {
@@ -237,14 +249,28 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
       for (int r = threadIdx.x >> 5; r < nrows; r += DEP_THREADS / 32) {
         const int ly = blo[1 % D] + (D == 2 ? r : r % ny);
         const int lz = D == 2 ? 0 : blo[D - 1] + r / ny;
-        const size_t gy = (size_t)((anchor[1 % D] - half + ly) & mask);
-        const size_t grow = D == 2 ? gy * N : ((size_t)((anchor[D - 1] - half + lz) & mask) * N + gy) * N;
+        const size_t gy = (size_t)((origin[1 % D] + ly) & mask);
+        const size_t grow = D == 2 ? gy * N : ((size_t)((origin[D - 1] + lz) & mask) * N + gy) * N;
         T* wrow = win + ((size_t)lz * side + ly) * side;
-        for (int x = blo[0] + lane; x <= bhi[0]; x += 32) {
-          const T v = wrow[x];
-          if (v != (T)0) {
-            atomicAdd(&rho[grow + ((anchor[0] - half + x) & mask)], W::value(v, inv_scale));
-            wrow[x] = (T)0;
+        if constexpr (W::fixed) {  // four nodes per lane: one 16-byte shared load, one vector add
+          for (int x = (blo[0] & ~3) + 4 * lane; x <= bhi[0]; x += 128) {
+            const int4 v = *reinterpret_cast<const int4*>(wrow + x);
+            if ((v.x | v.y | v.z | v.w) != 0) {
+              float* dst = rho + grow + ((origin[0] + x) & mask);
+              asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst),
+                           "f"(W::value(v.x, inv_scale)), "f"(W::value(v.y, inv_scale)),
+                           "f"(W::value(v.z, inv_scale)), "f"(W::value(v.w, inv_scale))
+                           : "memory");
+              *reinterpret_cast<int4*>(wrow + x) = make_int4(0, 0, 0, 0);
+            }
+          }
+        } else {
+          for (int x = blo[0] + lane; x <= bhi[0]; x += 32) {
+            const T v = wrow[x];
+            if (v != (T)0) {
+              atomicAdd(&rho[grow + ((origin[0] + x) & mask)], W::value(v, inv_scale));
+              wrow[x] = (T)0;
+            }
           }
         }
       }
@@ -256,14 +282,18 @@ template <typename real, int D>
 int launch_deposit(const PArrays<real, D>& p, size_t np, int n, real inv_cell_vol, real* rho, int win_cap_nodes,
                    real scale, real inv_scale, real shift, cudaStream_t s) {
   if (np == 0) return SG_OK;
+  if (n < 2) {  // the flush adds groups of 4 aligned nodes of a row
+    set_error("deposit: level n must be at least 2");
+    return SG_ERR_UNSUPPORTED;
+  }
   using T = typename WinAcc<real>::T;
   const long long cap = (long long)win_cap_nodes * 8 / (long long)sizeof(T);  // same bytes for either type
-  int side = 2;  // largest even side with side^D <= capacity
+  int side = 4;  // largest multiple of 4 with side^D <= capacity (16-byte window rows)
   while (true) {
     long long nxt = 1;
-    for (int m = 0; m < D; ++m) nxt *= (side + 2);
+    for (int m = 0; m < D; ++m) nxt *= (side + 4);
     if (nxt > cap) break;
-    side += 2;
+    side += 4;
   }
   long long nodes = 1;
   for (int m = 0; m < D; ++m) nodes *= side;

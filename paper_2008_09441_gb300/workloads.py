@@ -20,6 +20,12 @@ dataset is involved):
   L = 1, uniform in area, charge weight 1 + 0.01 cos(3 theta), density
   magnitude 0.1 (omega_p^2 / omega_c^2 = 0.1 with B_z = 1), cold, initial
   velocity the E x B drift of the unperturbed annulus' analytic radial field.
+* ``penning3d`` - 3D electrons in a Penning trap (Section 5.2): periodic
+  [0, 20]^3, B = (0, 0, 5), quadrupole E_ext = (-15/L (x - L/2),
+  -15/L (y - L/2), 30/L (z - L/2)), Gaussian positions about the centre with
+  standard deviations (0.15, 0.05, 0.2) L (wrapped into the box), v ~ N(0, 1)
+  per axis, total charge -1562.5 shared equally, dt = 0.05; the paper's
+  estimator settings are (P_c)_ref = 1 and alpha = 0.005.
 * ``serving_mix`` - parameters of independent runs (dimension, level,
   particle count, amplitude, wavenumber, arrival time).
 """
@@ -108,12 +114,28 @@ def diocotron2d(n_particles=1 << 23, n=9, tau=1, r_in=0.3, r_out=0.4, amplitude=
                     extra={"mode": mode, "amplitude": amplitude})
 
 
+def penning3d(n_particles=1 << 21, n=7, tau=1, Q=-1562.5, Bz=5.0, dt=0.05, steps=300, seed=None):
+    rng = np.random.default_rng(SEED_BASE + 5 if seed is None else seed)
+    L = 20.0
+    sd = np.array([0.15, 0.05, 0.2]) * L
+    x = rng.normal(0.5 * L, sd, size=(n_particles, 3))
+    u = x / L
+    u = u - np.floor(u)
+    u[u >= 1.0] = 0.0
+    v = rng.normal(0.0, 1.0, size=(n_particles, 3))
+    q = np.full(n_particles, Q / n_particles)
+    return Workload("penning3d", 3, (L, L, L), n, tau, u, v, q, dt, B=(0.0, 0.0, Bz),
+                    eext_lin=(-15.0 / L, -15.0 / L, 30.0 / L), steps=steps,
+                    extra={"alpha": 0.005, "pc_ref": 1.0})
+
+
 WORKLOADS = {
     # name: (generator, kwargs) -- the five configurations of the benchmark
     "landau2d_n6_fp64": (landau2d, dict(n_particles=65536, n=6, tau=1, steps=10)),
     "landau2d_n10_fp32": (landau2d, dict(n_particles=4194304, n=10, tau=1, steps=200, seed=SEED_BASE + 1)),
     "twostream3d_n7_fp32": (twostream3d, dict(n_particles=16777216, n=7, tau=1, steps=10)),
     "diocotron2d_n9_fp32": (diocotron2d, dict(n_particles=8388608, n=9, tau=1, steps=1000)),
+    "penning3d_n7_fp32": (penning3d, dict(n_particles=1 << 21, n=7, tau=1, steps=300)),
 }
 
 

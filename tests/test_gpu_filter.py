@@ -91,3 +91,47 @@ def test_adaptive_tau_follows_oracle(torch_cuda, mode):
         assert e_u < 1e-12 and e_v < 1e-12, (s, e_u, e_v)
     assert max(ref.tau_history) > 1  # the case exercises a tau other than the default
     run.close()
+
+
+@pytest.mark.parametrize("mode", ["combine", "filter"])
+def test_penning_adaptive_tau_follows_oracle(torch_cuda, mode):
+    """The paper's 3D Penning trap (Section 5.2: B_z = 5, quadrupole E_ext,
+    Gaussian bunch, (P_c)_ref = 1, alpha = 0.005) with Algorithm 1 before
+    every field evaluation: tau sequence and particle state against the
+    oracle (FP64)."""
+    from paper_2008_09441_gb300._lib import SG_TAU_ADAPTIVE
+    wl = workloads.penning3d(n_particles=20000, n=6, seed=61)
+    run, (u64, v64, q64) = make_run(wl, "fp64", torch_cuda, tau=SG_TAU_ADAPTIVE, alpha=0.005, pc_ref=1.0,
+                                    mode=mode)
+    ref = O.OracleRun(wl.L, wl.n, u64, v64, q64, wl.dt, qm=wl.qm, B=wl.B, eext_lin=wl.eext_lin, tau="adaptive",
+                      mode=mode, alpha=0.005, pc_ref=1.0, tau_constants="paper")
+    assert run.diagnostics()["tau"] == ref.tau_history[0]
+    for s in range(3):
+        run.step(1)
+        ref.step(1)
+        assert run.diagnostics()["tau"] == ref.tau_history[-1], s
+        ug, vg, _ = run.particles()
+        e_u = nrmse_periodic(ug, ref.u)
+        e_v = nrmse(vg, ref.velocities())
+        assert e_u < 1e-12 and e_v < 1e-12, (s, e_u, e_v)
+    run.close()
+
+
+@pytest.mark.parametrize("centring", ["node", "cell"])
+def test_penning_fp32_trajectory(torch_cuda, centring):
+    """Penning trap, FP32 path, fixed tau = 2, five steps (Boris rotation with
+    the quadrupole field) against the FP64 oracle."""
+    wl = workloads.penning3d(n_particles=30000, n=6, tau=2, seed=62)
+    run, (u64, v64, q64) = make_run(wl, "fp32", torch_cuda, centring=centring)
+    ref = O.OracleRun(wl.L, wl.n, u64, v64, q64, wl.dt, qm=wl.qm, tau=2, B=wl.B, eext_lin=wl.eext_lin,
+                      centring=centring)
+    for s in range(5):
+        run.step(1)
+        ref.step(1)
+        ug, vg, _ = run.particles()
+        e_u = nrmse_periodic(ug, ref.u)
+        e_v = nrmse(vg, ref.velocities())
+        assert e_u < TOL["fp32"] and e_v < TOL["fp32"], (s, e_u, e_v)
+    dg, rd = run.diagnostics(), ref.diagnostics()
+    assert abs(dg["field_energy"] - rd["field_energy"]) <= 20 * TOL["fp32"] * abs(rd["field_energy"])
+    run.close()

@@ -116,3 +116,26 @@ def test_cold_two_stream_growth():
     assert amps[idx[-1]] > 20 * amps[0]
     gamma = np.polyfit(ts[idx], np.log(amps[idx]), 1)[0]
     assert gamma == pytest.approx(gamma_th, rel=0.1)
+
+
+def test_penning_axial_leapfrog_closed_form():
+    """Penning trap (Section 5.2) with a vanishing charge: the axial motion is
+    the harmonic oscillator z'' = (q/m) (30/L) (z - L/2), omega_z^2 = 1.5 for
+    electrons.  Leapfrog started with the backward half kick reproduces the
+    discrete cosine z_k - L/2 = a cos(k theta), cos theta = 1 - omega_z^2 dt^2 / 2,
+    exactly; the radial coordinates of a particle on the axis stay put."""
+    from paper_2008_09441_gb300 import workloads
+    wl = workloads.penning3d(n_particles=3, n=3, seed=1)
+    L = wl.L[0]
+    a = 1.3
+    u = np.array([[0.5, 0.5, 0.5 + a / L]] * 3)
+    v = np.zeros((3, 3))
+    q = np.full(3, 1e-200)  # no self-field worth the name
+    run = O.OracleRun(wl.L, wl.n, u, v, q, wl.dt, qm=-1.0, tau=1, B=wl.B, eext_lin=wl.eext_lin)
+    wz2 = 30.0 / L
+    theta = np.arccos(1.0 - wz2 * wl.dt ** 2 / 2.0)
+    for k in range(1, 40):
+        run.step(1)
+        z = run.u[0, 2] * L - L / 2
+        assert abs(z - a * np.cos(k * theta)) < 1e-11, k
+        assert abs(run.u[0, 0] - 0.5) < 1e-14 and abs(run.u[0, 1] - 0.5) < 1e-14
