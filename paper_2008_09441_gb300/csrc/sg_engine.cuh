@@ -32,7 +32,10 @@ struct EngineConfig {
   int sort_every = 0;
   int mode = SG_MODE_COMBINE;
   bool cell = false;  // cell-centred grids (nodes at (k + 1/2) h)
-  int win_cap = 4096;  // deposit window capacity in regular nodes (64-bit accumulators)
+  // deposit window capacity in regular nodes with 64-bit accumulators (64 KB;
+  // a 128 x 128 window of 32-bit fixed point in 2D, 24^3 in 3D): large enough
+  // for a chunk's particles a few steps after a sort
+  int win_cap = 8192;
 };
 
 class EngineBase {
