@@ -823,10 +823,14 @@ class Engine final : public EngineBase {
             set_error("restriction: level out of range");
             return SG_ERR_UNSUPPORTED;
           }
-          J.tmask |= 1 << tl;
-          J.tmin = std::min(J.tmin, tl);
           std::vector<int> key = kv.first;
           key.push_back(tl);
+          if (a < D - 1 && tl == n_) {  // unrestricted along this axis: the source itself, same layout
+            next[key] = prev.at(kv.first);
+            continue;
+          }
+          J.tmask |= 1 << tl;
+          J.tmin = std::min(J.tmin, tl);
           real* dst;
           if (a == D - 1) {  // final pass writes the component grid
             int gi = find_grid(key);
@@ -837,8 +841,13 @@ class Engine final : public EngineBase {
           }
           J.dst[tl] = dst;
         }
+        if (J.tmask == 0) continue;  // every target aliases the source
         total_lines += outer * inner;
         jobs.push_back(J);
+      }
+      if (jobs.empty()) {  // e.g. tau = n: nothing to restrict along this axis
+        prev.swap(next);
+        continue;
       }
       // lines per block: contiguous lines (pass 0) need no tile, so blocks
       // are sized to cover every SM twice; strided lines take tiles of 8

@@ -395,7 +395,7 @@ int launch_tile_keys(const PArrays<real, D>& p, size_t np, int n, const SortFuse
 // counts there with native 32-bit shared atomics and issues one global
 // atomic per distinct tile, otherwise each key adds to the global counter.
 constexpr int TB_THREADS = 256;
-constexpr int TB_PER_THREAD = 8;
+constexpr int TB_PER_THREAD = 4;
 constexpr int TB_ITEMS = TB_THREADS * TB_PER_THREAD;
 constexpr int TB_SPAN = 1024;
 
@@ -637,7 +637,7 @@ int launch_tile_scatter(const PArrays<real, D>& src, const PArrays<real, D>& dst
   if (np == 0) return SG_OK;
   const size_t smem = ScatterStage<real, D>::on ? ScatterStage<real, D>::bytes : 0;
   static bool attr_set = false;
-  if (!attr_set && smem > 48 * 1024) {
+  if (!attr_set && smem > 0) {  // with the static counters the total may pass 48 KB
     SG_CUDA(cudaFuncSetAttribute(k_tile_scatter<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr_set = true;
   }
