@@ -200,7 +200,8 @@ int sg_pic_get_grids(sg_pic* h, int* n_grids, int* levels, int* coeffs, int cap)
 /* Checkpoint: *size receives the byte size; with buf != NULL and *size large
  * enough, writes the full run state (particles in original order, step, tau,
  * time-centring).  sg_pic_load restores it into a run created with the same
- * domain, level, dimension, precision and particle count. */
+ * domain, level, dimension, precision, particle count, mode and centring;
+ * otherwise SG_ERR_INVALID. */
 int sg_pic_save(sg_pic* h, void* buf, size_t* size);
 int sg_pic_load(sg_pic* h, const void* buf, size_t size);
 

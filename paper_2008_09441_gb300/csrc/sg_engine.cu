@@ -455,7 +455,7 @@ class Engine final : public EngineBase {
   // Checkpoint layout: header, then u[d], v[d], w arrays in original order.
   struct Header {
     char magic[8];
-    int version, dim, precision, n, tau, adaptive;
+    int version, dim, precision, n, tau, adaptive, mode, centring;
     long long np, step;
     double dt;
     DevDiag dd;
@@ -469,8 +469,10 @@ class Engine final : public EngineBase {
     }
     Header hd;
     std::memset(&hd, 0, sizeof(hd));
-    std::memcpy(hd.magic, "SGPICv1", 8);
-    hd.version = 1;
+    std::memcpy(hd.magic, "SGPICv2", 8);
+    hd.version = 2;
+    hd.mode = cfg_.mode;
+    hd.centring = cfg_.cell ? SG_CELL_CENTRED : SG_NODE_CENTRED;
     hd.dim = D;
     hd.precision = sizeof(real) == 4 ? SG_FP32 : SG_FP64;
     hd.n = n_;
@@ -501,9 +503,11 @@ class Engine final : public EngineBase {
     if (!buf || size < sizeof(Header)) return size_error("sg_pic_load");
     Header hd;
     std::memcpy(&hd, buf, sizeof(hd));
-    if (std::memcmp(hd.magic, "SGPICv1", 8) != 0 || hd.dim != D ||
-        hd.precision != (sizeof(real) == 4 ? SG_FP32 : SG_FP64) || hd.n != n_ || hd.np != (long long)np_) {
-      set_error("sg_pic_load: checkpoint does not match this run (magic, dim, precision, level or particle count)");
+    if (std::memcmp(hd.magic, "SGPICv2", 8) != 0 || hd.dim != D ||
+        hd.precision != (sizeof(real) == 4 ? SG_FP32 : SG_FP64) || hd.n != n_ || hd.np != (long long)np_ ||
+        hd.mode != cfg_.mode || hd.centring != (cfg_.cell ? SG_CELL_CENTRED : SG_NODE_CENTRED)) {
+      set_error("sg_pic_load: checkpoint does not match this run (magic, dim, precision, level, particle count, "
+                "mode or centring)");
       return SG_ERR_INVALID;
     }
     size_t need = sizeof(Header) + (size_t)(2 * D + 1) * np_ * sizeof(real);

@@ -158,3 +158,22 @@ def test_cell_invalid_centring_rejected(torch_cuda):
     wl = workloads.landau2d(n_particles=1000, n=5, tau=1, seed=551)
     with pytest.raises(SGError):
         make_run(wl, "fp64", torch_cuda, centring=7)
+
+
+def test_cell_save_load_continues_and_rejects_other_centring(torch_cuda):
+    from paper_2008_09441_gb300 import SGError
+    wl = workloads.landau2d(n_particles=20000, n=6, tau=1, seed=561)
+    a, _ = make_run(wl, "fp64", torch_cuda, centring="cell")
+    a.step(3)
+    blob = a.save()
+    a.step(3)
+    b, _ = make_run(wl, "fp64", torch_cuda, centring="cell")
+    b.load(blob)
+    b.step(3)
+    for x, y in zip(a.particles(), b.particles()):
+        assert nrmse(x, y) < 1e-13
+    c, _ = make_run(wl, "fp64", torch_cuda)  # node-centred
+    with pytest.raises(SGError):
+        c.load(blob)
+    for r in (a, b, c):
+        r.close()
