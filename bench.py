@@ -38,6 +38,12 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s and HBM-roofline fraction (deposit, gather); p50/p99 step latency"
 UNIT = "particle-steps/s"
 WORKLOAD = "landau2d_n10_fp32"
+# --workload name -> registered workload (the first is the default line)
+WORKLOAD_NAMES = {"landau": "landau2d_n10_fp32", "twostream3d": "twostream3d_n7_fp32",
+                  "diocotron2d": "diocotron2d_n9_fp32", "penning3d": "penning3d_n7_fp32"}
+DESCRIPTIONS = {"landau2d": "2D Landau damping", "twostream3d": "3D two-stream instability",
+                "diocotron2d": "2D diocotron annulus (B_z = 1, Boris)",
+                "penning3d": "3D Penning trap (B_z = 5, quadrupole E_ext, Boris)"}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -161,10 +167,10 @@ def algorithmic_bytes(np_, n, d, real_bytes=4):
     return {"deposit": dep, "push": push}
 
 
-def cpu_baseline():
+def cpu_baseline(workload=WORKLOAD):
     """cpu_baseline_sample in a child process with one BLAS thread."""
     env = dict(os.environ, **_SINGLE_THREAD_ENV)
-    code = "import json, bench; print(json.dumps(bench.cpu_baseline_sample()))"
+    code = f"import json, bench; print(json.dumps(bench.cpu_baseline_sample({workload!r})))"
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
     if r.returncode != 0:
@@ -172,16 +178,16 @@ def cpu_baseline():
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline_sample(sample_particles=1 << 18, min_seconds=10.0, max_steps=50):
+def cpu_baseline_sample(workload=WORKLOAD, sample_particles=1 << 18, min_seconds=10.0, max_steps=50):
     """The oracle as it stands on a bounded sample: steps of 2^18 particles
     until about min_seconds of CPU work (at most max_steps)."""
     from oracle import sgpic_oracle as O
     from paper_2008_09441_gb300 import workloads
-    wl = workloads.make(WORKLOAD, n_particles=sample_particles)
+    wl = workloads.make(workload, n_particles=sample_particles)
     u = wl.u.astype(np.float32).astype(np.float64)
     v = wl.v.astype(np.float32).astype(np.float64)
     q = wl.q.astype(np.float32).astype(np.float64)
-    run = O.OracleRun(wl.L, wl.n, u, v, q, wl.dt, tau=wl.tau)
+    run = O.OracleRun(wl.L, wl.n, u, v, q, wl.dt, qm=wl.qm, tau=wl.tau, B=wl.B, eext_lin=wl.eext_lin)
     t0 = time.perf_counter()
     steps = 0
     while steps < max_steps and (steps == 0 or time.perf_counter() - t0 < min_seconds):
@@ -189,8 +195,8 @@ def cpu_baseline_sample(sample_particles=1 << 18, min_seconds=10.0, max_steps=50
         steps += 1
     dt = time.perf_counter() - t0
     return {"value": sample_particles * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} step(s) of {sample_particles} particles of the {WORKLOAD} workload "
-                      f"(n=10, tau=1, 19 grids), FP64 numpy oracle, single thread, {dt:.1f} s"}
+            "sample": f"{steps} step(s) of {sample_particles} particles of the {workload} workload "
+                      f"(n={wl.n}, tau={wl.tau}), FP64 numpy oracle, single thread, {dt:.1f} s"}
 
 
 def run_reference(args, world, rank, pg):
@@ -288,7 +294,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--particles", type=int, default=4194304)
+    ap.add_argument("--particles", type=int, default=0, help="0: the workload's own count")
     ap.add_argument("--sort-every", type=int, default=0)
     ap.add_argument("--mode", default="combine", choices=["combine", "filter"],
                     help="combine: solves on every component grid, fields combined (the default line); "
@@ -304,8 +310,11 @@ def main():
     ap.add_argument("--ref-budget-s", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="landau", choices=["landau", "serving"],
-                    help="landau: the 2D n=10 Landau run (default line); serving: the serving mix")
+    ap.add_argument("--workload", default="landau", choices=list(WORKLOAD_NAMES) + ["serving"],
+                    help="landau: the 2D n=10 Landau run (the default line); twostream3d (3D, n=7, "
+                         "16,777,216 particles), diocotron2d (n=9, 8,388,608, Boris), penning3d (n=7, "
+                         "2,097,152, Boris + quadrupole field): the paper's other workloads; serving: the "
+                         "serving mix")
     ap.add_argument("--serving-runs", type=int, default=48)
     ap.add_argument("--serving-max-log2", type=int, default=21)
     args = ap.parse_args()
@@ -327,16 +336,21 @@ def main():
     # timing events all run on it.
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
-    wl = workloads.make(WORKLOAD, n_particles=args.particles, seed=workloads.SEED_BASE + 1 + rank)
+    wname = WORKLOAD_NAMES[args.workload]
+    over = {"seed": workloads.SEED_BASE + 1 + rank}
+    if args.particles > 0:
+        over["n_particles"] = args.particles
+    wl = workloads.make(wname, **over)
     d, n = wl.dim, wl.n
     u = torch.from_numpy(wl.u.astype(np.float32)).to(dev)
     v = torch.from_numpy(wl.v.astype(np.float32)).to(dev)
     q = torch.from_numpy(wl.q.astype(np.float32)).to(dev)
     sort_every = args.sort_every if args.sort_every > 0 else 4  # the library default
-    run = Run(wl.L, n, u, v, q, wl.dt, tau=wl.tau, precision="fp32", sort_every=sort_every,
-              stream=stream.cuda_stream, mode=args.mode, centring=args.centring)
+    run = Run(wl.L, n, u, v, q, wl.dt, tau=wl.tau, qm=wl.qm, B=wl.B, eext_lin=wl.eext_lin, precision="fp32",
+              sort_every=sort_every, stream=stream.cuda_stream, mode=args.mode, centring=args.centring)
     if args.solve_variant != "auto":
         run.set_solve_variant(args.solve_variant)
+    run_grids = run.grids()
     del u, v, q
     # L2 flush between steps: write one buffer larger than L2, then read a
     # second one, so that each step starts with none of its data in L2 and no
@@ -424,8 +438,8 @@ def main():
         from paper_2008_09441_gb300 import _lib as L
         import ctypes as C
         t0 = time.perf_counter()
-        r2 = Run(wl.L, n, hu, hv, hq, wl.dt, tau=wl.tau, precision="fp32", sort_every=sort_every,
-                 stream=stream.cuda_stream, mode=args.mode, centring=args.centring)
+        r2 = Run(wl.L, n, hu, hv, hq, wl.dt, tau=wl.tau, qm=wl.qm, B=wl.B, eext_lin=wl.eext_lin, precision="fp32",
+                 sort_every=sort_every, stream=stream.cuda_stream, mode=args.mode, centring=args.centring)
         if args.solve_variant != "auto":
             r2.set_solve_variant(args.solve_variant)
         diag_bytes = 0
@@ -456,7 +470,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline(wname)
 
     if rank == 0:
         srt = sorted(step_ms)
@@ -465,9 +479,9 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-               "data": "synthetic (seeded Landau-damping particles)",
-               "config": {"workload": f"{WORKLOAD}: 2D Landau damping, n=10, tau=1, 19 component grids, "
-                                      f"{np_} FP32 particles, dt=0.05",
+               "data": f"synthetic (seeded {wl.name} particles)",
+               "config": {"workload": f"{wname}: {DESCRIPTIONS[wl.name]}, n={n}, tau={wl.tau}, "
+                                      f"{len(run_grids)} component grids, {np_} FP32 particles, dt={wl.dt}",
                           "particles_per_gpu": np_, "sort_every": sort_every, "l2": "flushed before every step (512 MB written, then a different 256 MB read)",
                           "mode": args.mode + (" (stage 'solve' = density filter, 'combine' = regular-grid solve)"
                                                if args.mode == "filter" else ""),

@@ -199,13 +199,31 @@ class Engine final : public EngineBase {
 
   int diagnostics(sg_diag* out) override {
     SG_TRY(launch_grid_charges<real>(grids_dev_, ngrids_, rho_arena_, nullptr, charges_dev_, stream_));
-    DevDiag dd;
-    SG_CUDA(cudaMemcpyAsync(&dd, dd_, sizeof(DevDiag), cudaMemcpyDeviceToHost, stream_));
-    std::vector<double> ch(ngrids_);
-    SG_CUDA(cudaMemcpyAsync(ch.data(), charges_dev_, ngrids_ * sizeof(double), cudaMemcpyDeviceToHost, stream_));
-    unsigned long long cks = 0;
-    SG_CUDA(cudaMemcpyAsync(&cks, checksum_, sizeof(cks), cudaMemcpyDeviceToHost, stream_));
+    // one synchronisation: the device record, the checksum, the status word
+    // and the grid charges land in a pinned staging buffer
+    const size_t o_cks = (sizeof(DevDiag) + 15) / 16 * 16, o_st = o_cks + 8, o_ch = o_cks + 16;
+    const size_t bytes = o_ch + (size_t)ngrids_ * sizeof(double);
+    if (bytes > diag_host_bytes_) {
+      if (diag_host_) cudaFreeHost(diag_host_);
+      diag_host_ = nullptr;
+      diag_host_bytes_ = 0;
+      SG_CUDA(cudaHostAlloc(&diag_host_, bytes, cudaHostAllocDefault));
+      diag_host_bytes_ = bytes;
+    }
+    char* h = static_cast<char*>(diag_host_);
+    SG_CUDA(cudaMemcpyAsync(h, dd_, sizeof(DevDiag), cudaMemcpyDeviceToHost, stream_));
+    SG_CUDA(cudaMemcpyAsync(h + o_cks, checksum_, 8, cudaMemcpyDeviceToHost, stream_));
+    SG_CUDA(cudaMemcpyAsync(h + o_st, status_, sizeof(unsigned), cudaMemcpyDeviceToHost, stream_));
+    SG_CUDA(cudaMemcpyAsync(h + o_ch, charges_dev_, ngrids_ * sizeof(double), cudaMemcpyDeviceToHost, stream_));
     SG_CUDA(cudaStreamSynchronize(stream_));
+    DevDiag dd;
+    std::memcpy(&dd, h, sizeof(DevDiag));
+    unsigned long long cks = 0;
+    std::memcpy(&cks, h + o_cks, 8);
+    unsigned st = 0;
+    std::memcpy(&st, h + o_st, sizeof(unsigned));
+    std::vector<double> ch(ngrids_);
+    std::memcpy(ch.data(), h + o_ch, ngrids_ * sizeof(double));
     std::memset(out, 0, sizeof(*out));
     out->step = step_;
     out->t = (double)step_ * cfg_.dt;
@@ -223,7 +241,11 @@ class Engine final : public EngineBase {
     out->field_energy_prev = dd.field_energy_prev;
     out->kinetic_energy = dd.kinetic_energy;
     out->count_checksum = cks;
-    return check_status();
+    if (st & ST_NONFINITE) {
+      set_error("a kernel produced a non-finite particle state");
+      return SG_ERR_NONFINITE;
+    }
+    return SG_OK;
   }
 
   int select_tau(int* tau, double* est_grid, double* est_noise, int cap) override {
@@ -642,6 +664,9 @@ class Engine final : public EngineBase {
     if (stream_) cudaStreamSynchronize(stream_);
     for (auto& b : bufs_) cudaFree(b.p);
     bufs_.clear();
+    if (diag_host_) cudaFreeHost(diag_host_);
+    diag_host_ = nullptr;
+    diag_host_bytes_ = 0;
     for (int i = 0; i < 8; ++i)
       if (ev_[i]) cudaEventDestroy(ev_[i]);
     if (own_stream_ && stream_) cudaStreamDestroy(stream_);
@@ -1301,6 +1326,8 @@ class Engine final : public EngineBase {
   float solve_ms_[2] = {0, 0};
   GridDesc* grids_dev_ = nullptr;
   double* charges_dev_ = nullptr;
+  void* diag_host_ = nullptr;  // pinned staging of the diagnostics read-back
+  size_t diag_host_bytes_ = 0;
   real* rho_arena_ = nullptr;
   cplx<real>* A_ = nullptr;
   cplx<real>* B_ = nullptr;
