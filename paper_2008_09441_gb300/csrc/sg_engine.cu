@@ -1030,7 +1030,6 @@ class Engine final : public EngineBase {
   SortFuse sort_fuse() const {
     SortFuse sf;
     sf.keys = keys_;
-    sf.tile_count = tile_count_;
     sf.checksum = checksum_;
     sf.tile_shift = tile_shift_;
     return sf;

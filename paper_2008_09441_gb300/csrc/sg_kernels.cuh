@@ -205,7 +205,6 @@ struct PushParams {
 // Sort work fused into the push on sort steps (keys == nullptr: none).
 struct SortFuse {
   uint32_t* keys = nullptr;        // tile key per particle (storage order)
-  uint32_t* tile_count = nullptr;  // per-tile counts (zeroed by the caller)
   unsigned long long* checksum = nullptr;
   int tile_shift = 0;              // tile = level-n Morton key >> (D * tile_shift)
 };

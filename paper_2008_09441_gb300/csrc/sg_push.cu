@@ -6,8 +6,8 @@
 //
 // Each thread advances four consecutive particles per iteration with 16-byte
 // vector loads and stores.  On a sort step the kernel also emits the tile key
-// of every new position and the per-tile counts (the first half of the
-// counting sort), and adds sum (cell key + 1) to the checksum.
+// of every new position (the counting sort's keys; k_tile_hist counts them)
+// and adds sum (cell key + 1) to the checksum.
 #include "sg_kernels.cuh"
 
 namespace sg {
@@ -185,16 +185,8 @@ __device__ __forceinline__ uint32_t tile_key(const real (&u)[D], int n, int shif
   return k >> (D * shift);
 }
 
-// Warp-aggregated count of equal tile keys among the active lanes.
-__device__ __forceinline__ void count_tile(uint32_t* tile_count, uint32_t t, bool valid) {
-  const unsigned act = __activemask();
-  const uint32_t key = valid ? t : 0xFFFFFFFFu;
-  const unsigned peers = __match_any_sync(act, key);
-  if (valid && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&tile_count[t], (uint32_t)__popc(peers));
-}
-
 template <typename real, int D>
-__global__ void __launch_bounds__(256, sizeof(real) == 4 ? (D == 2 ? 4 : 3) : 0) k_push(PArrays<real, D> p, size_t np, int n, const real* __restrict__ Ec,
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? (D == 2 ? 4 : 2) : 0) k_push(PArrays<real, D> p, size_t np, int n, const real* __restrict__ Ec,
                                               PushParams<real> pp, double* __restrict__ ke_partials,
                                               unsigned* status, SortFuse sf) {
   __shared__ double red[32];
