@@ -498,6 +498,21 @@ __global__ void __launch_bounds__(TB_THREADS) k_tile_scatter(PArrays<real, D> sr
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t t[TB_PER_THREAD];
   load_keys(keys, np, chunk, t);
+  // the payload's loads go out now, so that their latency overlaps the ranking
+  real pu[TB_PER_THREAD][D], pv[TB_PER_THREAD][D], pw[TB_PER_THREAD];
+  uint32_t ppid[TB_PER_THREAD];
+#pragma unroll
+  for (int k = 0; k < TB_PER_THREAD; ++k) {
+    const size_t i = chunk + (size_t)k * TB_THREADS + threadIdx.x;
+    const bool valid = i < np;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      pu[k][m] = valid ? __ldg(src.u[m] + i) : (real)0;
+      pv[k][m] = valid ? __ldg(src.v[m] + i) : (real)0;
+    }
+    pw[k] = valid ? __ldg(src.w + i) : (real)0;
+    ppid[k] = valid ? __ldg(src.pid + i) : 0u;
+  }
   if (threadIdx.x == 0) {
     s_lo = 0xFFFFFFFFu;
     s_hi = 0;
@@ -560,11 +575,11 @@ __global__ void __launch_bounds__(TB_THREADS) k_tile_scatter(PArrays<real, D> sr
           const uint32_t L = s_cnt[ti] + pos[k];
 #pragma unroll
           for (int m = 0; m < D; ++m) {
-            su[(size_t)m * TB_ITEMS + L] = __ldg(src.u[m] + i);
-            su[(size_t)(D + m) * TB_ITEMS + L] = __ldg(src.v[m] + i);
+            su[(size_t)m * TB_ITEMS + L] = pu[k][m];
+            su[(size_t)(D + m) * TB_ITEMS + L] = pv[k][m];
           }
-          su[(size_t)(2 * D) * TB_ITEMS + L] = __ldg(src.w + i);
-          spid[L] = __ldg(src.pid + i);
+          su[(size_t)(2 * D) * TB_ITEMS + L] = pw[k];
+          spid[L] = ppid[k];
           sdst[L] = s_base[ti] + pos[k];
         }
       }
@@ -597,37 +612,19 @@ __global__ void __launch_bounds__(TB_THREADS) k_tile_scatter(PArrays<real, D> sr
       pos[k] = __shfl_sync(0xffffffffu, base, leader) + (uint32_t)__popc(peers & ((1u << lane) - 1u));
     }
   }
-  // direct move: loads of a group of items first, then the stores
-  constexpr int G = 4;
+  // direct move of the payload loaded at the start
 #pragma unroll
-  for (int g0 = 0; g0 < TB_PER_THREAD; g0 += G) {
-    real pu[G][D], pv[G][D], pw[G];
-    uint32_t pid[G];
+  for (int k = 0; k < TB_PER_THREAD; ++k) {
+    const size_t i = chunk + (size_t)k * TB_THREADS + threadIdx.x;
+    if (i >= np) continue;
+    const uint32_t p = pos[k];
 #pragma unroll
-    for (int k = 0; k < G; ++k) {
-      const size_t i = chunk + (size_t)(g0 + k) * TB_THREADS + threadIdx.x;
-      const bool valid = i < np;
-#pragma unroll
-      for (int m = 0; m < D; ++m) {
-        pu[k][m] = valid ? __ldg(src.u[m] + i) : (real)0;
-        pv[k][m] = valid ? __ldg(src.v[m] + i) : (real)0;
-      }
-      pw[k] = valid ? __ldg(src.w + i) : (real)0;
-      pid[k] = valid ? __ldg(src.pid + i) : 0u;
+    for (int m = 0; m < D; ++m) {
+      dst.u[m][p] = pu[k][m];
+      dst.v[m][p] = pv[k][m];
     }
-#pragma unroll
-    for (int k = 0; k < G; ++k) {
-      const size_t i = chunk + (size_t)(g0 + k) * TB_THREADS + threadIdx.x;
-      if (i >= np) continue;
-      const uint32_t p = pos[g0 + k];
-#pragma unroll
-      for (int m = 0; m < D; ++m) {
-        dst.u[m][p] = pu[k][m];
-        dst.v[m][p] = pv[k][m];
-      }
-      dst.w[p] = pw[k];
-      dst.pid[p] = pid[k];
-    }
+    dst.w[p] = pw[k];
+    dst.pid[p] = ppid[k];
   }
 }
 
