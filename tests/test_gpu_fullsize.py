@@ -1,0 +1,75 @@
+"""The benchmark's own workload at full size, in the launch configuration
+bench.py times (2D Landau damping, n = 10, tau = 1, 19 component grids,
+4,194,304 FP32 particles on the device, sort every 4 steps, graph-launched
+steps), against the FP64 oracle: integer work bit for bit, densities and
+fields in full or at sampled nodes, and the particles' first step on a
+sample the oracle advances one by one."""
+import numpy as np
+import pytest
+
+from oracle import sgpic_oracle as O
+from paper_2008_09441_gb300 import workloads
+from test_gpu_parity import TOL, make_run, nrmse, nrmse_periodic, torch_cuda  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def test_fullsize_landau_bench_configuration(torch_cuda):
+    wl = workloads.make("landau2d_n10_fp32")
+    n, d = wl.n, wl.dim
+    assert wl.n_particles == 4194304 and n == 10 and wl.tau == 1
+    run, (u64, v64, q64) = make_run(wl, "fp32", torch_cuda, sort_every=4)
+    u64 = O.wrap_unit(u64)
+    tol = TOL["fp32"]
+
+    # cell keys and per-cell counts of the uploaded positions: bit-exact
+    keys, counts = run.keys()
+    k_ref = O.cell_keys(u64, n)
+    assert np.array_equal(np.sort(keys), np.sort(k_ref))
+    c_ref = np.bincount(k_ref.astype(np.int64), minlength=2 ** (n * d))
+    assert np.array_equal(counts, c_ref)
+
+    # the regular-grid density in full, every component density (R_i of it,
+    # equal to the direct deposit by Proposition 1) and the combined field
+    # at sampled regular nodes
+    reg = O.deposit_cic(u64, q64, (n,) * d, wl.L)
+    assert nrmse(run.regular_charge(), reg) < tol
+    gq = run.grid_charges()
+    comps = []
+    for l, c in O.combination_grids(d, n, wl.tau):
+        rho = O.restrict(reg, n, l)
+        assert nrmse(gq[l], rho) < tol, l
+        comps.append((l, c, rho, O.solve_poisson_spectral(rho, wl.L)))
+    rng = np.random.default_rng(2008)
+    idx = rng.integers(0, 1 << n, size=(4000, d))
+    Eg = run.field()
+    for m in range(d):
+        ref = sum(c * O.prolong_at(E[m], n, l, idx) for l, c, rho, E in comps)
+        assert nrmse(Eg[m][idx[:, 0], idx[:, 1]], ref) < 20 * tol, m
+
+    # first step on a sample: backward half kick at init, then kick and drift
+    # with the initial field (both use E(x^0))
+    s = np.sort(rng.choice(wl.n_particles, 8192, replace=False))
+    us = u64[s]
+    Ep = O.field_at_particles(comps, us, wl.L, wl.eext_lin)
+    vs = [v64[s, m] for m in range(d)]
+    vh = O.kick_rotate(vs, Ep, wl.qm, -0.5 * wl.dt, wl.B)
+    v1 = O.kick_rotate(vh, Ep, wl.qm, wl.dt, wl.B)
+    u1 = O.drift(us, v1, wl.dt, wl.L)
+    run.step(1)
+    ug, vg, _ = run.particles()
+    assert nrmse_periodic(ug[s], u1) < tol
+    assert nrmse(vg[s], np.stack(v1, axis=1)) < tol
+
+    # three more steps end in a sort step (the push emits the tile keys): the
+    # keys, the counts and the checksum of the GPU's own positions, bit-exact
+    run.step(3)
+    ug, _, _ = run.particles()
+    ug64 = O.wrap_unit(ug.astype(np.float64))
+    k4 = O.cell_keys(ug64, n)
+    keys, counts = run.keys()
+    assert np.array_equal(np.sort(keys), np.sort(k4))
+    c4 = np.bincount(k4.astype(np.int64), minlength=2 ** (n * d))
+    assert np.array_equal(counts, c4)
+    assert run.diagnostics()["count_checksum"] == O.count_checksum(c4)
+    run.close()
