@@ -92,7 +92,7 @@ class Engine final : public EngineBase {
     SG_TRY(alloc((void**)&tile_count_, ntiles_ * 4));
     SG_TRY(alloc((void**)&cursor_, ntiles_ * 4));
     SG_TRY(alloc((void**)&scan_sums_, scan_block_sums_words(ntiles_) * 4));
-    nke_ = push_blocks(np_);
+    nke_ = push_blocks<real, D>(np_);
     SG_TRY(alloc((void**)&ke_partials_, (size_t)nke_ * sizeof(double)));
     SG_CUDA(cudaMemsetAsync(ke_partials_, 0, (size_t)nke_ * sizeof(double), stream_));
 

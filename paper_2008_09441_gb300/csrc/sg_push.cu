@@ -15,13 +15,6 @@ namespace sg {
 static __device__ __forceinline__ bool finite_r(float x) { return isfinite(x); }
 static __device__ __forceinline__ bool finite_r(double x) { return isfinite(x); }
 
-int push_blocks(size_t np) {
-  size_t b = (np / 4 + 255) / 256;
-  const size_t cap = 152 * 8;
-  if (b > cap) b = cap;
-  if (b == 0) b = 1;
-  return (int)b;
-}
 
 // Kinetic-energy accumulator of one thread: FP32 path a float pair whose
 // low part collects the exact rounding error of every addition (two_sum);
@@ -269,10 +262,34 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? (D == 2 ? 4 : 2) : 0)
   if (threadIdx.x == 0 && ke_partials) ke_partials[blockIdx.x] = tot;
 }
 
+// Blocks of the push: one resident wave (SMs x blocks per SM at the kernel's
+// register budget), each block walking its particles grid-stride; fewer for
+// small runs.  A second wave of blocks measured 7% slower on the 2D step.
+template <typename real, int D>
+int push_blocks(size_t np) {
+  static int cap = 0;
+  if (!cap) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<real, D>, 256, 0) == cudaSuccess &&
+        sms > 0 && per_sm > 0) {
+      cap = sms * per_sm;
+    } else {
+      cudaGetLastError();
+      cap = 152 * 4;
+    }
+  }
+  size_t b = (np / 4 + 255) / 256;
+  if (b > (size_t)cap) b = (size_t)cap;
+  if (b == 0) b = 1;
+  return (int)b;
+}
+
 template <typename real, int D>
 int launch_push(const PArrays<real, D>& p, size_t np, int n, const real* Ecomb, PushParams<real> pp,
                 double* ke_partials, unsigned* status, const SortFuse& sf, cudaStream_t s) {
-  int blocks = push_blocks(np);
+  int blocks = push_blocks<real, D>(np);
   if (sf.keys)  // sort steps: memsets precede the push
     k_push<real, D><<<blocks, 256, 0, s>>>(p, np, n, Ecomb, pp, ke_partials, status, sf);
   else
@@ -283,7 +300,8 @@ int launch_push(const PArrays<real, D>& p, size_t np, int n, const real* Ecomb, 
 
 #define SG_INST_PUSH(real, D)                                                                           \
   template int launch_push<real, D>(const PArrays<real, D>&, size_t, int, const real*, PushParams<real>, \
-                                    double*, unsigned*, const SortFuse&, cudaStream_t);
+                                    double*, unsigned*, const SortFuse&, cudaStream_t);                  \
+  template int push_blocks<real, D>(size_t);
 SG_INST_PUSH(float, 2)
 SG_INST_PUSH(float, 3)
 SG_INST_PUSH(double, 2)
