@@ -245,6 +245,23 @@ const char* sg_strerror(int status);
 const char* sg_last_error(void);
 const char* sg_version(void);
 
+/* ---- host-only helpers (no GPU and no CUDA call) --------------------------
+ * sg_combination_grids: the component grids of the truncated combination
+ * technique (Section 4.2) for dim in {2, 3}, level n and truncation tau:
+ * every level vector l with tau <= l_m <= n and |l|_1 = n + (dim-1) tau - q,
+ * coefficient (-1)^q C(dim-1, q), q = 0..dim-1, in the order the library
+ * uses (q ascending, then lexicographic with the last axis fastest).
+ * *count receives the number of grids.  With levels and coeffs non-NULL and
+ * cap >= *count, levels[3 i + m] receives l_m of grid i (0 for m >= dim) and
+ * coeffs[i] its coefficient.  SG_ERR_INVALID for dim outside {2, 3}, n < 1,
+ * tau outside [1, n] or a NULL count; SG_ERR_SIZE when cap is too small
+ * (*count is still written). */
+int sg_combination_grids(int dim, int n, int tau, int* levels, int* coeffs, int cap, int* count);
+/* sg_estimate_footprint: the device bytes a run of these sizes allocates, as
+ * the serving layer's admission control estimates them (an upper estimate).
+ * SG_ERR_INVALID for a bad precision, dim, n or tau, or a NULL bytes. */
+int sg_estimate_footprint(int precision, int dim, int n, int tau, size_t n_particles, size_t* bytes);
+
 /* ---- cell-key sort as a stand-alone operation ----------------------------
  * sg_cell_sort: keys (Morton order of floor(u_m 2^level)), a stable sort
  * permutation and per-cell counts of n positions u (device pointers,

@@ -93,6 +93,8 @@ SIGNATURES = {
     "sg_pic_kernel_launches": (C.c_int, [_P, C.POINTER(C.c_ulonglong)]),
     "sg_pic_set_profiling": (C.c_int, [_P, C.c_int]),
     "sg_pic_set_solve_variant": (C.c_int, [_P, C.c_int]),
+    "sg_combination_grids": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, C.c_int, _P]),
+    "sg_estimate_footprint": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_size_t, _P]),
     "sg_pic_stage_times": (C.c_int, [_P, _P, C.c_int]),
     "sg_pic_destroy": (None, [_P]),
     "sg_strerror": (C.c_char_p, [C.c_int]),

@@ -36,6 +36,33 @@ extern "C" {
 
 const char* sg_version(void) { return "sgpic-gb300 1.0 (sm_103a)"; }
 
+int sg_combination_grids(int dim, int n, int tau, int* levels, int* coeffs, int cap, int* count) {
+  if (!count) return invalid("sg_combination_grids: count is NULL");
+  if ((dim != 2 && dim != 3) || n < 1 || tau < 1 || tau > n || dim * n > 30)
+    return invalid("sg_combination_grids: need dim in {2, 3} and 1 <= tau <= n");
+  const std::vector<GridSpec> g = combination_grids(dim, n, tau);
+  *count = (int)g.size();
+  if (!levels || !coeffs) return SG_OK;
+  if (cap < (int)g.size()) {
+    set_error("sg_combination_grids: capacity below the grid count");
+    return SG_ERR_SIZE;
+  }
+  for (size_t i = 0; i < g.size(); ++i) {
+    for (int m = 0; m < 3; ++m) levels[3 * i + m] = m < dim ? g[i].l[m] : 0;
+    coeffs[i] = g[i].coeff;
+  }
+  return SG_OK;
+}
+
+int sg_estimate_footprint(int precision, int dim, int n, int tau, size_t n_particles, size_t* bytes) {
+  if (!bytes) return invalid("sg_estimate_footprint: bytes is NULL");
+  if ((precision != SG_FP32 && precision != SG_FP64) || (dim != 2 && dim != 3) || n < 2 || dim * n > 24 ||
+      tau < 1 || tau > n)
+    return invalid("sg_estimate_footprint: bad precision, dim, level or tau");
+  *bytes = estimate_footprint(precision, dim, n, tau, n_particles);
+  return SG_OK;
+}
+
 const char* sg_strerror(int status) {
   switch (status) {
     case SG_OK: return "ok";

@@ -120,6 +120,25 @@ def sg_version():
     return lib().sg_version().decode()
 
 
+def sg_combination_grids(dim, n, tau):
+    """The library's grid set (host only): list of (levels tuple, coefficient)."""
+    cnt = C.c_int()
+    check(lib().sg_combination_grids(dim, n, tau, None, None, 0, C.byref(cnt)), "sg_combination_grids")
+    levels = np.zeros(3 * cnt.value, dtype=np.int32)
+    coeffs = np.zeros(cnt.value, dtype=np.int32)
+    check(lib().sg_combination_grids(dim, n, tau, levels.ctypes.data, coeffs.ctypes.data, cnt.value,
+                                     C.byref(cnt)), "sg_combination_grids")
+    return [(tuple(int(x) for x in levels[3 * i:3 * i + dim]), int(coeffs[i])) for i in range(cnt.value)]
+
+
+def sg_estimate_footprint(precision, dim, n, tau, n_particles):
+    """Device bytes of a run of these sizes as the serving layer estimates them (host only)."""
+    b = C.c_size_t()
+    prec = L.SG_FP32 if precision in ("fp32", L.SG_FP32) else L.SG_FP64
+    check(lib().sg_estimate_footprint(prec, dim, n, tau, int(n_particles), C.byref(b)), "sg_estimate_footprint")
+    return int(b.value)
+
+
 def sg_cell_sort(u_cols, level, precision=L.SG_FP32, stream=None):
     """Stand-alone cell-key sort of torch CUDA position columns.  Returns
     (sorted keys, permutation, counts) as torch uint32-in-int32 tensors."""
