@@ -1,0 +1,85 @@
+"""The identities the GPU's cell-centred transfer kernels rest on, checked on
+the CPU against the oracle's dense cell-centred matrices (eq. restriction
+between cell centres):
+
+* restriction: R_l = FW_odd o FW^(n-l-1) o A, with A the average onto the
+  faces a[t] = (x[t-1] + x[t]) / 2, FW full weighting at the even nodes and
+  FW_odd full weighting evaluated at the odd nodes (R_n = identity);
+* prolongation: linear interpolation through the level-l centres is the
+  node-centred interpolant of the level-(l+1) line whose odd nodes hold the
+  centre values and whose even nodes hold the midpoints, sampled at the
+  regular centres, the midpoints of the level-n nodes.
+
+These restate the kernels' arithmetic in numpy; the GPU parity tests check
+the kernels themselves."""
+import numpy as np
+import pytest
+
+from oracle import sgpic_oracle as O
+
+
+def full_weighting_even(a):
+    return 0.25 * np.roll(a, 1)[::2] + 0.5 * a[::2] + 0.25 * np.roll(a, -1)[::2]
+
+
+def full_weighting_odd(a):
+    return 0.25 * a[::2] + 0.5 * a[1::2] + 0.25 * np.roll(a, -2)[::2]
+
+
+def cascade_restrict(x, n, lev):
+    if lev == n:
+        return x.copy()
+    a = 0.5 * (np.roll(x, 1) + x)
+    for _ in range(n - lev - 1):
+        a = full_weighting_even(a)
+    return full_weighting_odd(a)
+
+
+def node_prolong_step(t):
+    """Node-centred linear interpolation to the next finer level (periodic)."""
+    out = np.empty(2 * t.size)
+    out[::2] = t
+    out[1::2] = 0.5 * (t + np.roll(t, -1))
+    return out
+
+
+def embed(E):
+    """Centre values at the odd level-(l+1) nodes, midpoints at the even ones."""
+    g = np.empty(2 * E.size)
+    g[1::2] = E
+    g[::2] = 0.5 * (np.roll(E, 1) + E)
+    return g
+
+
+def horner_cell_combination(fields, n):
+    """sum_l c_l P_l E_l on the regular centres the way the combination kernel
+    evaluates it: Horner over the node-centred levels with every grid entering
+    one level higher, a final half step, then the level-n grids."""
+    T = np.zeros(1)  # level 0: one node
+    for L in range(1, n + 1):
+        T = node_prolong_step(T)
+        for lev, c, E in fields:
+            if lev == L - 1:
+                T = T + c * embed(E)
+    out = 0.5 * (T + np.roll(T, -1))
+    for lev, c, E in fields:
+        if lev == n:
+            out = out + c * E
+    return out
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 7])
+def test_cell_restriction_cascade_equals_matrix(n):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(2 ** n)
+    for lev in range(1, n + 1):
+        ref = O.restriction_matrix_1d(n, lev, "cell") @ x
+        np.testing.assert_allclose(cascade_restrict(x, n, lev), ref, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [2, 4, 6])
+def test_cell_prolongation_horner_equals_matrix(n):
+    rng = np.random.default_rng(10 + n)
+    fields = [(lev, float(rng.choice([-2.0, -1.0, 1.0])), rng.standard_normal(2 ** lev)) for lev in range(1, n + 1)]
+    ref = sum(c * (O.prolongation_matrix_1d(n, lev, "cell") @ E) for lev, c, E in fields)
+    np.testing.assert_allclose(horner_cell_combination(fields, n), ref, rtol=0, atol=1e-12)
