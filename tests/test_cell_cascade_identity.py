@@ -83,3 +83,32 @@ def test_cell_prolongation_horner_equals_matrix(n):
     fields = [(lev, float(rng.choice([-2.0, -1.0, 1.0])), rng.standard_normal(2 ** lev)) for lev in range(1, n + 1)]
     ref = sum(c * (O.prolongation_matrix_1d(n, lev, "cell") @ E) for lev, c, E in fields)
     np.testing.assert_allclose(horner_cell_combination(fields, n), ref, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [2, 4, 7])
+def test_node_restriction_cascade_equals_matrix(n):
+    """Node-centred: R_l is full weighting applied n - l times (the coarse hat
+    is linear between fine nodes, Appendix A)."""
+    rng = np.random.default_rng(20 + n)
+    x = rng.standard_normal(2 ** n)
+    for lev in range(1, n + 1):
+        a = x.copy()
+        for _ in range(n - lev):
+            a = full_weighting_even(a)
+        np.testing.assert_allclose(a, O.restriction_matrix_1d(n, lev) @ x, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [2, 5])
+def test_node_prolongation_horner_equals_matrix(n):
+    """Node-centred: sum_l c_l P_l E_l by Horner's scheme (prolong one level,
+    add the grids of that level)."""
+    rng = np.random.default_rng(30 + n)
+    fields = [(lev, float(rng.choice([-1.0, 1.0])), rng.standard_normal(2 ** lev)) for lev in range(1, n + 1)]
+    T = np.zeros(1)
+    for L in range(1, n + 1):
+        T = node_prolong_step(T)
+        for lev, c, E in fields:
+            if lev == L:
+                T = T + c * E
+    ref = sum(c * (O.prolongation_matrix_1d(n, lev) @ E) for lev, c, E in fields)
+    np.testing.assert_allclose(T, ref, rtol=0, atol=1e-12)
