@@ -14,6 +14,9 @@
  *   -> signed combination of the component fields on the regular nodes
  *      (eq. sparse_filter applied to the fields, coefficients of Section 4.2)
  *   -> CIC gather and leapfrog / Boris push (Section 2, steps 3-4).
+ * sg_params.mode selects the paper's filter mode instead (eq. sparse_filter,
+ * Algorithm 2): the regular-grid density is filtered by the same
+ * combination and solved once on the regular grid.
  *
  * Conventions shared by every call:
  *   - Every function returns an int status: SG_OK (0) or a negative SG_ERR_*
@@ -23,7 +26,9 @@
  *   - Geometry: periodic box [0, L_1) x ... x [0, L_d), d in {2, 3}.  Particle
  *     positions are passed as fractions of the box, u_m = x_m / L_m (values
  *     outside [0, 1) are wrapped periodically).  Velocities are physical.
- *     Grids are node-centred: node k of a level-l axis is at x = k L / 2^l.
+ *     Grids are node-centred by default (node k of a level-l axis at
+ *     x = k L / 2^l) or cell-centred (x = (k + 1/2) L / 2^l, sg_params.centring);
+ *     "regular nodes" below are the level-n nodes in either case.
  *   - Grid arrays are flat, x fastest: index = i_1 + 2^l_1 (i_2 + 2^l_2 i_3).
  *   - Particle arrays are structure-of-arrays in the run's precision
  *     (float for SG_FP32, double for SG_FP64).
