@@ -83,7 +83,8 @@ def combination_grids(d: int, n: int, tau: int):
 
 def wrap_unit(u):
     """Map fractional positions into [0, 1): u - floor(u), and 1.0 -> 0.0
-    (the subtraction can round up to exactly 1 for tiny negative u)."""
+    (the subtraction can round up to exactly 1 for tiny negative u).  The
+    periodic box of Section 5's test cases."""
     u = np.asarray(u, dtype=np.float64)
     w = u - np.floor(u)
     w[w >= 1.0] = 0.0
@@ -91,7 +92,8 @@ def wrap_unit(u):
 
 
 def cell_index(u, n):
-    """Cell index floor(u_m 2^n) of every particle along every axis (N_p x d)."""
+    """Cell index floor(u_m 2^n) of every particle along every axis (N_p x d):
+    the level-n cell that holds it (regular grid of Section 4.1)."""
     u = np.asarray(u, dtype=np.float64)
     return np.floor(u * float(2 ** n)).astype(np.int64)
 
@@ -100,7 +102,9 @@ def cell_keys(u, n):
     """Morton (Z-order) key of each particle's level-n cell.
 
     Bit b of the cell index along axis m goes to key bit b*d + m (x is the
-    lowest bit).  Written as the plain bit loop."""
+    lowest bit).  Written as the plain bit loop.  The paper has no sort;
+    this is the reference for the GPU path's cell-key sort, which orders
+    particles by cell for the deposit."""
     idx = cell_index(u, n)
     d = idx.shape[1]
     key = np.zeros(idx.shape[0], dtype=np.int64)
@@ -112,7 +116,8 @@ def cell_keys(u, n):
 
 def sort_by_key(keys, n, d):
     """Stable counting sort by cell key: returns (permutation, sorted keys,
-    counts per cell).  Ties keep their previous order."""
+    counts per cell).  Ties keep their previous order.  (No paper
+    counterpart: the reference of the GPU path's stand-alone sort.)"""
     keys = np.asarray(keys, dtype=np.int64)
     perm = np.argsort(keys, kind="stable")
     counts = np.bincount(keys, minlength=2 ** (n * d)).astype(np.uint32)
@@ -120,7 +125,9 @@ def sort_by_key(keys, n, d):
 
 
 def count_checksum(counts):
-    """sum_k (k + 1) * count[k] modulo 2^64 (= sum over particles of key+1)."""
+    """sum_k (k + 1) * count[k] modulo 2^64 (= sum over particles of key+1):
+    an order-free integer fingerprint of the cell occupation (no paper
+    counterpart; a diagnostic of the GPU path)."""
     c = np.asarray(counts, dtype=np.uint64)
     k = np.arange(1, c.size + 1, dtype=np.uint64)
     return int(np.sum(c * k, dtype=np.uint64))
@@ -163,6 +170,8 @@ def _cic_corners(u, l, centring="node"):
 
 
 def cell_volume(l, L):
+    """V_i = prod_m L_m / 2^(l_m), the cell volume of component grid l
+    (eq. restriction)."""
     return float(np.prod([L[m] / 2 ** l[m] for m in range(len(l))]))
 
 
@@ -269,7 +278,8 @@ def prolong_at(field, n, l, idx, centring="node"):
 
 
 def wavenumbers(N, Lm):
-    """k_m = 2 pi m / L for the DFT frequencies m in [-N/2, N/2-1]."""
+    """k_m = 2 pi m / L for the DFT frequencies m in [-N/2, N/2-1] (the
+    spectral solve of the Poisson problem of Section 2)."""
     return 2.0 * np.pi * np.fft.fftfreq(N, d=Lm / N)
 
 
@@ -303,7 +313,8 @@ def solve_poisson_spectral(rho, L):
 
 
 def potential_spectral(rho, L):
-    """phi with -Laplace phi = rho (k = 0 mode zero); used by the pins."""
+    """phi with -Laplace phi = rho (k = 0 mode zero), Section 2; used by the
+    pins."""
     rho = np.asarray(rho, dtype=np.float64)
     d = rho.ndim
     rh = np.fft.fftn(rho)
@@ -321,7 +332,9 @@ def potential_spectral(rho, L):
 
 
 def gather_cic(field, u, l, centring="node"):
-    """CIC interpolation of a level-l nodal field to the particles."""
+    """CIC interpolation of a level-l nodal field to the particles: the
+    field at the particles with the deposit's shape W (Section 2, the
+    interpolation step; eq. restriction's hat function)."""
     out = np.zeros(np.asarray(u).shape[0], dtype=np.float64)
     for idx, w in _cic_corners(u, l, centring):
         out += w * field[idx]
@@ -330,7 +343,8 @@ def gather_cic(field, u, l, centring="node"):
 
 def regular_node_positions(n, d, centring="node"):
     """Fractional positions (j + o) / 2^n of all level-n nodes, in array
-    order (o = 0 node-centred, 1/2 cell-centred)."""
+    order (o = 0 node-centred, 1/2 cell-centred): the regular grid of
+    Section 4.1."""
     N = 2 ** n
     o = _node_offset(centring)
     axes = np.meshgrid(*[(np.arange(N) + o) / N for _ in range(d)], indexing="ij")
@@ -353,8 +367,9 @@ def external_field(u, L, eext_lin):
 def kick_rotate(v, E, qm, dt, B):
     """Velocity update over dt: half electric kick, magnetic rotation, half
     kick (Boris).  With B = 0 this is the plain leapfrog kick
-    v + (q/m) E dt.  ``v`` and ``E`` are lists of d arrays; in 2D only B_z
-    acts (in-plane velocities)."""
+    v + (q/m) E dt (Section 2, the push; the magnetised cases of Sections
+    5.1-5.2 need the rotation).  ``v`` and ``E`` are lists of d arrays; in 2D
+    only B_z acts (in-plane velocities)."""
     d = len(v)
     vm = [v[m] + qm * E[m] * (0.5 * dt) for m in range(d)]
     if d == 2:
@@ -383,7 +398,8 @@ def kick_rotate(v, E, qm, dt, B):
 
 
 def drift(u, v, dt, L):
-    """x^{n+1} = x^n + v^{n+1/2} dt, in fractional coordinates, wrapped."""
+    """x^{n+1} = x^n + v^{n+1/2} dt, in fractional coordinates, wrapped into
+    the periodic box (Section 2, the push)."""
     u = np.asarray(u, dtype=np.float64)
     out = np.empty_like(u)
     for m in range(u.shape[1]):
@@ -511,6 +527,9 @@ class OracleRun:
         self.v = kick_rotate(self.v, E, self.qm, -0.5 * self.dt, self.B)
 
     def _fields(self):
+        """The field evaluation of one step: Algorithm 1 first when tau is
+        adaptive, then the component fields (Section 4.1) or the filter
+        mode's regular-grid field (Algorithm 2)."""
         if self.adaptive:
             rho = deposit_cic(self.u, self.q, (self.n,) * self.d, self.L, self.centring)
             self.tau = tau_estimator(rho, len(self.q), self.L[0], self.alpha, self.pc_ref,
@@ -545,6 +564,8 @@ class OracleRun:
         return 0.5 * hd * float(sum(np.sum(e * e) for e in Ec))
 
     def step(self, nsteps=1):
+        """Leapfrog steps (Section 2): kick with the current field, drift,
+        new field; the kinetic energy is time-centred over the kick."""
         for _ in range(nsteps):
             E = self.field_at(self.u)
             vnew = kick_rotate(self.v, E, self.qm, self.dt, self.B)
@@ -557,9 +578,13 @@ class OracleRun:
             self.step_count += 1
 
     def grid_charges(self):
+        """V_i sum_k rho_i(x_k) per component grid: the charge each grid holds
+        (the deposit's partition of unity keeps it equal to sum_p q_p)."""
         return [float(np.sum(rho)) * cell_volume(l, self.L) for l, _, rho, _ in self.comps]
 
     def diagnostics(self):
+        """Charges per grid and combined (coefficients of Section 4.2), field
+        and kinetic energies, tau, and the cell-occupation checksum."""
         qsum = float(np.sum(self.q))
         ch = self.grid_charges()
         coeffs = [c for _, c, _, _ in self.comps]
@@ -579,6 +604,7 @@ class OracleRun:
         }
 
     def velocities(self):
+        """v^{n-1/2} as an (N_p, d) array."""
         return np.stack(self.v, axis=1)
 
 
