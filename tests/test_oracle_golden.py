@@ -52,3 +52,25 @@ def test_tau_range_printed():
     for n in range(4, 12):
         assert O.tau_range(2, n)[-1] == n - 3
         assert O.tau_range(3, n)[-1] == n - 2
+
+
+def test_penning_workload_matches_printed_parameters():
+    """The Penning-trap inputs (box, fields, charge, time step, the moments
+    of the Gaussian bunch) against the values Section 5.2 prints."""
+    import os
+    from paper_2008_09441_gb300 import workloads
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "penning_trap_parameters.json")))
+    wl = workloads.penning3d(n_particles=200000, n=6, seed=7)
+    L = g["L"]["value"]
+    assert wl.L == (L, L, L)
+    assert list(wl.B) == g["B_ext"]["value"]
+    assert np.allclose(wl.eext_lin, np.array(g["E_ext_linear"]["value"]) / L, rtol=0, atol=1e-15)
+    assert wl.dt == g["dt"]["value"]
+    assert abs(wl.q.sum() - g["Q_e"]["value"]) < 1e-9 and np.all(wl.q == wl.q[0])
+    v = wl.v
+    assert np.all(np.abs(v.mean(axis=0)) < 0.01) and np.all(np.abs(v.std(axis=0) - 1.0) < 0.01)
+    # positions about the centre in units of L (the tails that wrap around the
+    # box, beyond 2.5 standard deviations in z, change the moments by < 2%)
+    x = wl.u - 0.5
+    assert np.all(np.abs(x.mean(axis=0)) < 0.002)
+    assert np.allclose(x.std(axis=0), g["position"]["std_over_L"], rtol=0.02, atol=0)
