@@ -58,3 +58,21 @@ def test_fp32_cell_frac_gives_exact_cic_weights(n, shift):
     # off the ties (and off the tiny-negative case) the cell is the floor itself
     off = (ref_f > 0) & ~neg
     assert np.array_equal(c[off] % N, ref_c[off] % N)
+
+
+def test_fixed_point_quantisation_is_round_to_nearest_even():
+    """The deposit window's FP32 fixed point: bits(fma(a, b, 1.5 2^23)) -
+    bits(1.5 2^23) is the integer nearest a*b (ties to even) for |a*b| < 2^22,
+    since the sum lands in [2^23, 2^24) where floats are spaced by 1.  fma
+    rounds once: emulated as one rounding of the exact double a*b + 1.5 2^23."""
+    rng = np.random.default_rng(3)
+    a = (rng.standard_normal(200000) * 3e4).astype(np.float32)
+    b = rng.random(200000).astype(np.float32)
+    ties = np.array([0.5, 1.5, 2.5, -0.5, -1.5, -2.5, 2.0 ** 21 + 0.5, -(2.0 ** 21) - 0.5], dtype=np.float32)
+    a = np.concatenate([a, ties])
+    b = np.concatenate([b, np.ones(ties.size, dtype=np.float32)])
+    exact = a.astype(np.float64) * b.astype(np.float64)
+    assert np.all(np.abs(exact) < 2.0 ** 22)
+    t = (exact + 12582912.0).astype(np.float32)  # the single rounding of fmaf
+    q = t.view(np.int32).astype(np.int64) - 0x4B400000
+    np.testing.assert_array_equal(q, np.rint(exact).astype(np.int64))  # rint: ties to even
