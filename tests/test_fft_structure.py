@@ -1,0 +1,78 @@
+"""The component and regular-grid transforms' structure, restated in numpy
+(CPU only): input in bit-reversed order, decimation-in-time stages taken in
+pairs (radix 2^2: four elements i, i+h, i+2h, i+3h, the butterflies of stage
+s with span 2h and of stage s+1 with span 4h) with an odd last stage as a
+plain radix-2 pass, twiddles tw[k] = exp(-2 pi i k / 2^nmax) indexed
+pos << (nmax - s); the inverse conjugates them.  Checked against numpy.fft.
+Also the pairing of two real field components in one inverse transform."""
+import numpy as np
+import pytest
+
+
+def bitrev(t, logn):
+    return int(format(t, f"0{logn}b")[::-1], 2) if logn else 0
+
+
+def fft_pairs(x, logn, log_nmax, inverse=False):
+    n = 1 << logn
+    tw = np.exp(-2j * np.pi * np.arange(1 << (log_nmax - 1)) / (1 << log_nmax))
+    if inverse:
+        tw = np.conj(tw)
+    buf = np.empty(n, dtype=complex)
+    for t in range(n):
+        buf[bitrev(t, logn)] = x[t]
+    s0 = 1
+    while s0 + 1 <= logn:
+        h = 1 << (s0 - 1)
+        t1, t2 = log_nmax - s0, log_nmax - s0 - 1
+        for jj in range(n >> 2):
+            pos = jj & (h - 1)
+            grp = jj >> (s0 - 1)
+            i0 = grp * 4 * h + pos
+            w1, w2, w3 = tw[pos << t1], tw[pos << t2], tw[(pos + h) << t2]
+            a0, a1, a2, a3 = buf[i0], buf[i0 + h], buf[i0 + 2 * h], buf[i0 + 3 * h]
+            m1, m3 = a1 * w1, a3 * w1
+            b0, b1, b2, b3 = a0 + m1, a0 - m1, a2 + m3, a2 - m3
+            n2, n3 = b2 * w2, b3 * w3
+            buf[i0], buf[i0 + 2 * h] = b0 + n2, b0 - n2
+            buf[i0 + h], buf[i0 + 3 * h] = b1 + n3, b1 - n3
+        s0 += 2
+    for s in range(s0, logn + 1):
+        half = 1 << (s - 1)
+        for jj in range(n >> 1):
+            pos = jj & (half - 1)
+            grp = jj >> (s - 1)
+            i0 = grp * 2 * half + pos
+            w = tw[pos << (log_nmax - s)]
+            a, b = buf[i0], buf[i0 + half] * w
+            buf[i0], buf[i0 + half] = a + b, a - b
+    return buf
+
+
+@pytest.mark.parametrize("logn,log_nmax", [(1, 1), (2, 4), (3, 3), (5, 7), (6, 6), (7, 10)])
+def test_radix4_pairs_equal_numpy(logn, log_nmax):
+    rng = np.random.default_rng(logn + 10 * log_nmax)
+    x = rng.standard_normal(1 << logn) + 1j * rng.standard_normal(1 << logn)
+    np.testing.assert_allclose(fft_pairs(x, logn, log_nmax), np.fft.fft(x), rtol=0, atol=1e-11)
+    np.testing.assert_allclose(fft_pairs(x, logn, log_nmax, inverse=True), np.fft.ifft(x) * x.size, rtol=0,
+                               atol=1e-11)
+
+
+def test_two_real_components_share_one_inverse():
+    """F^-1(E^_a + i E^_b) has E_a as its real and E_b as its imaginary part
+    when both spectra are those of real fields, Nyquist planes zeroed."""
+    rng = np.random.default_rng(5)
+    rho = rng.standard_normal((16, 32))
+    rh = np.fft.fft2(rho)
+    kx = 2 * np.pi * np.fft.fftfreq(16, d=1 / 16)
+    ky = 2 * np.pi * np.fft.fftfreq(32, d=1 / 32)
+    KX, KY = np.meshgrid(kx, ky, indexing="ij")
+    k2 = KX ** 2 + KY ** 2
+    phi = np.where(k2 > 0, rh / np.where(k2 > 0, k2, 1), 0)
+    KXn = np.where(np.arange(16)[:, None] == 8, 0.0, KX)
+    KYn = np.where(np.arange(32)[None, :] == 16, 0.0, KY)
+    Ea, Eb = -1j * KXn * phi, -1j * KYn * phi
+    both = np.fft.ifft2(Ea + 1j * Eb)
+    np.testing.assert_allclose(both.real, np.real(np.fft.ifft2(Ea)), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(both.imag, np.real(np.fft.ifft2(Eb)), rtol=0, atol=1e-12)
+    assert np.max(np.abs(np.imag(np.fft.ifft2(Ea)))) < 1e-12  # each alone is real
