@@ -494,3 +494,16 @@ def test_filter_mode_run_tau_n_equals_regular_pic():
     b.step(3)
     assert np.max(np.abs(a.u - b.u)) < 1e-12
     assert abs(a.field_energy() - b.field_energy()) < 1e-12 * a.field_energy()
+
+
+@pytest.mark.parametrize("d,n", [(2, 10), (3, 7)])
+def test_morton_key_prefix_is_coarse_cell_key(d, n):
+    """The step sort orders by tile key, the level-n key shifted right by
+    d s bits: that is the Morton key of the level-(n - s) cell (the key's
+    high bits interleave the cell index's high bits), so tiles are compact
+    blocks of 2^s cells per axis."""
+    rng = np.random.default_rng(77 + d)
+    u = rng.random((5000, d))
+    k = O.cell_keys(u, n).astype(np.int64)
+    for s in range(0, n):
+        np.testing.assert_array_equal(k >> (d * s), O.cell_keys(u, n - s).astype(np.int64))
