@@ -112,3 +112,31 @@ def test_node_prolongation_horner_equals_matrix(n):
                 T = T + c * E
     ref = sum(c * (O.prolongation_matrix_1d(n, lev) @ E) for lev, c, E in fields)
     np.testing.assert_allclose(T, ref, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("centring", ["node", "cell"])
+def test_transverse_bracket_equals_prolongation_rows(centring):
+    """The combination's transverse interpolation (the kernels' integer
+    bracket): node-centred k0 = y >> r, f = (y mod 2^r) / 2^r; cell-centred
+    num = 2y + 1 - 2^r, k0 = num >> (r + 1) (an arithmetic shift: floor,
+    -1 wraps), f = (num - k0 2^(r+1)) / 2^(r+1).  Weights 1 - f on k0 and f on
+    k0 + 1 (periodic) must be the rows of the oracle's P."""
+    for n in (3, 6):
+        for lev in range(1, n + 1):
+            P = O.prolongation_matrix_1d(n, lev, centring)
+            r = n - lev
+            nl = 1 << lev
+            for y in range(1 << n):
+                if centring == "node":
+                    k0 = y >> r
+                    f = (y & ((1 << r) - 1)) / (1 << r)
+                else:
+                    num = 2 * y + 1 - (1 << r)
+                    fl = num >> (r + 1)  # Python's >> floors negative numbers like the kernels' shift
+                    f = (num - fl * (2 << r)) / (2 << r)
+                    k0 = fl & (nl - 1)
+                k1 = (k0 + 1) & (nl - 1)
+                row = np.zeros(nl)
+                row[k0] += 1.0 - f
+                row[k1] += f
+                np.testing.assert_allclose(P[y], row, rtol=0, atol=1e-15)
