@@ -140,3 +140,27 @@ def test_transverse_bracket_equals_prolongation_rows(centring):
                 row[k0] += 1.0 - f
                 row[k1] += f
                 np.testing.assert_allclose(P[y], row, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("L", [6, 8, 10])
+def test_lane_chunks_of_the_cell_embedding(L):
+    """The combination kernel's per-lane form of the embedding at Horner level
+    L (2^L = 32 K values, lane j holding K of them from x0 = j K): the lane
+    reads its K/2 centre values from c0 = x0/2 and the one before,
+    cm = (c0 - 1) mod 2^(L-1), and writes g[x0 + 2i + 1] = E[c0 + i],
+    g[x0 + 2i] = (E[c0 + i - 1] + E[c0 + i]) / 2."""
+    rng = np.random.default_rng(L)
+    E = rng.standard_normal(1 << (L - 1))
+    K = (1 << L) // 32
+    H = K // 2
+    nc = 1 << (L - 1)
+    g = np.empty(1 << L)
+    for lane in range(32):
+        x0 = lane * K
+        c0 = x0 >> 1
+        cm = (c0 - 1) & (nc - 1)
+        t = np.concatenate([[E[cm]], E[c0:c0 + H]])
+        for i in range(H):
+            g[x0 + 2 * i + 1] = t[i + 1]
+            g[x0 + 2 * i] = 0.5 * (t[i] + t[i + 1])
+    np.testing.assert_array_equal(g, embed(E))
