@@ -50,7 +50,7 @@ extern "C" {
 /* ---- status codes ---------------------------------------------------- */
 #define SG_OK 0
 #define SG_ERR_INVALID (-1)     /* bad argument (NULL, out of range, non-finite input) */
-#define SG_ERR_UNSUPPORTED (-2) /* valid request this build does not implement */
+#define SG_ERR_UNSUPPORTED (-2) /* valid request the library does not implement */
 #define SG_ERR_OOM (-3)         /* device allocation failed */
 #define SG_ERR_SIZE (-4)        /* caller buffer too small / size mismatch */
 #define SG_ERR_TIMEOUT (-5)     /* a bounded wait expired */
