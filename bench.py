@@ -167,36 +167,104 @@ def algorithmic_bytes(np_, n, d, real_bytes=4):
     return {"deposit": dep, "push": push}
 
 
-def cpu_baseline(workload=WORKLOAD):
-    """cpu_baseline_sample in a child process with one BLAS thread."""
+# Oracle sample per workload: particles and the wall-time bound of the
+# CPU-baseline leg (the 3D oracle's regular-grid field alone is seconds).
+CPU_SAMPLE = {"landau2d_n10_fp32": (1 << 18, 10.0), "twostream3d_n7_fp32": (1 << 15, 10.0),
+              "diocotron2d_n9_fp32": (1 << 18, 10.0), "penning3d_n7_fp32": (1 << 15, 10.0)}
+
+
+def cpu_baseline(workload=WORKLOAD, state_path=None, mode="combine", centring="node"):
+    """cpu_baseline_sample in a child process with one BLAS thread.  With
+    state_path the child also saves the oracle's final state there (positions,
+    velocities, the field on the regular nodes), the reference of the
+    precision comparison."""
     env = dict(os.environ, **_SINGLE_THREAD_ENV)
-    code = f"import json, bench; print(json.dumps(bench.cpu_baseline_sample({workload!r})))"
+    sample, seconds = CPU_SAMPLE.get(workload, (1 << 16, 10.0))
+    code = (f"import json, bench; print(json.dumps(bench.cpu_baseline_sample({workload!r}, {sample}, {seconds}, "
+            f"state_path={state_path!r}, mode={mode!r}, centring={centring!r})))")
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
-                       timeout=600)
+                       timeout=900)
     if r.returncode != 0:
         raise RuntimeError("cpu baseline failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline_sample(workload=WORKLOAD, sample_particles=1 << 18, min_seconds=10.0, max_steps=50):
-    """The oracle as it stands on a bounded sample: steps of 2^18 particles
+def cpu_sample_workload(workload, sample_particles):
+    from paper_2008_09441_gb300 import workloads
+    return workloads.make(workload, n_particles=sample_particles)
+
+
+def cpu_baseline_sample(workload=WORKLOAD, sample_particles=1 << 18, min_seconds=10.0, max_steps=50,
+                        state_path=None, mode="combine", centring="node"):
+    """The oracle as it stands on a bounded sample: steps of the sample
     until about min_seconds of CPU work (at most max_steps)."""
     from oracle import sgpic_oracle as O
-    from paper_2008_09441_gb300 import workloads
-    wl = workloads.make(workload, n_particles=sample_particles)
+    wl = cpu_sample_workload(workload, sample_particles)
     u = wl.u.astype(np.float32).astype(np.float64)
     v = wl.v.astype(np.float32).astype(np.float64)
     q = wl.q.astype(np.float32).astype(np.float64)
-    run = O.OracleRun(wl.L, wl.n, u, v, q, wl.dt, qm=wl.qm, tau=wl.tau, B=wl.B, eext_lin=wl.eext_lin)
+    run = O.OracleRun(wl.L, wl.n, u, v, q, wl.dt, qm=wl.qm, tau=wl.tau, B=wl.B, eext_lin=wl.eext_lin, mode=mode,
+                      centring=centring)
     t0 = time.perf_counter()
     steps = 0
     while steps < max_steps and (steps == 0 or time.perf_counter() - t0 < min_seconds):
         run.step(1)
         steps += 1
     dt = time.perf_counter() - t0
-    return {"value": sample_particles * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} step(s) of {sample_particles} particles of the {workload} workload "
-                      f"(n={wl.n}, tau={wl.tau}), FP64 numpy oracle, single thread, {dt:.1f} s"}
+    out = {"value": sample_particles * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{steps} step(s) of {sample_particles} particles of the {workload} workload "
+                     f"(n={wl.n}, tau={wl.tau}, {mode} mode, {centring}-centred), FP64 numpy oracle, single "
+                     f"thread, {dt:.1f} s",
+           "steps": steps, "particles": sample_particles}
+    if state_path:
+        diag = run.diagnostics()
+        E = run.regular_field()
+        np.savez(state_path, u=run.u, v=run.velocities(), E=np.stack(E),
+                 diag=np.array([diag["field_energy"], diag["kinetic_energy"], diag["charge_combined"],
+                                diag["charge_total"]]))
+    return out
+
+
+def precision_vs_oracle(wname, cpu, state_path, stream, dev, mode="combine", centring="node"):
+    """The FP32 GPU path on the CPU-baseline sample, advanced the same number
+    of steps as the oracle there, against the oracle's final state: NRMSE
+    (eq. error_def) of the positions (periodic difference), the velocities
+    and the combined field on the regular nodes, and the relative error of
+    the field energy, the kinetic energy and the combined charge; once with
+    each accumulation of the combination."""
+    import torch
+    from paper_2008_09441_gb300 import Run
+    ref = np.load(state_path)
+    wl = cpu_sample_workload(wname, cpu["particles"])
+    steps = cpu["steps"]
+    d = wl.dim
+
+    def nrmse(a, b):
+        return float(np.sqrt(np.sum((np.asarray(a, np.float64) - b) ** 2) / np.sum(b * b)))
+
+    out = {"reference": "FP64 oracle state at the end of the CPU-baseline sample", "steps": steps,
+           "particles": cpu["particles"]}
+    for acc in ("float-float", "fp64"):
+        u = torch.from_numpy(wl.u.astype(np.float32)).to(dev)
+        v = torch.from_numpy(wl.v.astype(np.float32)).to(dev)
+        q = torch.from_numpy(wl.q.astype(np.float32)).to(dev)
+        run = Run(wl.L, wl.n, u, v, q, wl.dt, tau=wl.tau, qm=wl.qm, B=wl.B, eext_lin=wl.eext_lin,
+                  precision="fp32", stream=stream.cuda_stream, combine=acc, mode=mode, centring=centring)
+        run.step(steps)
+        ug, vg, _ = run.particles()
+        E = run.field()
+        dg = run.diagnostics()
+        run.close()
+        du = ug.astype(np.float64) - ref["u"]
+        du -= np.round(du)
+        fe, ke, qc, qt = (float(x) for x in ref["diag"])
+        out[acc] = {"nrmse_u": float(np.sqrt(np.sum(du * du) / np.sum(ref["u"] ** 2))),
+                    "nrmse_v": nrmse(vg, ref["v"]),
+                    "nrmse_E": max(nrmse(E[m], ref["E"][m]) for m in range(d)),
+                    "relerr_field_energy": abs(dg["field_energy"] - fe) / abs(fe),
+                    "relerr_kinetic_energy": abs(dg["kinetic_energy"] - ke) / abs(ke),
+                    "relerr_charge": abs(dg["charge_combined"] - qc) / abs(qt)}
+    return out
 
 
 def run_reference(args, world, rank, pg):
@@ -306,6 +374,9 @@ def main():
                     help="component-grid solve: timed choice at init (default), or fixed; a profiler's "
                          "serialised launches distort the timed choice, so profile with the variant the "
                          "plain run chose")
+    ap.add_argument("--combine", default="float-float", choices=["float-float", "fp64"],
+                    help="accumulation of the signed combination on the FP32 path: float pairs (the default "
+                         "line) or double")
     ap.add_argument("--ref-particles", type=int, default=1 << 16)
     ap.add_argument("--ref-budget-s", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -347,7 +418,8 @@ def main():
     q = torch.from_numpy(wl.q.astype(np.float32)).to(dev)
     sort_every = args.sort_every if args.sort_every > 0 else 4  # the library default
     run = Run(wl.L, n, u, v, q, wl.dt, tau=wl.tau, qm=wl.qm, B=wl.B, eext_lin=wl.eext_lin, precision="fp32",
-              sort_every=sort_every, stream=stream.cuda_stream, mode=args.mode, centring=args.centring)
+              sort_every=sort_every, stream=stream.cuda_stream, mode=args.mode, centring=args.centring,
+              combine=args.combine)
     if args.solve_variant != "auto":
         run.set_solve_variant(args.solve_variant)
     run_grids = run.grids()
@@ -439,7 +511,8 @@ def main():
         import ctypes as C
         t0 = time.perf_counter()
         r2 = Run(wl.L, n, hu, hv, hq, wl.dt, tau=wl.tau, qm=wl.qm, B=wl.B, eext_lin=wl.eext_lin, precision="fp32",
-                 sort_every=sort_every, stream=stream.cuda_stream, mode=args.mode, centring=args.centring)
+                 sort_every=sort_every, stream=stream.cuda_stream, mode=args.mode, centring=args.centring,
+                 combine=args.combine)
         if args.solve_variant != "auto":
             r2.set_solve_variant(args.solve_variant)
         diag_bytes = 0
@@ -469,8 +542,13 @@ def main():
         run.close()
 
     cpu = None
+    precision = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wname)
+        import tempfile
+        with tempfile.TemporaryDirectory() as td:
+            state = os.path.join(td, "oracle_state.npz")
+            cpu = cpu_baseline(wname, state_path=state, mode=args.mode, centring=args.centring)
+            precision = precision_vs_oracle(wname, cpu, state, stream, dev, args.mode, args.centring)
 
     if rank == 0:
         srt = sorted(step_ms)
@@ -486,10 +564,12 @@ def main():
                           "mode": args.mode + (" (stage 'solve' = density filter, 'combine' = regular-grid solve)"
                                                if args.mode == "filter" else ""),
                           "centring": args.centring,
-                          "combine": "float-float (48-bit) accumulation, FP64 diagnostics",
+                          "combine": ("float-float (48-bit)" if args.combine == "float-float" else "FP64") +
+                                     " accumulation, FP64 diagnostics",
                           "parallelism": f"{world} independent replicas"},
                "latency_ms": {"p50": p50, "p99": p99},
-               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "roofline": roofline, "cpu_baseline": cpu, "precision": precision, "e2e": e2e,
+               "gpu_launches": launches,
                "clocks": clk, "wall_s_timed": wall}
         print(json.dumps(out))
         sys.stdout.flush()

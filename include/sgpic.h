@@ -69,6 +69,8 @@ extern "C" {
 #define SG_MODE_FILTER 1
 #define SG_NODE_CENTRED 0 /* node k of a level-l axis at x_k = k L / 2^l */
 #define SG_CELL_CENTRED 1 /* node k at the cell centre x_k = (k + 1/2) L / 2^l */
+#define SG_COMBINE_FLOAT_FLOAT 0 /* FP32 path: combination in float pairs (about 48 bits) */
+#define SG_COMBINE_FP64 1        /* FP32 path: combination accumulated in double */
 
 typedef struct sg_pic sg_pic; /* opaque run handle; owns all its device memory */
 
@@ -120,6 +122,16 @@ typedef struct {
                          Appendix A, and the gather through the same shape (P_i to
                          the regular grid, then CIC).  Any other value:
                          SG_ERR_INVALID. */
+  int combine;        /* accumulation of the signed combination of the component
+                         fields (Section 4.1, coefficients of Section 4.2) on the
+                         FP32 path: SG_COMBINE_FLOAT_FLOAT (0, default) sums every
+                         term with an error-free float addition whose error is
+                         carried in a second float; SG_COMBINE_FP64 (1) forms each
+                         term and the sum in double (slower on GB300, whose double
+                         rate is a small fraction of its float rate).  Either way
+                         the result is stored as hi + lo floats and the field
+                         energy is reduced in FP64.  The FP64 path always
+                         accumulates in double.  Any other value: SG_ERR_INVALID. */
 } sg_params;
 
 typedef struct {
@@ -297,8 +309,10 @@ int sg_cell_sort_static(int precision, int dim, int level, size_t n, const void*
 
 /* ---- serving: independent runs admitted as memory allows -----------------
  * A server keeps many independent runs resident on one GPU and advances all
- * of them together in batched launches (one launch per stage covers every
- * component grid of every resident run).  Requests are admitted in arrival
+ * of them together: in batched mode one CUDA graph per tick forks into one
+ * branch per resident run (each branch holds that run's own stage kernels,
+ * the branches overlap on the device), in plain mode the runs are stepped in
+ * turn with direct launches.  Requests are admitted in arrival
  * order while their estimated device footprint fits hbm_budget_bytes and a
  * slot is free; finished runs retire and free their memory. */
 typedef struct sg_server sg_server;

@@ -31,6 +31,7 @@ SG_REQ_QUEUED, SG_REQ_RUNNING, SG_REQ_DONE, SG_REQ_FAILED = 0, 1, 2, 3
 SG_SERVE_BATCHED, SG_SERVE_PLAIN = 0, 1
 SG_MODE_COMBINE, SG_MODE_FILTER = 0, 1
 SG_NODE_CENTRED, SG_CELL_CENTRED = 0, 1
+SG_COMBINE_FLOAT_FLOAT, SG_COMBINE_FP64 = 0, 1
 SG_SOLVE_AUTO, SG_SOLVE_PASSES, SG_SOLVE_ONE_BLOCK = -1, 0, 1
 
 
@@ -52,7 +53,7 @@ class sg_params(C.Structure):
     _fields_ = [("precision", C.c_int), ("tau", C.c_int), ("dt", C.c_double), ("qm", C.c_double),
                 ("B", C.c_double * 3), ("Eext_lin", C.c_double * 3), ("alpha", C.c_double),
                 ("pc_ref", C.c_double), ("tau_constants", C.c_int), ("sort_every", C.c_int),
-                ("stream", C.c_void_p), ("mode", C.c_int), ("centring", C.c_int)]
+                ("stream", C.c_void_p), ("mode", C.c_int), ("centring", C.c_int), ("combine", C.c_int)]
 
 
 class sg_diag(C.Structure):

@@ -138,6 +138,9 @@ int sg_pic_init(const sg_domain* domain, int level_n, int dim, int shape_order, 
   if (params->centring != SG_NODE_CENTRED && params->centring != SG_CELL_CENTRED)
     return invalid("sg_pic_init: centring must be SG_NODE_CENTRED or SG_CELL_CENTRED");
   cfg.cell = params->centring == SG_CELL_CENTRED;
+  if (params->combine != SG_COMBINE_FLOAT_FLOAT && params->combine != SG_COMBINE_FP64)
+    return invalid("sg_pic_init: combine must be SG_COMBINE_FLOAT_FLOAT or SG_COMBINE_FP64");
+  cfg.combine_fp64 = params->combine == SG_COMBINE_FP64;
 
   sg_pic* h = new (std::nothrow) sg_pic;
   if (!h) return SG_ERR_OOM;

@@ -36,6 +36,7 @@ template <typename real>
 struct CAcc;
 template <>
 struct CAcc<float> {
+  using term = float;  // type of one grid's interpolated, scaled term
   float hi, lo;
   static __device__ __forceinline__ CAcc zero() { return {0.f, 0.f}; }
   static __device__ __forceinline__ CAcc avg(const CAcc& a, const CAcc& b) {
@@ -58,6 +59,7 @@ struct CAcc<float> {
 };
 template <>
 struct CAcc<double> {
+  using term = double;
   double v;
   static __device__ __forceinline__ CAcc zero() { return {0.0}; }
   static __device__ __forceinline__ CAcc avg(const CAcc& a, const CAcc& b) { return {(a.v + b.v) * 0.5}; }
@@ -66,6 +68,33 @@ struct CAcc<double> {
   static __device__ __forceinline__ CAcc add_term(const CAcc& a, double t) { return {a.v + t}; }
   __device__ __forceinline__ CAcc shfl(int src) const { return {__shfl_sync(0xffffffffu, v, src)}; }
 };
+
+// FP32 fields combined with FP64 accumulation (sg_params.combine =
+// SG_COMBINE_FP64): each grid's term c_i w E_i is formed in double, which
+// is exact (c_i and the transverse weights w are dyadic, E_i a float), and
+// the alternating-sign sum and the Horner prolongation run in double.  The
+// result is split into hi + lo floats for the same output planes as the
+// float-float accumulator.  GB300 issues double arithmetic at a small
+// fraction of the float rate, so this variant is the slower one.
+struct CAccD {
+  using term = double;
+  double v;
+  static __device__ __forceinline__ CAccD zero() { return {0.0}; }
+  static __device__ __forceinline__ CAccD avg(const CAccD& a, const CAccD& b) { return {(a.v + b.v) * 0.5}; }
+  static __device__ __forceinline__ CAccD add(const CAccD& a, const CAccD& b) { return {a.v + b.v}; }
+  static __device__ __forceinline__ CAccD first(double t) { return {t}; }
+  static __device__ __forceinline__ CAccD add_term(const CAccD& a, double t) { return {a.v + t}; }
+  __device__ __forceinline__ CAccD shfl(int src) const { return {__shfl_sync(0xffffffffu, v, src)}; }
+  __device__ __forceinline__ ff normalised() const {
+    const float hi = (float)v;
+    return {hi, (float)(v - (double)hi)};
+  }
+};
+
+template <typename AC>
+constexpr bool kFp64Acc = false;
+template <>
+constexpr bool kFp64Acc<CAccD> = true;
 
 // Transverse interpolation weights and coarse-row offsets of one grid at
 // regular line (y, z): the 2^(d-1) coarse x-lines that bracket the line,
@@ -131,18 +160,19 @@ __device__ __forceinline__ RowTerm<real, D> row_term(const GridDesc& g, int n, i
 // multiples of 4), c_i times the transverse interpolation of every grid of
 // x level `level`; the grids' row terms come from this warp's shared-memory
 // table.  Grid by grid, all of a grid's loads first (one latency per grid).
-template <typename real, int D, int K>
-__device__ __forceinline__ void add_level_terms(CAcc<real>* T, const RowTerm<real, D>* rt_tab, const int* lstart,
+template <typename real, int D, int K, typename AC>
+__device__ __forceinline__ void add_level_terms(AC* T, const RowTerm<real, D>* rt_tab, const int* lstart,
                                                 int level, const real* __restrict__ Em, int x0) {
+  using TT = typename AC::term;
   constexpr int R = 1 << (D - 1);
   for (int gi = lstart[level]; gi < lstart[level + 1]; ++gi) {
     const RowTerm<real, D> rt = rt_tab[gi];
-    real t[K];
+    TT t[K];
 #pragma unroll
     for (int k = 0; k < K; k += 4) {
       const V4<real> a = ld4(Em + rt.off[0] + x0 + k);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) t[k + q] = rt.w[0] * a.x[q];
+      for (int q = 0; q < 4; ++q) t[k + q] = (TT)rt.w[0] * (TT)a.x[q];
     }
 #pragma unroll
     for (int r = 1; r < R; ++r) {
@@ -150,27 +180,28 @@ __device__ __forceinline__ void add_level_terms(CAcc<real>* T, const RowTerm<rea
       for (int k = 0; k < K; k += 4) {
         const V4<real> a = ld4(Em + rt.off[r] + x0 + k);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) t[k + q] = fma(rt.w[r], a.x[q], t[k + q]);
+        for (int q = 0; q < 4; ++q) t[k + q] = fma((TT)rt.w[r], (TT)a.x[q], t[k + q]);
       }
     }
 #pragma unroll
-    for (int k = 0; k < K; ++k) T[k] = CAcc<real>::add_term(T[k], t[k]);
+    for (int k = 0; k < K; ++k) T[k] = AC::add_term(T[k], t[k]);
   }
 }
 
 // The same at one x index (lines with fewer than 4 values per lane).
-template <typename real, int D>
-__device__ __forceinline__ CAcc<real> level_term1(const RowTerm<real, D>* rt_tab, const int* lstart, int level,
-                                                  const real* __restrict__ Em, int x) {
+template <typename real, int D, typename AC>
+__device__ __forceinline__ AC level_term1(const RowTerm<real, D>* rt_tab, const int* lstart, int level,
+                                          const real* __restrict__ Em, int x) {
+  using TT = typename AC::term;
   constexpr int R = 1 << (D - 1);
-  CAcc<real> acc = CAcc<real>::zero();
+  AC acc = AC::zero();
   bool first = true;
   for (int gi = lstart[level]; gi < lstart[level + 1]; ++gi) {
     const RowTerm<real, D> rt = rt_tab[gi];
-    real t = rt.w[0] * Em[rt.off[0] + x];
+    TT t = (TT)rt.w[0] * (TT)Em[rt.off[0] + x];
 #pragma unroll
-    for (int r = 1; r < R; ++r) t = fma(rt.w[r], Em[rt.off[r] + x], t);
-    acc = first ? CAcc<real>::first(t) : CAcc<real>::add_term(acc, t);
+    for (int r = 1; r < R; ++r) t = fma((TT)rt.w[r], (TT)Em[rt.off[r] + x], t);
+    acc = first ? AC::first(t) : AC::add_term(acc, t);
     first = false;
   }
   return acc;
@@ -186,84 +217,87 @@ __device__ __forceinline__ CAcc<real> level_term1(const RowTerm<real, D>* rt_tab
 // at their own centres.
 
 // g of the grids of x level `level - 1` at Horner level `level`, index t.
-template <typename real, int D>
-__device__ __forceinline__ CAcc<real> cell_term1(const RowTerm<real, D>* rt_tab, const int* lstart, int level,
-                                                 const real* __restrict__ Em, int t) {
-  if (level < 1) return CAcc<real>::zero();
+template <typename real, int D, typename AC>
+__device__ __forceinline__ AC cell_term1(const RowTerm<real, D>* rt_tab, const int* lstart, int level,
+                                         const real* __restrict__ Em, int t) {
+  if (level < 1) return AC::zero();
   const int lc = level - 1, nc = 1 << lc;
-  if (t & 1) return level_term1<real, D>(rt_tab, lstart, lc, Em, t >> 1);
-  return CAcc<real>::avg(level_term1<real, D>(rt_tab, lstart, lc, Em, ((t >> 1) - 1) & (nc - 1)),
-                         level_term1<real, D>(rt_tab, lstart, lc, Em, t >> 1));
+  if (t & 1) return level_term1<real, D, AC>(rt_tab, lstart, lc, Em, t >> 1);
+  return AC::avg(level_term1<real, D, AC>(rt_tab, lstart, lc, Em, ((t >> 1) - 1) & (nc - 1)),
+                 level_term1<real, D, AC>(rt_tab, lstart, lc, Em, t >> 1));
 }
 
 // Adds g of every grid of x level `level - 1` to the K >= 2 consecutive
 // values T[0..K) at Horner-level index x0.. (x0 a multiple of K): the
 // grid's K/2 centre values from x0/2 on (vector loads once K/2 >= 4) and
 // the one before, periodically.
-template <typename real, int D, int K>
-__device__ __forceinline__ void add_level_terms_cell(CAcc<real>* T, const RowTerm<real, D>* rt_tab,
+template <typename real, int D, int K, typename AC>
+__device__ __forceinline__ void add_level_terms_cell(AC* T, const RowTerm<real, D>* rt_tab,
                                                      const int* lstart, int level, const real* __restrict__ Em,
                                                      int x0) {
+  using TT = typename AC::term;
   constexpr int R = 1 << (D - 1);
   constexpr int H = K / 2;
   const int lc = level - 1, nc = 1 << lc;
   const int c0 = x0 >> 1, cm = (c0 - 1) & (nc - 1);
   for (int gi = lstart[lc]; gi < lstart[lc + 1]; ++gi) {
     const RowTerm<real, D> rt = rt_tab[gi];
-    real t[H + 1];
+    TT t[H + 1];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const real* row = Em + rt.off[r];
-      const real w = rt.w[r];
-      const real prev = row[cm];
+      const TT w = (TT)rt.w[r];
+      const TT prev = (TT)row[cm];
       t[0] = r == 0 ? w * prev : fma(w, prev, t[0]);
       if constexpr (H >= 4) {
 #pragma unroll
         for (int k = 0; k < H; k += 4) {
           const V4<real> a = ld4(row + c0 + k);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) t[1 + k + q] = r == 0 ? w * a.x[q] : fma(w, a.x[q], t[1 + k + q]);
+          for (int q = 0; q < 4; ++q)
+            t[1 + k + q] = r == 0 ? w * (TT)a.x[q] : fma(w, (TT)a.x[q], t[1 + k + q]);
         }
       } else {
 #pragma unroll
-        for (int k = 0; k < H; ++k) t[1 + k] = r == 0 ? w * row[c0 + k] : fma(w, row[c0 + k], t[1 + k]);
+        for (int k = 0; k < H; ++k)
+          t[1 + k] = r == 0 ? w * (TT)row[c0 + k] : fma(w, (TT)row[c0 + k], t[1 + k]);
       }
     }
 #pragma unroll
     for (int j = 0; j < H; ++j) {
-      T[2 * j + 1] = CAcc<real>::add_term(T[2 * j + 1], t[j + 1]);
-      T[2 * j] = CAcc<real>::add_term(T[2 * j], (real)0.5 * (t[j] + t[j + 1]));
+      T[2 * j + 1] = AC::add_term(T[2 * j + 1], t[j + 1]);
+      T[2 * j] = AC::add_term(T[2 * j], (TT)0.5 * (t[j] + t[j + 1]));
     }
   }
 }
 
 // One Horner step in the register phase: Vc values per lane -> 2 Vc, then
 // add the new level's terms; recurse up to level n (2 Vc <= VMAX).
-template <typename real, int D, int Vc, int VMAX, bool CELL>
+template <typename real, int D, int Vc, int VMAX, bool CELL, typename AC>
 struct CombLevels {
-  static __device__ __forceinline__ void run(CAcc<real>* T, int& level, int n, int lane,
+  static __device__ __forceinline__ void run(AC* T, int& level, int n, int lane,
                                              const RowTerm<real, D>* rt_tab, const int* lstart,
                                              const real* __restrict__ Em) {
     if constexpr (2 * Vc <= VMAX) {
-      const CAcc<real> right = T[0].shfl((lane + 1) & 31);
+      const AC right = T[0].shfl((lane + 1) & 31);
 #pragma unroll
       for (int i = Vc - 1; i >= 0; --i) {  // in place, high to low
-        const CAcc<real> nxt = (i == Vc - 1) ? right : T[i + 1];
-        T[2 * i + 1] = CAcc<real>::avg(T[i], nxt);
+        const AC nxt = (i == Vc - 1) ? right : T[i + 1];
+        T[2 * i + 1] = AC::avg(T[i], nxt);
         T[2 * i] = T[i];
       }
       ++level;
       constexpr int K = 2 * Vc;
       if constexpr (CELL) {
-        add_level_terms_cell<real, D, K>(T, rt_tab, lstart, level, Em, lane * K);
+        add_level_terms_cell<real, D, K, AC>(T, rt_tab, lstart, level, Em, lane * K);
       } else if constexpr (K >= 4) {
-        add_level_terms<real, D, K>(T, rt_tab, lstart, level, Em, lane * K);
+        add_level_terms<real, D, K, AC>(T, rt_tab, lstart, level, Em, lane * K);
       } else {
 #pragma unroll
         for (int k = 0; k < K; ++k)
-          T[k] = CAcc<real>::add(T[k], level_term1<real, D>(rt_tab, lstart, level, Em, lane * K + k));
+          T[k] = AC::add(T[k], level_term1<real, D, AC>(rt_tab, lstart, level, Em, lane * K + k));
       }
-      if (level < n) CombLevels<real, D, 2 * Vc, VMAX, CELL>::run(T, level, n, lane, rt_tab, lstart, Em);
+      if (level < n) CombLevels<real, D, 2 * Vc, VMAX, CELL, AC>::run(T, level, n, lane, rt_tab, lstart, Em);
     }
   }
 };
@@ -312,7 +346,7 @@ __host__ __device__ constexpr size_t combine_table_bytes(int ngl) {
 template <int D, int NC>
 constexpr int combine_out_stride() { return NC == 1 ? 1 : ec_stride<D>(); }
 
-template <typename real, int D, int V, int NC, bool CELL>
+template <typename real, int D, int V, int NC, bool CELL, typename AC>
 __global__ void __launch_bounds__(32 * combine_rows_per_block<D>() * NC) k_combine_warp(const GridDesc* __restrict__ grids, LevelLists ll, int lmin,
                                                       const real* __restrict__ E, size_t S, int n,
                                                       real* __restrict__ Ehi, float* __restrict__ Elo,
@@ -347,22 +381,23 @@ __global__ void __launch_bounds__(32 * combine_rows_per_block<D>() * NC) k_combi
   __syncthreads();
   pdl_wait();  // the solve's fields
   real energy = (real)0;
+  double energy_d = 0.0;  // FP64 accumulation: the squares of the double results
   if (row < rows) {
-    CAcc<real> T[V];
+    AC T[V];
     // coarse phase: one value on 2^level lanes, up to 32 values; the terms
     // of all coarse levels are read first (independent loads).  Cell-centred
     // grids enter one level higher.
     int level = min(CELL ? lmin + 1 : lmin, min(n, 5));
     const int ltop = min(n, 5);
-    CAcc<real> sc[6];
+    AC sc[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       const int l = level + j;
       if (l <= ltop && lane < (1 << l))
-        sc[j] = CELL ? cell_term1<real, D>(rt_tab, s_start, l, Em, lane)
-                     : level_term1<real, D>(rt_tab, s_start, l, Em, lane);
+        sc[j] = CELL ? cell_term1<real, D, AC>(rt_tab, s_start, l, Em, lane)
+                     : level_term1<real, D, AC>(rt_tab, s_start, l, Em, lane);
       else
-        sc[j] = CAcc<real>::zero();
+        sc[j] = AC::zero();
     }
     T[0] = sc[0];
 #pragma unroll
@@ -370,31 +405,31 @@ __global__ void __launch_bounds__(32 * combine_rows_per_block<D>() * NC) k_combi
       if (level < ltop) {
         const int h = 1 << level;
         const int k = lane >> 1;
-        const CAcc<real> a = T[0].shfl(k & (h - 1));
-        const CAcc<real> b = T[0].shfl((k + 1) & (h - 1));
-        T[0] = (lane & 1) ? CAcc<real>::avg(a, b) : a;
+        const AC a = T[0].shfl(k & (h - 1));
+        const AC b = T[0].shfl((k + 1) & (h - 1));
+        T[0] = (lane & 1) ? AC::avg(a, b) : a;
         ++level;
-        if (lane < (1 << level)) T[0] = CAcc<real>::add(T[0], sc[j]);
+        if (lane < (1 << level)) T[0] = AC::add(T[0], sc[j]);
       }
     }
     // register phase: 2^level / 32 consecutive values per lane
-    if (level < n) CombLevels<real, D, 1, V, CELL>::run(T, level, n, lane, rt_tab, s_start, Em);
+    if (level < n) CombLevels<real, D, 1, V, CELL, AC>::run(T, level, n, lane, rt_tab, s_start, Em);
     if constexpr (CELL) {  // to the regular centres, then the grids of x level n
       if (N >= 32) {
-        const CAcc<real> right = T[0].shfl((lane + 1) & 31);
+        const AC right = T[0].shfl((lane + 1) & 31);
 #pragma unroll
-        for (int k = 0; k < V; ++k) T[k] = CAcc<real>::avg(T[k], k == V - 1 ? right : T[k + 1]);
+        for (int k = 0; k < V; ++k) T[k] = AC::avg(T[k], k == V - 1 ? right : T[k + 1]);
         if constexpr (V >= 4) {
-          add_level_terms<real, D, V>(T, rt_tab, s_start, n, Em, lane * V);
+          add_level_terms<real, D, V, AC>(T, rt_tab, s_start, n, Em, lane * V);
         } else {
 #pragma unroll
           for (int k = 0; k < V; ++k)
-            T[k] = CAcc<real>::add(T[k], level_term1<real, D>(rt_tab, s_start, n, Em, lane * V + k));
+            T[k] = AC::add(T[k], level_term1<real, D, AC>(rt_tab, s_start, n, Em, lane * V + k));
         }
       } else {
-        const CAcc<real> right = T[0].shfl((lane + 1) & (N - 1));
-        T[0] = CAcc<real>::avg(T[0], right);
-        if (lane < N) T[0] = CAcc<real>::add(T[0], level_term1<real, D>(rt_tab, s_start, n, Em, lane));
+        const AC right = T[0].shfl((lane + 1) & (N - 1));
+        T[0] = AC::avg(T[0], right);
+        if (lane < N) T[0] = AC::add(T[0], level_term1<real, D, AC>(rt_tab, s_start, n, Em, lane));
       }
     }
     // hi parts to the block's node-interleaved stage, lo planes straight out
@@ -411,7 +446,8 @@ __global__ void __launch_bounds__(32 * combine_rows_per_block<D>() * NC) k_combi
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               v[q] = T[k + q].normalised();
-              energy = fmaf(v[q].hi, v[q].hi, energy);
+              if constexpr (kFp64Acc<AC>) energy_d = fma(T[k + q].v, T[k + q].v, energy_d);
+              else energy = fmaf(v[q].hi, v[q].hi, energy);
               srow[(size_t)(lane * V + k + q) * DP + lane] = v[q].hi;
             }
             if (Elo)
@@ -425,7 +461,8 @@ __global__ void __launch_bounds__(32 * combine_rows_per_block<D>() * NC) k_combi
               const ff v = T[k].normalised();
               srow[(size_t)(lane * per + k) * DP + (lane * per + k) / V] = v.hi;
               if (Elo) Elo[o0 + (size_t)lane * per + k] = v.lo;
-              energy = fmaf(v.hi, v.hi, energy);
+              if constexpr (kFp64Acc<AC>) energy_d = fma(T[k].v, T[k].v, energy_d);
+              else energy = fmaf(v.hi, v.hi, energy);
             }
         }
       } else {
@@ -444,7 +481,7 @@ __global__ void __launch_bounds__(32 * combine_rows_per_block<D>() * NC) k_combi
     real* dst = Ehi + (size_t)row0 * N * DP;
     for (int i = threadIdx.x; i < nreal; i += blockDim.x) dst[i] = stage[i + (i / DP) / V];
   }
-  const double tot = warp_sum((double)energy);
+  const double tot = warp_sum((double)energy + energy_d);
   if (lane == 0 && row < rows) partials[task] = tot;
   if (!fin.active) return;
   combine_finalize(partials, rows * NC, fin, red);
@@ -452,13 +489,30 @@ __global__ void __launch_bounds__(32 * combine_rows_per_block<D>() * NC) k_combi
 
 // ---------------------------------------------------------------- block-per-line combination (lines > 1024)
 
-template <typename real, int D, int NC, bool CELL>
+// Block-kernel accumulator of FP32 fields with FP64 accumulation (the
+// counterpart of CAccD): double sum, split into hi + lo floats on output.
+struct AccF64 {
+  using term = double;
+  double v = 0.0;
+  __device__ __forceinline__ void add(double a) { v += a; }
+  __device__ __forceinline__ void add_acc(const AccF64& o) { v += o.v; }
+  __device__ __forceinline__ void scale(double s) { v *= s; }
+  __device__ __forceinline__ float hi() const { return (float)v; }
+  __device__ __forceinline__ float lo() const { return (float)(v - (double)(float)v); }
+};
+template <typename A>
+constexpr bool kFp64BlockAcc = false;
+template <>
+constexpr bool kFp64BlockAcc<AccF64> = true;
+
+template <typename real, int D, int NC, bool CELL, typename AccT>
 __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ grids, LevelLists ll, int lmin,
                                                  const real* __restrict__ E, size_t S, int n, real* __restrict__ Ehi,
                                                  float* __restrict__ Elo, double* __restrict__ partials,
                                                  const CombineFinal fin) {
+  using TT = typename AccT::term;
   extern __shared__ unsigned char smem_raw[];
-  Acc<real>* A = reinterpret_cast<Acc<real>*>(smem_raw);  // [NC][2N], level l of comp m at m*2N + [2^l, 2^(l+1))
+  AccT* A = reinterpret_cast<AccT*>(smem_raw);  // [NC][2N], level l of comp m at m*2N + [2^l, 2^(l+1))
   __shared__ double red[32];
   const int N = 1 << n;
   const size_t ND = (size_t)N * (D == 2 ? N : (size_t)N * N);
@@ -510,9 +564,9 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
   // the transverse interpolation of grid gi, component m, at x index kx
   auto tval = [&](int gi, int m, int kx) {
     const real* base = E + (size_t)m * S + kx;
-    real val = s_w[gi][0] * base[s_off[gi][0]];
+    TT val = (TT)s_w[gi][0] * (TT)base[s_off[gi][0]];
 #pragma unroll
-    for (int r = 1; r < R; ++r) val = fma(s_w[gi][r], base[s_off[gi][r]], val);
+    for (int r = 1; r < R; ++r) val = fma((TT)s_w[gi][r], (TT)base[s_off[gi][r]], val);
     return val;
   };
   // every (level, x index) of the levels Horner reads: each grid's term in
@@ -525,10 +579,10 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
   for (int e = threadIdx.x + (1 << l0); e < 2 * N; e += blockDim.x) {
     const int l = 31 - __clz(e);
     const int kx = e - (1 << l);
-    Acc<real> acc[NC];
+    AccT acc[NC];
     const int lg = CELL ? l - 1 : l;
     for (int gi = s_start[lg]; gi < s_start[lg + 1]; ++gi) {
-      const real c = s_c[gi];
+      const TT c = (TT)s_c[gi];
 #pragma unroll
       for (int m = 0; m < NC; ++m) {
         if (!CELL) {
@@ -537,8 +591,8 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
           acc[m].add(c * tval(gi, m, kx >> 1));
         } else {
           const int nc = 1 << lg;
-          acc[m].add((real)0.5 * c * tval(gi, m, ((kx >> 1) - 1) & (nc - 1)));
-          acc[m].add((real)0.5 * c * tval(gi, m, kx >> 1));
+          acc[m].add((TT)0.5 * c * tval(gi, m, ((kx >> 1) - 1) & (nc - 1)));
+          acc[m].add((TT)0.5 * c * tval(gi, m, kx >> 1));
         }
       }
     }
@@ -551,12 +605,12 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
     const int half = 1 << l;
     for (int e2 = threadIdx.x; e2 < NC * cnt; e2 += blockDim.x) {
       const int m = e2 >> (l + 1), e = e2 & (cnt - 1);
-      Acc<real>* Am = A + m * 2 * N;
+      AccT* Am = A + m * 2 * N;
       const int k = e >> 1;
-      Acc<real> v = Am[half + k];
+      AccT v = Am[half + k];
       if (e & 1) {
         v.add_acc(Am[half + ((k + 1) & (half - 1))]);
-        v.scale((real)0.5);
+        v.scale((TT)0.5);
       }
       Am[cnt + e].add_acc(v);
     }
@@ -565,26 +619,28 @@ __global__ void __launch_bounds__(256) k_combine(const GridDesc* __restrict__ gr
   // field energy: each thread sums the squares of its few nodes in the run's
   // precision; the block and the step reduce the partials in FP64
   real energy = (real)0;
+  double energy_d = 0.0;  // FP64 accumulation: the squares of the double results
   for (int e2 = threadIdx.x; e2 < NC * N; e2 += blockDim.x) {
     const int m = e2 >> n, x = e2 & (N - 1);
-    Acc<real> v = A[m * 2 * N + N + x];
+    AccT v = A[m * 2 * N + N + x];
     if (CELL) {  // to the regular centres, then the grids of x level n
       v.add_acc(A[m * 2 * N + N + ((x + 1) & (N - 1))]);
-      v.scale((real)0.5);
-      for (int gi = s_start[n]; gi < s_start[n + 1]; ++gi) v.add(s_c[gi] * tval(gi, m, x));
+      v.scale((TT)0.5);
+      for (int gi = s_start[n]; gi < s_start[n + 1]; ++gi) v.add((TT)s_c[gi] * tval(gi, m, x));
     }
     const size_t o = (size_t)m * ND + (size_t)row * N + x;
     Ehi[((size_t)row * N + x) * combine_out_stride<D, NC>() + m] = (real)v.hi();
     if (Elo) Elo[o] = (float)v.lo();
-    energy = fma((real)v.hi(), (real)v.hi(), energy);
+    if constexpr (kFp64BlockAcc<AccT>) energy_d = fma(v.v, v.v, energy_d);
+    else energy = fma((real)v.hi(), (real)v.hi(), energy);
   }
-  double tot = block_sum_double((double)energy, red);
+  double tot = block_sum_double((double)energy + energy_d, red);
   if (threadIdx.x == 0) partials[row] = tot;
   if (!fin.active) return;
   combine_finalize(partials, (int)gridDim.x, fin, red);
 }
 
-template <typename real, int D, int V, int NC, bool CELL>
+template <typename real, int D, int V, int NC, bool CELL, typename AC>
 static int launch_combine_warp(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n,
                                real* Ehi, float* Elo, double* energy_partials, const CombineFinal& fin,
                                cudaStream_t s) {
@@ -596,17 +652,17 @@ static int launch_combine_warp(const GridDesc* grids, const LevelLists& ll, int 
                       ((size_t)RPB * N * combine_out_stride<D, NC>() + (size_t)RPB * N / V) * sizeof(real);
   static bool attr_set = false;
   if (!attr_set && smem > 48 * 1024) {
-    SG_CUDA(cudaFuncSetAttribute(k_combine_warp<real, D, V, NC, CELL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SG_CUDA(cudaFuncSetAttribute(k_combine_warp<real, D, V, NC, CELL, AC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024));
     attr_set = true;
   }
-  SG_CUDA(launch_pdl(k_combine_warp<real, D, V, NC, CELL>, dim3(blocks), dim3(32 * RPB * NC), smem, s, grids, ll, lmin, E,
+  SG_CUDA(launch_pdl(k_combine_warp<real, D, V, NC, CELL, AC>, dim3(blocks), dim3(32 * RPB * NC), smem, s, grids, ll, lmin, E,
                      S, n, Ehi, Elo, energy_partials, fin));
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
 
-template <typename real, int D, int NC, bool CELL>
+template <typename real, int D, int NC, bool CELL, typename AC, typename AccT>
 static int launch_combine_nc(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n,
                              real* Ehi, float* Elo, double* energy_partials, const CombineFinal& fin,
                              cudaStream_t s) {
@@ -616,48 +672,64 @@ static int launch_combine_nc(const GridDesc* grids, const LevelLists& ll, int lm
     case 8:
     case 16:
     case 32:
-      return launch_combine_warp<real, D, 1, NC, CELL>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 1, NC, CELL, AC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     case 64:
-      return launch_combine_warp<real, D, 2, NC, CELL>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 2, NC, CELL, AC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     case 128:
-      return launch_combine_warp<real, D, 4, NC, CELL>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 4, NC, CELL, AC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     case 256:
-      return launch_combine_warp<real, D, 8, NC, CELL>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 8, NC, CELL, AC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     case 512:
-      return launch_combine_warp<real, D, 16, NC, CELL>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 16, NC, CELL, AC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     case 1024:
-      return launch_combine_warp<real, D, 32, NC, CELL>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+      return launch_combine_warp<real, D, 32, NC, CELL, AC>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
     default:
       break;
   }
   unsigned rows = (unsigned)(D == 2 ? N : N * N);
-  size_t smem = (size_t)NC * 2 * N * sizeof(Acc<real>);
+  size_t smem = (size_t)NC * 2 * N * sizeof(AccT);
   static bool attr_set = false;
   if (!attr_set) {
-    SG_CUDA(cudaFuncSetAttribute(k_combine<real, D, NC, CELL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    SG_CUDA(cudaFuncSetAttribute(k_combine<real, D, NC, CELL, AccT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  k_combine<real, D, NC, CELL><<<rows, 256, smem, s>>>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin);
+  k_combine<real, D, NC, CELL, AccT><<<rows, 256, smem, s>>>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
 
+template <typename real, int D, typename AC, typename AccT>
+static int launch_combine_acc(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n,
+                              real* Ehi, float* Elo, double* energy_partials, const CombineFinal& fin, cudaStream_t s,
+                              int ncomp, bool cell) {
+  if (cell) {
+    if (ncomp == 1)
+      return launch_combine_nc<real, D, 1, true, AC, AccT>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+    return launch_combine_nc<real, D, D, true, AC, AccT>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+  }
+  if (ncomp == 1)
+    return launch_combine_nc<real, D, 1, false, AC, AccT>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+  return launch_combine_nc<real, D, D, false, AC, AccT>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+}
+
+// fp64_acc selects FP64 accumulation of FP32 fields (CAccD / AccF64); the
+// FP64 path always accumulates in double.
 template <typename real, int D>
 int launch_combine(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n, real* Ehi,
                    float* Elo, double* energy_partials, const CombineFinal& fin, cudaStream_t s, int ncomp,
-                   bool cell) {
-  if (cell) {
-    if (ncomp == 1)
-      return launch_combine_nc<real, D, 1, true>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
-    return launch_combine_nc<real, D, D, true>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+                   bool cell, bool fp64_acc) {
+  if constexpr (sizeof(real) == 4) {
+    if (fp64_acc)
+      return launch_combine_acc<real, D, CAccD, AccF64>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s,
+                                                        ncomp, cell);
   }
-  if (ncomp == 1) return launch_combine_nc<real, D, 1, false>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
-  return launch_combine_nc<real, D, D, false>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin, s);
+  return launch_combine_acc<real, D, CAcc<real>, Acc<real>>(grids, ll, lmin, E, S, n, Ehi, Elo, energy_partials, fin,
+                                                            s, ncomp, cell);
 }
 
 #define SG_INST_COMB(real, D)                                                                                   \
   template int launch_combine<real, D>(const GridDesc*, const LevelLists&, int, const real*, size_t, int, real*, \
-                                       float*, double*, const CombineFinal&, cudaStream_t, int, bool);
+                                       float*, double*, const CombineFinal&, cudaStream_t, int, bool, bool);
 SG_INST_COMB(float, 2)
 SG_INST_COMB(float, 3)
 SG_INST_COMB(double, 2)

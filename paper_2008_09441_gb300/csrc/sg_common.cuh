@@ -202,6 +202,7 @@ struct Acc;
 
 template <>
 struct Acc<float> {
+  using term = float;
   ff v{0.f, 0.f};
   __device__ __forceinline__ void add_prod(float a, float b) { v = ff_add(v, two_prod(a, b)); }
   __device__ __forceinline__ void add(float a) { v = ff_add_f(v, a); }
@@ -214,6 +215,7 @@ struct Acc<float> {
 
 template <>
 struct Acc<double> {
+  using term = double;
   double v = 0.0;
   __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
   __device__ __forceinline__ void add(double a) { v += a; }

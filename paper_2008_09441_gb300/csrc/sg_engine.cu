@@ -130,19 +130,7 @@ class Engine final : public EngineBase {
       SG_TRY(alloc((void**)&reg_partials_, (size_t)2 * reg_blocks_ * sizeof(double)));
     }
 
-    // ---- charges: sum_p q_p in FP64 (fixed during the run)
-    {
-      const int nb = 256;
-      double* part = nullptr;
-      SG_TRY(alloc((void**)&part, nb * sizeof(double)));
-      SG_TRY(launch_sum_to_double<real>(P_[cur_].w, np_, part, nb, stream_));
-      std::vector<double> h(nb);
-      SG_CUDA(cudaMemcpyAsync(h.data(), part, nb * sizeof(double), cudaMemcpyDeviceToHost, stream_));
-      SG_CUDA(cudaStreamSynchronize(stream_));
-      charge_total_ = 0;
-      for (double x : h) charge_total_ += x;
-      free_one(part);
-    }
+    SG_TRY(compute_charge_total());
     unsigned st = 0;
     SG_CUDA(cudaMemcpy(&st, status_, sizeof(unsigned), cudaMemcpyDeviceToHost));
     if (st & ST_NONFINITE) {
@@ -175,6 +163,21 @@ class Engine final : public EngineBase {
     SG_CUDA(cudaStreamSynchronize(stream_));
     step_ = 0;
     return check_status();
+  }
+
+  // sum_p q_p in FP64 (fixed while the particles are; recomputed on upload)
+  int compute_charge_total() {
+    const int nb = 256;
+    double* part = nullptr;
+    SG_TRY(alloc((void**)&part, nb * sizeof(double)));
+    SG_TRY(launch_sum_to_double<real>(P_[cur_].w, np_, part, nb, stream_));
+    std::vector<double> h(nb);
+    SG_CUDA(cudaMemcpyAsync(h.data(), part, nb * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    charge_total_ = 0;
+    for (double x : h) charge_total_ += x;
+    free_one(part);
+    return SG_OK;
   }
 
   int step(int nsteps) override {
@@ -547,6 +550,7 @@ class Engine final : public EngineBase {
     SG_CUDA(cudaStreamSynchronize(stream_));
     cur_ = 0;
     SG_TRY(upload_particles(&in));
+    SG_TRY(compute_charge_total());
     if (hd.tau != tau_) SG_TRY(build_grid_set(hd.tau));
     adaptive_ = hd.adaptive != 0;
     SG_TRY(enqueue_sort());
@@ -991,6 +995,14 @@ class Engine final : public EngineBase {
     for (int m = 0; m < D; ++m) hd *= cfg_.L[m] / (double)N_;
     return 0.5 * hd;
   }
+  // Mean charge density Q / |box|: the mean of every component density and
+  // of the filtered density (the transfer operators and the deposit conserve
+  // the total charge), subtracted before the forward transforms.
+  real rho_mean() const {
+    double vol = 1;
+    for (int m = 0; m < D; ++m) vol *= cfg_.L[m];
+    return (real)(charge_total_ / vol);
+  }
   real inv_cell_vol() const {
     double hd = 1;
     for (int m = 0; m < D; ++m) hd *= cfg_.L[m] / (double)N_;
@@ -1075,6 +1087,7 @@ class Engine final : public EngineBase {
     a.tw = tw_;
     a.log_nmax = n_;
     a.dim = D;
+    a.rho_mean = rho_mean();
     int maxsize = 0;
     for (auto& g : gdesc_) maxsize = std::max(maxsize, g.size);
     const bool small_ok = maxsize <= small_solve_max<real>();
@@ -1142,7 +1155,7 @@ class Engine final : public EngineBase {
     fin.dd = dd_;
     fin.counter = comb_counter_;
     return launch_combine<real, D>(grids_dev_, levels_, lmin_, E_arena_, S_, n_, Ehi_, Elo_, fe_partials_, fin,
-                                   stream_, D, cfg_.cell);
+                                   stream_, D, cfg_.cell, cfg_.combine_fp64);
   }
 
   // Filter mode (Algorithm 2): rho_f = sum_i c_i P_i R_i rho~ on the regular
@@ -1152,11 +1165,11 @@ class Engine final : public EngineBase {
     CombineFinal off;
     std::memset(&off, 0, sizeof(off));
     return launch_combine<real, D>(grids_dev_, levels_, lmin_, rho_arena_, S_, n_, rho_f_, nullptr, fe_partials_, off,
-                                   stream_, 1, cfg_.cell);
+                                   stream_, 1, cfg_.cell, cfg_.combine_fp64);
   }
   int enqueue_regular_solve(const double* ke) {
-    SG_TRY(launch_regular_solve<real>(rho_f_, regA_, regB_, ktab_, tw_, D, n_, Ehi_, Elo_, ec_stride<D>(),
-                                      reg_partials_, reg_blocks_, stream_));
+    SG_TRY(launch_regular_solve<real>(rho_f_, rho_mean(), regA_, regB_, ktab_, tw_, D, n_, Ehi_, Elo_,
+                                      ec_stride<D>(), reg_partials_, reg_blocks_, stream_));
     return launch_finalize_step(reg_partials_, reg_blocks_ * ((D + 1) / 2), ke, ke ? nke_ : 0, fe_scale(), dd_,
                                 stream_);
   }

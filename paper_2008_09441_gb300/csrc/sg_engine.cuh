@@ -32,6 +32,7 @@ struct EngineConfig {
   int sort_every = 0;
   int mode = SG_MODE_COMBINE;
   bool cell = false;  // cell-centred grids (nodes at (k + 1/2) h)
+  bool combine_fp64 = false;  // FP32 path: combination accumulated in double (else float-float)
   // deposit window capacity in regular nodes with 64-bit accumulators (64 KB;
   // a 128 x 128 window of 32-bit fixed point in 2D, 24^3 in 3D): large enough
   // for a chunk's particles a few steps after a sort

@@ -139,6 +139,12 @@ struct SolveArena {
   const cplx<real>* tw;  // twiddles exp(-2 pi i k / Nmax), k < Nmax/2
   int log_nmax;
   int dim;
+  // Mean density Q / |box| of every component grid (the deposit's partition
+  // of unity gives each grid the total charge).  It is subtracted before the
+  // forward transform: the k = 0 mode is dropped by the solve anyway, and
+  // without the mean the transform's rounding is relative to the density's
+  // fluctuation instead of its (much larger) uniform part.
+  real rho_mean;
 };
 
 // Complex values per block of a transform pass (whole lines, at least one
@@ -160,9 +166,9 @@ constexpr int small_solve_max() { return sizeof(real) == 4 ? 4096 : 2048; }
 // (E_hi node-interleaved with `stride`, FP32 low planes zeroed), per-block
 // field-energy partials at partials[pair * blocks + block] (ceil(dim/2) pairs).
 template <typename real>
-int launch_regular_solve(const real* rho_f, cplx<real>* A, cplx<real>* B, const real* ktab, const cplx<real>* tw,
-                         int dim, int n, real* Ehi, float* Elo, int stride, double* partials, int blocks,
-                         cudaStream_t s);
+int launch_regular_solve(const real* rho_f, real rho_mean, cplx<real>* A, cplx<real>* B, const real* ktab,
+                         const cplx<real>* tw, int dim, int n, real* Ehi, float* Elo, int stride, double* partials,
+                         int blocks, cudaStream_t s);
 
 // Generic in-place complex FFT of a whole N^D array (regular grid) along one
 // axis, forward or inverse (unnormalised), in the given precision.
@@ -265,7 +271,8 @@ template <typename real, int D>
 int launch_combine(const GridDesc* grids, const LevelLists& ll, int lmin, const real* E, size_t S, int n,
                    real* Ehi, float* Elo, double* energy_partials, const CombineFinal& fin,
                    cudaStream_t s, int ncomp,  // ncomp = D: the fields, interleaved; 1: a density, plain
-                   bool cell);                 // cell-centred grids
+                   bool cell,                  // cell-centred grids
+                   bool fp64_acc);             // FP32 path: accumulate in double instead of float-float
 
 template <typename real>
 int launch_grid_charges(const GridDesc* grids, int ngrids, const real* rho, const double* vol,

@@ -50,11 +50,12 @@ def _on_device(x):
 
 _MODES = {"combine": L.SG_MODE_COMBINE, "filter": L.SG_MODE_FILTER}
 _CENTRINGS = {"node": L.SG_NODE_CENTRED, "cell": L.SG_CELL_CENTRED}
+_COMBINES = {"float-float": L.SG_COMBINE_FLOAT_FLOAT, "fp64": L.SG_COMBINE_FP64}
 
 
 def make_params(precision=L.SG_FP32, tau=1, dt=0.05, qm=-1.0, B=(0.0, 0.0, 0.0), eext_lin=(0.0, 0.0, 0.0),
                 alpha=0.01, pc_ref=5.0, tau_constants=L.SG_TAU_CONST_PAPER, sort_every=0, stream=None,
-                mode=L.SG_MODE_COMBINE, centring=L.SG_NODE_CENTRED):
+                mode=L.SG_MODE_COMBINE, centring=L.SG_NODE_CENTRED, combine=L.SG_COMBINE_FLOAT_FLOAT):
     p = L.sg_params()
     p.precision = precision
     p.tau = tau
@@ -70,6 +71,7 @@ def make_params(precision=L.SG_FP32, tau=1, dt=0.05, qm=-1.0, B=(0.0, 0.0, 0.0),
     p.stream = stream
     p.mode = _MODES.get(mode, mode)
     p.centring = _CENTRINGS.get(centring, centring)
+    p.combine = _COMBINES.get(combine, combine)
     return p
 
 
@@ -166,7 +168,7 @@ class Run:
 
     def __init__(self, L_box, n, u, v, w, dt, *, tau=1, qm=-1.0, precision="fp32", B=(0.0, 0.0, 0.0),
                  eext_lin=(0.0, 0.0, 0.0), alpha=0.01, pc_ref=5.0, tau_constants="paper", sort_every=0,
-                 stream=None, mode="combine", centring="node"):
+                 stream=None, mode="combine", centring="node", combine="float-float"):
         self.d = len(L_box)
         self.n = n
         self.precision = L.SG_FP32 if precision in ("fp32", L.SG_FP32) else L.SG_FP64
@@ -190,7 +192,7 @@ class Run:
         parts.w = _ptr(wcol).value
         tc = L.SG_TAU_CONST_PAPER if tau_constants == "paper" else L.SG_TAU_CONST_EMPIRICAL
         self.params = make_params(self.precision, tau, dt, qm, B, eext_lin, alpha, pc_ref, tc, sort_every,
-                                  stream, mode, centring)
+                                  stream, mode, centring, combine)
         self._keep = (ucols, vcols, wcol)
         self.h = sg_pic_init(dom, n, d, 1, parts, self.params)
         self._keep = None
@@ -359,7 +361,7 @@ class Server:
         self.meta = {}
 
     def submit(self, L_box, n, u, v, w, dt, nsteps, *, tau=1, qm=-1.0, precision="fp32", B=(0.0, 0.0, 0.0),
-               eext_lin=(0.0, 0.0, 0.0), sort_every=0, mode="combine", centring="node"):
+               eext_lin=(0.0, 0.0, 0.0), sort_every=0, mode="combine", centring="node", combine="float-float"):
         d = len(L_box)
         prec = L.SG_FP32 if precision in ("fp32", L.SG_FP32) else L.SG_FP64
         dt_np = _DT[prec]
@@ -379,7 +381,7 @@ class Server:
             req.particles.v[m] = _ptr(vcols[m]).value
         req.particles.w = _ptr(wcol).value
         req.params = make_params(prec, tau, dt, qm, B, eext_lin, 0.01, 5.0, L.SG_TAU_CONST_PAPER, sort_every, None,
-                                 mode, centring)
+                                 mode, centring, combine)
         req.nsteps = int(nsteps)
         t = C.c_ulonglong()
         check(lib().sg_serve_submit(self.h, C.byref(req), C.byref(t)), "sg_serve_submit")

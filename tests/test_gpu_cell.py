@@ -6,7 +6,7 @@ import pytest
 
 from oracle import sgpic_oracle as O
 from paper_2008_09441_gb300 import workloads
-from test_gpu_parity import TOL, make_run, nrmse, nrmse_periodic, torch_cuda  # noqa: F401
+from test_gpu_parity import TOL, make_run, nrmse, nrmse_periodic, relerr, torch_cuda  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -37,11 +37,11 @@ def test_cell_fields_at_init(torch_cuda, prec, d, n, tau, np_):
         assert nrmse(gq[l], rho) < tol, l
         for m in range(d):
             if np.max(np.abs(E[m])) > 0:
-                assert nrmse(gf[l][m], E[m]) < 20 * tol, (l, m)
+                assert nrmse(gf[l][m], E[m]) < tol, (l, m)
     Ec = O.combined_field_regular(comps, n, d, "cell")
     Eg = run.field()
     for m in range(d):
-        assert nrmse(Eg[m], Ec[m]) < 20 * tol, m
+        assert nrmse(Eg[m], Ec[m]) < tol, m
     run.close()
 
 
@@ -64,7 +64,7 @@ def test_cell_line_lengths(torch_cuda, prec, d, n, tau, np_):
     for m in range(d):
         ref = sum(c * O.prolong_at(E[m], n, l, idx, "cell") for l, c, rho, E in comps)
         got = Eg[m][tuple(idx[:, a] for a in range(d))]
-        assert nrmse(got, ref) < 20 * TOL[prec], m
+        assert nrmse(got, ref) < TOL[prec], m
     run.close()
 
 
@@ -89,13 +89,13 @@ def test_cell_trajectory(torch_cuda, prec, mode, d, n):
     Eg = run.field()
     Er = ref.regular_field()
     for m in range(d):
-        assert nrmse(Eg[m], Er[m]) < 20 * tol
+        assert nrmse(Eg[m], Er[m]) < tol
     gq = run.grid_charges()
     for l, c, rho, _ in ref.comps:
         assert nrmse(gq[l], rho) < tol, l
     dg, rd = run.diagnostics(), ref.diagnostics()
     for key in ("field_energy", "field_energy_prev", "kinetic_energy"):
-        assert abs(dg[key] - rd[key]) <= 20 * tol * abs(rd[key]) + 1e-300, (key, dg[key], rd[key])
+        assert relerr(dg[key], rd[key]) <= tol, (key, dg[key], rd[key])
     ctol = 1e-10 if prec == "fp64" else tol
     assert abs(dg["charge_combined"] - rd["charge_combined"]) <= ctol * abs(rd["charge_total"])
     run.close()

@@ -45,7 +45,7 @@ def test_fullsize_landau_bench_configuration(torch_cuda):
     Eg = run.field()
     for m in range(d):
         ref = sum(c * O.prolong_at(E[m], n, l, idx) for l, c, rho, E in comps)
-        assert nrmse(Eg[m][idx[:, 0], idx[:, 1]], ref) < 20 * tol, m
+        assert nrmse(Eg[m][idx[:, 0], idx[:, 1]], ref) < tol, m
 
     # first step on a sample: backward half kick at init, then kick and drift
     # with the initial field (both use E(x^0))
@@ -72,4 +72,41 @@ def test_fullsize_landau_bench_configuration(torch_cuda):
     c4 = np.bincount(k4.astype(np.int64), minlength=2 ** (n * d))
     assert np.array_equal(counts, c4)
     assert run.diagnostics()["count_checksum"] == O.count_checksum(c4)
+    run.close()
+
+
+def test_landau_n10_fp32_ten_steps(torch_cuda):
+    """The benchmark's configuration (2D Landau damping, n = 10, tau = 1, 19
+    component grids, FP32, sort every 4 steps, graph-launched steps) over 10
+    steps on 262,144 particles, which the oracle advances in full: the
+    particle state after every step (steps 2-4 and 6-8 are the ones where
+    particles have drifted since the last sort and the deposit's windows
+    take their slow path), then the combined field, the component charges
+    and the energies and charges of the diagnostics at the end."""
+    from test_gpu_parity import relerr
+    wl = workloads.make("landau2d_n10_fp32", n_particles=1 << 18, steps=10)
+    n, d = wl.n, wl.dim
+    run, (u64, v64, q64) = make_run(wl, "fp32", torch_cuda, sort_every=4)
+    ref = O.OracleRun(wl.L, n, u64, v64, q64, wl.dt, qm=wl.qm, tau=wl.tau)
+    tol = TOL["fp32"]
+    for s in range(10):
+        run.step(1)
+        ref.step(1)
+        ug, vg, _ = run.particles()
+        e_u = nrmse_periodic(ug, ref.u)
+        e_v = nrmse(vg, ref.velocities())
+        assert e_u < tol and e_v < tol, (s, e_u, e_v)
+    Ec = O.combined_field_regular(ref.comps, n, d)
+    Eg = run.field()
+    for m in range(d):
+        assert nrmse(Eg[m], Ec[m]) < tol, m
+    gq = run.grid_charges()
+    for l, c, rho, E in ref.comps:
+        assert nrmse(gq[l], rho) < tol, l
+    dg, rd = run.diagnostics(), ref.diagnostics()
+    assert dg["step"] == 10 and dg["tau"] == 1
+    for key in ("field_energy", "field_energy_prev", "kinetic_energy"):
+        assert relerr(dg[key], rd[key]) <= tol, (key, dg[key], rd[key])
+    assert relerr(dg["charge_combined"], rd["charge_combined"]) <= tol
+    assert dg["charge_grid_max_abs_err"] <= tol * abs(rd["charge_total"])
     run.close()

@@ -28,6 +28,12 @@ def nrmse(a, ref):
     return float(np.sqrt(np.sum((a - ref) ** 2) / den))
 
 
+def relerr(a, ref):
+    """|a - ref| / |ref| of one scalar result (|a - ref| when ref is 0)."""
+    a, ref = float(a), float(ref)
+    return abs(a - ref) / abs(ref) if ref != 0.0 else abs(a - ref)
+
+
 def nrmse_periodic(u, ref):
     du = np.asarray(u, np.float64) - np.asarray(ref, np.float64)
     du -= np.round(du)
@@ -143,13 +149,13 @@ def test_fields_at_init(torch_cuda, prec, d, n, tau, np_):
         assert nrmse(gq[l], rho) < tol, l
         for m in range(d):
             if np.max(np.abs(E[m])) > 0:
-                assert nrmse(gf[l][m], E[m]) < 20 * tol, (l, m)
+                assert nrmse(gf[l][m], E[m]) < tol, (l, m)
             else:
                 assert np.max(np.abs(gf[l][m])) < 1e-12
     Ec = O.combined_field_regular(comps, n, d)
     Eg = run.field()
     for m in range(d):
-        assert nrmse(Eg[m], Ec[m]) < 20 * tol
+        assert nrmse(Eg[m], Ec[m]) < tol
     run.close()
 
 
@@ -178,7 +184,7 @@ def test_restriction_line_lengths(torch_cuda, prec, d, n, tau, np_):
     Eg = run.field()
     for m in range(d):
         got = Eg[m][tuple(idx[:, a] for a in range(d))]
-        assert nrmse(got, ref[m]) < 20 * TOL[prec], m
+        assert nrmse(got, ref[m]) < TOL[prec], m
     run.close()
 
 
@@ -208,13 +214,13 @@ def trajectory_check(wl, prec, torch, steps, tol_scale=1.0, **kw):
     Ec = O.combined_field_regular(ref.comps, ref.n, ref.d)
     Eg = run.field()
     for m in range(ref.d):
-        assert nrmse(Eg[m], Ec[m]) < 20 * tol
+        assert nrmse(Eg[m], Ec[m]) < tol
     gq = run.grid_charges()
     for l, c, rho, E in ref.comps:
         assert nrmse(gq[l], rho) < tol
     assert d["step"] == steps and d["tau"] == wl.tau
     for key in ("field_energy", "field_energy_prev", "kinetic_energy"):
-        assert abs(d[key] - rd[key]) <= 20 * tol * abs(rd[key]) + 1e-300, (key, d[key], rd[key])
+        assert relerr(d[key], rd[key]) <= tol, (key, d[key], rd[key])
     ctol = 1e-10 if prec == "fp64" else TOL[prec]
     assert abs(d["charge_combined"] - rd["charge_combined"]) <= ctol * abs(rd["charge_total"])
     assert d["charge_grid_max_abs_err"] <= (1e-10 if prec == "fp64" else 1e-5) * abs(rd["charge_total"])
@@ -365,8 +371,23 @@ def test_adaptive_tau_runs(torch_cuda):
     run.step(3)
     d = run.diagnostics()
     assert 1 <= d["tau"] <= 4
-    t, _, _ = run.select_tau()
-    assert t == d["tau"] or True  # the selection of the current state may move by one step
+    # the last selection was made on the current positions (after the last
+    # push): selecting again, and the oracle's Algorithm 1 on the GPU's
+    # positions, give the same tau, or a tie within 1e-9 of the total
+    t, g, z = run.select_tau()
+    ug, _, wg = run.particles()
+    reg = O.deposit_cic(O.wrap_unit(ug.astype(np.float64)), wg.astype(np.float64), (wl.n,) * 2, wl.L)
+    t_ref, table, _ = O.tau_estimator(reg, Np=len(wg), L=wl.L[0], alpha=0.05, pc_ref=5.0,
+                                      Qe=float(np.sum(wg.astype(np.float64))))
+    tot = {tt: ge + ze for tt, ge, ze in table}
+
+    def same(a, b):
+        return a == b or abs(tot[a] - tot[b]) <= 1e-9 * tot[b]
+
+    assert same(t, t_ref), (t, t_ref, tot)
+    assert same(d["tau"], t_ref), (d["tau"], t_ref, tot)
+    for tt, ge, ze in table:
+        assert g[tt - 1] == pytest.approx(ge, rel=1e-9) and z[tt - 1] == pytest.approx(ze, rel=1e-9)
     run.close()
 
 
@@ -459,3 +480,51 @@ def test_fixed_solve_variants_agree(torch_cuda, prec):
     runs[0].step(1)
     for run in runs:
         run.close()
+
+
+# ------------------------------------------------------------ combination accumulation (FP32 path)
+
+
+@pytest.mark.parametrize("d,n,tau,np_,centring,mode", [
+    (2, 7, 1, 20000, "node", "combine"), (3, 5, 1, 15000, "node", "combine"),
+    (2, 6, 1, 12000, "cell", "combine"), (2, 6, 2, 12000, "node", "filter"),
+    (2, 11, 2, 6000, "node", "combine"),  # lines of 2^11: the block-per-line kernel
+])
+def test_combine_fp64_accumulation(torch_cuda, d, n, tau, np_, centring, mode):
+    """sg_params.combine = SG_COMBINE_FP64 on the FP32 path: the combined
+    field (or the filter mode's field) equals the FP64 oracle within the FP32
+    tolerance, and float-float and FP64 accumulation land within 1e-6 of each
+    other (both are limited by the FP32 component fields, not by the sum)."""
+    if d == 2:
+        wl = workloads.landau2d(n_particles=np_, n=n, tau=tau, seed=181 + n)
+    else:
+        wl = workloads.twostream3d(n_particles=np_, n=n, tau=tau, seed=181 + n)
+    _, (u64, v64, q64) = make_run(wl, "fp32", torch_cuda, device_inputs=False, centring=centring, mode=mode)
+    u64 = O.wrap_unit(u64)
+    if mode == "filter":
+        Eref = O.filtered_field_regular(u64, q64, n, tau, wl.L, centring)[2]
+    else:
+        Eref = O.combined_field_regular(O.component_fields(u64, q64, n, tau, wl.L, centring), n, d, centring)
+    fields = {}
+    for acc in ("float-float", "fp64"):
+        run, _ = make_run(wl, "fp32", torch_cuda, centring=centring, mode=mode, combine=acc)
+        fields[acc] = run.field()
+        e = [nrmse(fields[acc][m], Eref[m]) for m in range(d)]
+        assert max(e) < TOL["fp32"], (acc, e)
+        run.close()
+    for m in range(d):
+        assert nrmse(fields["float-float"][m], fields["fp64"][m]) < 1e-6
+
+
+def test_combine_fp64_trajectory(torch_cuda):
+    """Ten FP32 steps with the FP64-accumulating combination against the
+    oracle (the trajectory check of the float-float path)."""
+    wl = workloads.landau2d(n_particles=40000, n=7, tau=1, seed=21)
+    trajectory_check(wl, "fp32", torch_cuda, 10, combine="fp64")
+
+
+def test_combine_invalid_value_rejected(torch_cuda):
+    from paper_2008_09441_gb300 import SGError
+    wl = workloads.landau2d(n_particles=100, n=4, tau=1, seed=1)
+    with pytest.raises(SGError):
+        make_run(wl, "fp32", torch_cuda, combine=7)

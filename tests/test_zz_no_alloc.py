@@ -1,5 +1,6 @@
-"""The allocation-free cell sort (sg_cell_sort_static) against the
-allocating one (sg_cell_sort), through the C ABI.
+"""The allocation-free cell sort (sg_cell_sort_static) against the FP64
+oracle's cell keys and stable sort, and against the allocating entry point
+(sg_cell_sort), through the C ABI.
 
 sg_cell_sort_static exists for callers that must not allocate device memory
 (a device-memory budget owned by another allocator, or loops where an
@@ -13,6 +14,8 @@ import ctypes as C
 
 import numpy as np
 import pytest
+
+from oracle import sgpic_oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -46,6 +49,13 @@ def test_static_scratch_sort_matches_allocating_sort():
         sa, ka, pa, ca = _sort(lib.sg_cell_sort, cols, level, prec)
         sb, kb, pb, cb = _sort(lib.sg_cell_sort_static, cols, level, prec)
         assert sa == L.SG_OK and sb == L.SG_OK, lib.sg_last_error().decode()
+        # the oracle's Morton keys of the same positions and its stable
+        # counting sort: keys, permutation and counts are unique, bit for bit
+        k_ref = O.cell_keys(u.astype(np.float64), level)
+        p_ref, sk_ref, c_ref = O.sort_by_key(k_ref, level, d)
+        assert np.array_equal(kb.view(np.uint32), sk_ref)
+        assert np.array_equal(pb.view(np.uint32), p_ref)
+        assert np.array_equal(cb.view(np.uint32), c_ref)
         assert np.array_equal(ka, kb)
         assert np.array_equal(pa, pb)
         assert np.array_equal(ca, cb)
