@@ -307,12 +307,17 @@ def run_reference(args, world, rank, pg):
 
 
 def run_serving(args, world, rank, local):
-    """Serving mix: independent 2D Landau / 3D two-stream runs (level n
-    uniform in 5..10 / 5..7, particles log-uniform 2^16..2^max) arriving as a
-    Poisson process, admitted by memory footprint, FP32, `--steps` steps
-    each; the same request stream is served batched (one graph per tick) and
-    plain (per run, per grid launches).  Reports p50 / p99 per-step latency
-    and aggregate particle-steps per second of device time, for both."""
+    """Serving mix: independent 2D Landau / 3D two-stream runs with the
+    serving configuration's parameter distribution (level n uniform in
+    5..10 / 5..7, particles log-uniform 2^16..2^max, amplitude log-uniform
+    1e-3..0.1, k uniform 0.3..0.6, `--steps` steps each), arriving as a
+    Poisson process whose rate is set to about 80% of the batched server's
+    measured capacity, admitted by memory footprint (8 GB budget, 16 slots).
+    The same arrival stream is served batched (one graph per tick) and plain
+    (runs stepped in turn with direct launches, one solve launch per grid).
+    Reports per mode: p50 / p99 per-step latency (device), particle-steps/s
+    of device time and of wall time, the device's busy fraction, and p50 /
+    p99 of the time from a request's arrival to its result."""
     import torch
     from paper_2008_09441_gb300 import workloads
     from paper_2008_09441_gb300.sgpic import Server
@@ -320,36 +325,62 @@ def run_serving(args, world, rank, local):
     steps = max(1, args.steps)
     params = workloads.serving_mix(n_runs=args.serving_runs, max_log2_particles=args.serving_max_log2)
     wls = []
-    for p in params:
+    for p in params:  # generated once, shared by both modes
         p["steps"] = steps
-        wls.append(workloads.serving_run_workload(p))
-    # Poisson arrivals scaled so that the stream keeps the device busy
-    total_ps = sum(w.n_particles for w in wls) * steps
-    out = {"metric": "serving: p50/p99 step latency and particle-steps/s", "unit": UNIT, "n_gpus": world,
-           "steps": steps, "runs": len(wls), "data": "synthetic (seeded serving mix)", "modes": {}}
-    for mode in ("batched", "plain"):
-        srv = Server(hbm_budget_bytes=8 << 30, max_slots=16)
+        wl = workloads.serving_run_workload(p)
+        wls.append((wl.L, wl.n, wl.u.astype(np.float32), wl.v.astype(np.float32), wl.q.astype(np.float32), wl.dt))
+    work = [p["n_particles"] * steps for p in params]
+    budget, slots = 8 << 30, 16
+
+    def serve(mode, arrivals):
+        srv = Server(hbm_budget_bytes=budget, max_slots=slots)
         srv.set_mode(mode)
-        tickets = []
+        tickets, done_at = [], {}
         t0 = time.perf_counter()
         i = 0
-        while len(tickets) < len(wls) or any(srv.poll(t)[0] < 2 for t in tickets):
+        while len(done_at) < len(arrivals):
             now = time.perf_counter() - t0
-            while i < len(wls) and params[i]["arrival_s"] * 0.0 <= now:  # all arrive at once, admission paces them
-                w = wls[i]
-                tickets.append(srv.submit(w.L, w.n, w.u.astype(np.float32), w.v.astype(np.float32),
-                                          w.q.astype(np.float32), w.dt, steps))
+            while i < len(arrivals) and arrivals[i] <= now:
+                L, n, u, v, q, dt = wls[i]
+                tickets.append(srv.submit(L, n, u, v, q, dt, steps))
                 i += 1
-            srv.tick()
+            if srv.tick() == 0 and i < len(arrivals):
+                time.sleep(max(0.0, min(0.01, arrivals[i] - (time.perf_counter() - t0))))
+            now = time.perf_counter() - t0
+            for j, t in enumerate(tickets):
+                if j not in done_at and srv.poll(t)[0] in (2, 3):
+                    done_at[j] = now
         wall = time.perf_counter() - t0
         st = srv.stats()
         ok = sum(1 for t in tickets if srv.poll(t)[0] == 2)
-        out["modes"][mode] = {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                              "particle_steps_per_s": st["particle_steps_per_s"],
-                              "wall_particle_steps_per_s": total_ps / wall, "wall_s": wall,
-                              "steps_served": st["steps"], "runs_done": ok}
         srv.close()
-    out["value"] = out["modes"]["batched"]["particle_steps_per_s"]
+        resp = sorted(done_at[j] - arrivals[j] for j in done_at)
+        total = sum(work[:len(arrivals)])
+        return {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "particle_steps_per_s": st["particle_steps_per_s"],
+                "wall_particle_steps_per_s": total / wall, "wall_s": wall, "steps_served": st["steps"],
+                "runs_done": ok, "device_busy": (total / st["particle_steps_per_s"]) / wall
+                if st["particle_steps_per_s"] > 0 else None,
+                "response_p50_s": resp[len(resp) // 2], "response_p99_s": resp[min(len(resp) - 1,
+                                                                                int(0.99 * len(resp)))]}
+
+    # capacity of the batched server: the first runs, all arriving at once
+    ncal = min(len(params), 24)
+    cal = serve("batched", [0.0] * ncal)
+    capacity = cal["wall_particle_steps_per_s"]
+    rate = 0.8 * capacity / (sum(work) / len(work))
+    rng = np.random.default_rng(workloads.SEED_BASE + 5)
+    arrivals = list(np.cumsum(rng.exponential(1.0 / rate, size=len(params))) - 0.0)
+    out = {"metric": "serving: p50/p99 step latency and particle-steps/s", "unit": UNIT, "n_gpus": world,
+           "steps": steps, "runs": len(params), "data": "synthetic (seeded serving mix)",
+           "config": {"workload": f"serving mix: {len(params)} runs (2D Landau n 5..10 / 3D two-stream n 5..7, "
+                                  f"2^16..2^{args.serving_max_log2} FP32 particles, {steps} steps), Poisson "
+                                  f"arrivals at {rate:.2f} runs/s (80% of the batched capacity "
+                                  f"{capacity:.3g} particle-steps/s measured on {ncal} runs arriving at once)",
+                      "budget_bytes": budget, "slots": slots},
+           "modes": {}}
+    for mode in ("batched", "plain"):
+        out["modes"][mode] = serve(mode, arrivals)
+    out["value"] = out["modes"]["batched"]["wall_particle_steps_per_s"]
     out["batched_over_plain"] = (out["modes"]["batched"]["wall_particle_steps_per_s"]
                                  / max(1e-30, out["modes"]["plain"]["wall_particle_steps_per_s"]))
     if rank == 0:
@@ -386,8 +417,8 @@ def main():
                          "16,777,216 particles), diocotron2d (n=9, 8,388,608, Boris), penning3d (n=7, "
                          "2,097,152, Boris + quadrupole field): the paper's other workloads; serving: the "
                          "serving mix")
-    ap.add_argument("--serving-runs", type=int, default=48)
-    ap.add_argument("--serving-max-log2", type=int, default=21)
+    ap.add_argument("--serving-runs", type=int, default=128)
+    ap.add_argument("--serving-max-log2", type=int, default=23)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local, pg = dist_setup(args)

@@ -238,7 +238,10 @@ int sg_pic_kernel_launches(sg_pic* h, unsigned long long* count);
  * sg_pic_set_profiling(h, 1), which replaces graph replay by direct launches
  * with events between the stages while on.  With cap >= 9, entries 6..8
  * report the init-time autotuner: the solve variant in use (0 per-axis
- * passes, 1 one block per grid) and the two timings (ms) it compared. */
+ * passes, 1 one block per grid) and the two timings (ms) it compared; with
+ * cap >= 10 entry 9 is 1 when those timings came from an earlier run of the
+ * same precision, dimension, level and tau in this process (the tuner's
+ * cache), 0 when this run measured them. */
 int sg_pic_set_profiling(sg_pic* h, int on);
 int sg_pic_stage_times(sg_pic* h, double* ms, int cap);
 
@@ -307,12 +310,53 @@ int sg_cell_sort(int precision, int dim, int level, size_t n, const void* const*
 int sg_cell_sort_static(int precision, int dim, int level, size_t n, const void* const* u,
                         uint32_t* keys_sorted, uint32_t* perm, uint32_t* counts, void* stream);
 
+/* ---- sharded runs: one run's particles split over several handles --------
+ * The particles of one run may be divided among several handles (one per
+ * GPU, or several on one GPU), each holding its part.  The regular-grid
+ * density is the only quantity the parts exchange: a step's deposit of each
+ * part (the deposit the paper's Algorithm 2 sums over processes with one
+ * MPI_Allreduce per component grid, Section 4.4) is summed over the parts
+ * into every part's density, after which each part restricts, solves and
+ * combines the same fields redundantly and pushes its own particles.
+ *
+ * sg_pic_init_deferred takes the arguments of sg_pic_init for this part's
+ * particles and stops after depositing them: no field, no backward half
+ * kick.  The caller then sums the densities (sg_pic_density_copy out, a sum
+ * over the parts, sg_pic_density_copy in), sets the whole run's charge with
+ * sg_pic_set_charge_total and calls sg_pic_start, which computes the fields
+ * of the summed density and applies the half kick.  Each step is then
+ * sg_pic_step_deposit, the same exchange, sg_pic_step_fields (sg_pic_step
+ * on such a handle does no exchange).  Adaptive tau is not supported on a
+ * deferred handle (SG_ERR_UNSUPPORTED: the estimator needs the whole run's
+ * particle count).  Diagnostics of a part: the field energy and the grid
+ * charges are the whole run's; the kinetic energy and the count checksum
+ * are the part's own (sum them over the parts).  Calls out of order return
+ * SG_ERR_STATE. */
+int sg_pic_init_deferred(const sg_domain* domain, int level_n, int dim, int shape_order,
+                         const sg_particles* particles, const sg_params* params, sg_pic** out);
+int sg_pic_start(sg_pic* h);
+/* First half of a step: push of this part's particles, the sort when due,
+ * their deposit on the regular grid. */
+int sg_pic_step_deposit(sg_pic* h);
+/* Second half: restriction, component solves and combination (or the filter
+ * mode's field) of the regular-grid density as it stands; completes the step. */
+int sg_pic_step_fields(sg_pic* h);
+/* The whole run's sum_p q_p (FP64): the mean density every solve removes and
+ * the reference of the charge diagnostics.  Defaults to this part's charge. */
+int sg_pic_set_charge_total(sg_pic* h, double q_total);
+/* Copy the regular-grid density (2^{dn} values of the run's precision, x
+ * fastest) between the run and the caller's device buffer of n values:
+ * to_run = 0 out of the run, 1 into it.  Synchronises the run's stream, so
+ * the buffer is ready for (or free after) the caller's own stream. */
+int sg_pic_density_copy(sg_pic* h, void* dev_buf, size_t n, int to_run);
+
 /* ---- serving: independent runs admitted as memory allows -----------------
  * A server keeps many independent runs resident on one GPU and advances all
- * of them together: in batched mode one CUDA graph per tick forks into one
- * branch per resident run (each branch holds that run's own stage kernels,
- * the branches overlap on the device), in plain mode the runs are stepped in
- * turn with direct launches.  Requests are admitted in arrival
+ * of them together: in batched mode a tick launches every resident run's own
+ * cached CUDA graph of one step on the run's own stream (the runs' kernels
+ * overlap on the device; no graph is captured again when runs arrive or
+ * leave), in plain mode the runs are stepped in turn with direct launches
+ * and one solve launch per component grid.  Requests are admitted in arrival
  * order while their estimated device footprint fits hbm_budget_bytes and a
  * slot is free; finished runs retire and free their memory. */
 typedef struct sg_server sg_server;
@@ -331,7 +375,7 @@ typedef struct {
 #define SG_REQ_DONE 2
 #define SG_REQ_FAILED 3
 
-#define SG_SERVE_BATCHED 0 /* one CUDA graph per tick, every resident run a parallel branch */
+#define SG_SERVE_BATCHED 0 /* every resident run's cached step graph, on its own stream */
 #define SG_SERVE_PLAIN 1   /* runs stepped in turn, direct launches, one solve launch per grid */
 
 int sg_serve_create(size_t hbm_budget_bytes, int max_slots, sg_server** out);

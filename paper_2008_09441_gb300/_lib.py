@@ -77,6 +77,13 @@ _SZ = C.c_size_t
 SIGNATURES = {
     "sg_pic_init": (C.c_int, [C.POINTER(sg_domain), C.c_int, C.c_int, C.c_int, C.POINTER(sg_particles),
                               C.POINTER(sg_params), C.POINTER(_P)]),
+    "sg_pic_init_deferred": (C.c_int, [C.POINTER(sg_domain), C.c_int, C.c_int, C.c_int, C.POINTER(sg_particles),
+                                       C.POINTER(sg_params), C.POINTER(_P)]),
+    "sg_pic_start": (C.c_int, [_P]),
+    "sg_pic_step_deposit": (C.c_int, [_P]),
+    "sg_pic_step_fields": (C.c_int, [_P]),
+    "sg_pic_set_charge_total": (C.c_int, [_P, C.c_double]),
+    "sg_pic_density_copy": (C.c_int, [_P, _P, _SZ, C.c_int]),
     "sg_pic_step": (C.c_int, [_P, C.c_int]),
     "sg_pic_diagnostics": (C.c_int, [_P, C.POINTER(sg_diag)]),
     "sg_pic_select_tau": (C.c_int, [_P, C.POINTER(C.c_int), _P, _P, C.c_int]),

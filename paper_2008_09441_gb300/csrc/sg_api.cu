@@ -81,8 +81,8 @@ const char* sg_strerror(int status) {
 
 const char* sg_last_error(void) { return last_error(); }
 
-int sg_pic_init(const sg_domain* domain, int level_n, int dim, int shape_order, const sg_particles* particles,
-                const sg_params* params, sg_pic** out) {
+static int init_run(const sg_domain* domain, int level_n, int dim, int shape_order, const sg_particles* particles,
+                    const sg_params* params, sg_pic** out, bool deferred) {
   if (!out) return invalid("sg_pic_init: out is NULL");
   *out = nullptr;
   if (!domain || !particles || !params) return invalid("sg_pic_init: NULL argument");
@@ -141,6 +141,7 @@ int sg_pic_init(const sg_domain* domain, int level_n, int dim, int shape_order, 
   if (params->combine != SG_COMBINE_FLOAT_FLOAT && params->combine != SG_COMBINE_FP64)
     return invalid("sg_pic_init: combine must be SG_COMBINE_FLOAT_FLOAT or SG_COMBINE_FP64");
   cfg.combine_fp64 = params->combine == SG_COMBINE_FP64;
+  cfg.deferred = deferred;
 
   sg_pic* h = new (std::nothrow) sg_pic;
   if (!h) return SG_ERR_OOM;
@@ -161,6 +162,16 @@ int sg_pic_init(const sg_domain* domain, int level_n, int dim, int shape_order, 
   return SG_OK;
 }
 
+int sg_pic_init(const sg_domain* domain, int level_n, int dim, int shape_order, const sg_particles* particles,
+                const sg_params* params, sg_pic** out) {
+  return init_run(domain, level_n, dim, shape_order, particles, params, out, false);
+}
+
+int sg_pic_init_deferred(const sg_domain* domain, int level_n, int dim, int shape_order,
+                         const sg_particles* particles, const sg_params* params, sg_pic** out) {
+  return init_run(domain, level_n, dim, shape_order, particles, params, out, true);
+}
+
 #define SG_H(h)                                         \
   do {                                                  \
     if (!(h) || !(h)->e) return invalid("NULL handle"); \
@@ -169,6 +180,32 @@ int sg_pic_init(const sg_domain* domain, int level_n, int dim, int shape_order, 
 int sg_pic_step(sg_pic* h, int nsteps) {
   SG_H(h);
   return h->e->step(nsteps);
+}
+
+int sg_pic_start(sg_pic* h) {
+  SG_H(h);
+  return h->e->start();
+}
+
+int sg_pic_step_deposit(sg_pic* h) {
+  SG_H(h);
+  return h->e->step_deposit();
+}
+
+int sg_pic_step_fields(sg_pic* h) {
+  SG_H(h);
+  return h->e->step_fields();
+}
+
+int sg_pic_set_charge_total(sg_pic* h, double q_total) {
+  SG_H(h);
+  return h->e->set_charge_total(q_total);
+}
+
+int sg_pic_density_copy(sg_pic* h, void* dev_buf, size_t n, int to_run) {
+  SG_H(h);
+  if (to_run != 0 && to_run != 1) return invalid("sg_pic_density_copy: to_run must be 0 or 1");
+  return h->e->density_copy(dev_buf, n, to_run);
 }
 
 int sg_pic_diagnostics(sg_pic* h, sg_diag* out) {

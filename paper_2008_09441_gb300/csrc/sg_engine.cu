@@ -3,7 +3,9 @@
 #include <climits>
 #include <cmath>
 #include <map>
+#include <mutex>
 #include <set>
+#include <tuple>
 
 #include "sg_engine.cuh"
 
@@ -36,6 +38,26 @@ std::vector<GridSpec> combination_grids(int d, int n, int tau) {
 }
 
 namespace {
+
+// Process-wide record of the solve-variant timings, by grid set.
+struct TuneKey {
+  int real_bytes, dim, n, tau;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(real_bytes, dim, n, tau) < std::tie(o.real_bytes, o.dim, o.n, o.tau);
+  }
+};
+struct TuneEntry {
+  int mode;
+  float ms[2];
+};
+std::map<TuneKey, TuneEntry>& tune_cache() {
+  static std::map<TuneKey, TuneEntry> m;
+  return m;
+}
+std::mutex& tune_mu() {
+  static std::mutex m;
+  return m;
+}
 
 struct DevBuf {
   void* p = nullptr;
@@ -141,6 +163,17 @@ class Engine final : public EngineBase {
     SG_TRY(build_grid_set(tau_));
     // Initial state: sort, fields at t = 0, backward half kick.
     SG_TRY(enqueue_sort());
+    if (cfg.deferred) {  // the caller sums the density across the run's parts, then start()
+      if (adaptive_) {
+        set_error("sg_pic_init_deferred: adaptive tau needs the whole run's particle count (not supported)");
+        return SG_ERR_UNSUPPORTED;
+      }
+      SG_TRY(enqueue_deposit());
+      SG_CUDA(cudaStreamSynchronize(stream_));
+      phase_ = kAwaitStart;
+      step_ = 0;
+      return check_status();
+    }
     if (adaptive_) {  // Algorithm 1 on the initial density picks the first tau
       SG_TRY(enqueue_deposit());
       int t = tau_;
@@ -180,10 +213,84 @@ class Engine final : public EngineBase {
     return SG_OK;
   }
 
+  // Sharded runs.  start(): the fields of the (summed) regular-grid density
+  // and the backward half kick, completing a deferred init.  step_deposit /
+  // step_fields: the two halves of sg_pic_step around the exchange of the
+  // density (push, sort when due and deposit; restriction, solves,
+  // combination), direct launches.
+  int start() override {
+    if (phase_ != kAwaitStart) {
+      set_error("sg_pic_start: the run was not created by sg_pic_init_deferred, or has started");
+      return SG_ERR_STATE;
+    }
+    SG_TRY(enqueue_restrict_solve_combine());
+    if (!filter_) {
+      SG_TRY(tune_solve());
+      SG_TRY(enqueue_combine(false));
+    }
+    SG_TRY(enqueue_push(-0.5 * cfg_.dt, false, nullptr));
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    phase_ = kReady;
+    return check_status();
+  }
+  int step_deposit() override {
+    if (phase_ != kReady || adaptive_) {
+      set_error(adaptive_ ? "sg_pic_step_deposit: not supported with adaptive tau"
+                          : "sg_pic_step_deposit: the run is not between steps");
+      return adaptive_ ? SG_ERR_UNSUPPORTED : SG_ERR_STATE;
+    }
+    const bool do_sort = ((step_ + 1) % sort_every_) == 0;
+    const unsigned long long l0 = launches_so_far();
+    SG_TRY(enqueue_push(cfg_.dt, true, ke_partials_, do_sort));
+    if (do_sort) SG_TRY(sort_finish());
+    SG_TRY(enqueue_deposit());
+    launches_ += launches_so_far() - l0;
+    phase_ = kHalfStep;
+    return SG_OK;
+  }
+  int step_fields() override {
+    if (phase_ != kHalfStep) {
+      set_error("sg_pic_step_fields: sg_pic_step_deposit must come first");
+      return SG_ERR_STATE;
+    }
+    const unsigned long long l0 = launches_so_far();
+    SG_TRY(enqueue_restrict_solve_combine(ke_partials_));
+    launches_ += launches_so_far() - l0;
+    ++step_;
+    phase_ = kReady;
+    return SG_OK;
+  }
+  int set_charge_total(double q) override {
+    if (!std::isfinite(q)) {
+      set_error("sg_pic_set_charge_total: non-finite charge");
+      return SG_ERR_INVALID;
+    }
+    charge_total_ = q;
+    return SG_OK;
+  }
+  int density_copy(void* dev_buf, size_t n, int to_run) override {
+    if (!dev_buf) {
+      set_error("sg_pic_density_copy: NULL buffer");
+      return SG_ERR_INVALID;
+    }
+    if (n != ND_) return size_error("sg_pic_density_copy");
+    if (to_run)
+      SG_CUDA(cudaMemcpyAsync(rho_reg_, dev_buf, ND_ * sizeof(real), cudaMemcpyDeviceToDevice, stream_));
+    else
+      SG_CUDA(cudaMemcpyAsync(dev_buf, rho_reg_, ND_ * sizeof(real), cudaMemcpyDeviceToDevice, stream_));
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    return SG_OK;
+  }
+
   int step(int nsteps) override {
     if (nsteps < 0) {
       set_error("sg_pic_step: nsteps < 0");
       return SG_ERR_INVALID;
+    }
+    if (phase_ != kReady) {
+      set_error(phase_ == kAwaitStart ? "sg_pic_step: a deferred run needs sg_pic_start first"
+                                      : "sg_pic_step: finish the split step with sg_pic_step_fields first");
+      return SG_ERR_STATE;
     }
     if (profiling_) std::fill(stage_ms_, stage_ms_ + 6, 0.0);
     for (int k = 0; k < nsteps; ++k) {
@@ -558,6 +665,7 @@ class Engine final : public EngineBase {
     SG_CUDA(cudaMemcpyAsync(dd_, &hd.dd, sizeof(DevDiag), cudaMemcpyHostToDevice, stream_));
     SG_CUDA(cudaStreamSynchronize(stream_));
     step_ = hd.step;
+    phase_ = kReady;
     invalidate_graphs();
     return check_status();
   }
@@ -606,6 +714,7 @@ class Engine final : public EngineBase {
     if (cap > 6) ms[6] = solve_mode_;
     if (cap > 7) ms[7] = solve_ms_[0];
     if (cap > 8) ms[8] = solve_ms_[1];
+    if (cap > 9) ms[9] = tuned_from_cache_ ? 1.0 : 0.0;
     return SG_OK;
   }
 
@@ -614,19 +723,7 @@ class Engine final : public EngineBase {
   cudaStream_t stream() const override { return stream_; }
   size_t n_particles() const override { return np_; }
   long long steps_done() const override { return step_; }
-  bool next_step_sorts() const override { return ((step_ + 1) % sort_every_) == 0; }
-  int cur_set() const override { return cur_; }
-  int capture_step(bool do_sort) override {
-    const int cb = cur_;
-    const int st = enqueue_step(do_sort);
-    cur_ = cb;
-    return st;
-  }
-  void commit_step(bool did_sort, unsigned long long kernels) override {
-    if (did_sort) cur_ ^= 1;
-    ++step_;
-    launches_ += kernels;
-  }
+  bool next_step_sorts() const { return ((step_ + 1) % sort_every_) == 0; }
   int step_plain() override {
     const bool do_sort = next_step_sorts();
     const unsigned long long l0 = launches_so_far();
@@ -1119,6 +1216,22 @@ class Engine final : public EngineBase {
       solve_mode_ = force_mode_;
       return SG_OK;
     }
+    // The choice depends only on the grid set and the precision: a run with
+    // the same (precision, d, n, tau) as an earlier one in this process
+    // takes the earlier timing instead of repeating it.
+    const TuneKey key{(int)sizeof(real), D, n_, tau_};
+    {
+      std::lock_guard<std::mutex> lk(tune_mu());
+      auto it = tune_cache().find(key);
+      if (it != tune_cache().end()) {
+        solve_mode_ = it->second.mode;
+        solve_ms_[0] = it->second.ms[0];
+        solve_ms_[1] = it->second.ms[1];
+        tuned_from_cache_ = true;
+        return SG_OK;
+      }
+    }
+    tuned_from_cache_ = false;
     cudaEvent_t e0, e1;
     SG_CUDA(cudaEventCreate(&e0));
     SG_CUDA(cudaEventCreate(&e1));
@@ -1140,6 +1253,8 @@ class Engine final : public EngineBase {
     solve_mode_ = best[1] < best[0] ? 1 : 0;
     solve_ms_[0] = best[0];
     solve_ms_[1] = best[1];
+    std::lock_guard<std::mutex> lk(tune_mu());
+    tune_cache()[key] = TuneEntry{solve_mode_, {best[0], best[1]}};
     return SG_OK;
   }
 
@@ -1285,6 +1400,8 @@ class Engine final : public EngineBase {
   }
 
   // ------------------------------------------------------------ state
+  enum Phase { kReady = 0, kAwaitStart = 1, kHalfStep = 2 };
+  Phase phase_ = kReady;
   EngineConfig cfg_;
   int n_ = 0, N_ = 0;
   size_t ND_ = 0, np_ = 0, S_ = 0;
@@ -1336,6 +1453,7 @@ class Engine final : public EngineBase {
   int solve_mode_ = -1;  // -1 untuned, 0 per-axis passes, 1 one block per grid
   int force_mode_ = -1;  // solve variant fixed by the caller, -1 autotuned
   float solve_ms_[2] = {0, 0};
+  bool tuned_from_cache_ = false;
   GridDesc* grids_dev_ = nullptr;
   double* charges_dev_ = nullptr;
   void* diag_host_ = nullptr;  // pinned staging of the diagnostics read-back

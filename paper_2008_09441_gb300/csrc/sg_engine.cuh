@@ -33,6 +33,7 @@ struct EngineConfig {
   int mode = SG_MODE_COMBINE;
   bool cell = false;  // cell-centred grids (nodes at (k + 1/2) h)
   bool combine_fp64 = false;  // FP32 path: combination accumulated in double (else float-float)
+  bool deferred = false;      // init stops after the deposit; start() computes the fields
   // deposit window capacity in regular nodes with 64-bit accumulators (64 KB;
   // a 128 x 128 window of 32-bit fixed point in 2D, 24^3 in 3D): large enough
   // for a chunk's particles a few steps after a sort
@@ -65,16 +66,14 @@ class EngineBase {
   virtual cudaStream_t stream() const = 0;
   virtual size_t n_particles() const = 0;
   virtual long long steps_done() const = 0;
-  // Batched serving: whether the next step sorts, which particle set is
-  // current, enqueue one step on the run's stream inside a caller's stream
-  // capture (host state unchanged), then commit the host state after the
-  // captured graph ran.
-  virtual bool next_step_sorts() const = 0;
-  virtual int cur_set() const = 0;
-  virtual int capture_step(bool do_sort) = 0;
-  virtual void commit_step(bool did_sort, unsigned long long kernels) = 0;
-  // Plain path: direct launches, one solve launch per component grid.
+  // Plain serving path: direct launches, one solve launch per component grid.
   virtual int step_plain() = 0;
+  // sharded runs (one handle per part of a run's particles)
+  virtual int start() = 0;
+  virtual int step_deposit() = 0;
+  virtual int step_fields() = 0;
+  virtual int set_charge_total(double q) = 0;
+  virtual int density_copy(void* dev_buf, size_t n, int to_run) = 0;
 };
 
 EngineBase* make_engine(int precision, int dim);

@@ -1,13 +1,12 @@
 // Serving: many independent runs resident on one GPU, admitted in arrival
 // order by device-memory footprint, advanced together tick by tick.
 //
-// Batched mode (default): one tick is one CUDA graph that forks from the
-// server's stream into every resident run's stream, enqueues one step of
-// each run there (the runs' kernels overlap on the device) and joins back;
-// graphs are cached per resident set and particle-buffer parity, so a tick is
-// a single graph launch.  Plain mode: each run steps in turn with direct
-// kernel launches and one solve launch per component grid, waiting for each
-// run before the next (the per-grid, per-run launch path).
+// Batched mode (default): a tick forks from the server's stream into every
+// resident run's stream, where the run launches its cached step graph (the
+// runs' kernels overlap on the device), and joins back.  Plain mode: each
+// run steps in turn with direct kernel launches and one solve launch per
+// component grid, each run's step waiting for the previous run's (the
+// per-grid, per-run launch path).
 #include <algorithm>
 #include <cstring>
 #include <deque>
@@ -31,15 +30,9 @@ struct Request {
   EngineBase* eng = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // timing
-  cudaEvent_t join = nullptr;                 // capture dependency (not timed)
   int steps_left = 0;
   sg_diag last{};
   std::vector<char> result_u[3], result_v[3], result_w;
-};
-
-struct CachedGraph {
-  cudaGraphExec_t exec = nullptr;
-  std::vector<unsigned long long> kernels;  // per resident run
 };
 
 }  // namespace
@@ -59,20 +52,13 @@ struct sg_server {
   unsigned long long steps_served = 0;
   cudaStream_t ds = nullptr;
   cudaEvent_t ev_start = nullptr, ev_end = nullptr;  // timing
-  cudaEvent_t fork = nullptr;                        // capture dependency (not timed)
-  std::map<std::string, CachedGraph> graphs;
+  cudaEvent_t fork = nullptr;                        // start of a tick for the runs' streams (not timed)
   std::mutex mu;
 };
 
 static int serr(const char* m, int code = SG_ERR_INVALID) {
   set_error(m);
   return code;
-}
-
-static void clear_graphs(sg_server* s) {
-  for (auto& kv : s->graphs)
-    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-  s->graphs.clear();
 }
 
 static void finish(sg_server* s, Request* r, int state) {
@@ -101,8 +87,6 @@ static void finish(sg_server* s, Request* r, int state) {
   }
   if (r->ev0) cudaEventDestroy(r->ev0);
   if (r->ev1) cudaEventDestroy(r->ev1);
-  if (r->join) cudaEventDestroy(r->join);
-  r->join = nullptr;
   if (r->stream) cudaStreamDestroy(r->stream);
   r->ev0 = r->ev1 = nullptr;
   r->stream = nullptr;
@@ -123,8 +107,7 @@ static int admit(sg_server* s, bool* changed, int* failed) {
     s->in_use += r->footprint;
     *changed = true;
     if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreate(&r->ev0) != cudaSuccess || cudaEventCreate(&r->ev1) != cudaSuccess ||
-        cudaEventCreateWithFlags(&r->join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreate(&r->ev0) != cudaSuccess || cudaEventCreate(&r->ev1) != cudaSuccess) {
       finish(s, r, SG_REQ_FAILED);
       continue;
     }
@@ -171,67 +154,38 @@ static int admit(sg_server* s, bool* changed, int* failed) {
   return SG_OK;
 }
 
-// One graph over every resident run that still has steps to take.
+// One step of every resident run that still has steps to take: each run
+// launches its own cached step graph (captured once per particle-buffer
+// parity and sort phase) on its own stream, all forked from the server's
+// stream and joined back, so the runs' kernels overlap on the device and
+// no graph is captured again when the resident set changes.
 static int tick_batched(sg_server* s, std::vector<Request*>& act) {
-  std::string key;
-  std::vector<bool> sorts(act.size());
-  for (size_t i = 0; i < act.size(); ++i) {
-    sorts[i] = act[i]->eng->next_step_sorts();
-    key += std::to_string(act[i]->ticket) + ":" + std::to_string(act[i]->eng->cur_set()) + (sorts[i] ? "s" : "n") + ";";
+  SG_CUDA(cudaEventRecord(s->ev_start, s->ds));
+  SG_CUDA(cudaEventRecord(s->fork, s->ds));
+  for (Request* r : act) {
+    SG_CUDA(cudaStreamWaitEvent(r->stream, s->fork, 0));
+    SG_TRY(r->eng->step(1));
+    SG_CUDA(cudaEventRecord(r->ev1, r->stream));
+    SG_CUDA(cudaStreamWaitEvent(s->ds, r->ev1, 0));
   }
-  auto it = s->graphs.find(key);
-  if (it == s->graphs.end()) {
-    CachedGraph cg;
-    cudaGraph_t g;
-    SG_CUDA(cudaStreamBeginCapture(s->ds, cudaStreamCaptureModeThreadLocal));
-    int st = SG_OK;
-    // Events recorded during capture are dependency markers only, unless
-    // recorded as external event nodes: the timing events are external, the
-    // fork / join events plain.
-    cudaEventRecordWithFlags(s->ev_start, s->ds, cudaEventRecordExternal);
-    cudaEventRecord(s->fork, s->ds);
-    for (size_t i = 0; i < act.size() && st == SG_OK; ++i) {
-      Request* r = act[i];
-      cudaStreamWaitEvent(r->stream, s->fork, 0);
-      const unsigned long long l0 = launches_so_far();
-      st = r->eng->capture_step(sorts[i]);
-      cg.kernels.push_back(launches_so_far() - l0);
-      cudaEventRecordWithFlags(r->ev1, r->stream, cudaEventRecordExternal);
-      cudaEventRecord(r->join, r->stream);
-      cudaStreamWaitEvent(s->ds, r->join, 0);
-    }
-    cudaEventRecordWithFlags(s->ev_end, s->ds, cudaEventRecordExternal);
-    cudaError_t e = cudaStreamEndCapture(s->ds, &g);
-    if (st != SG_OK) return st;
-    if (e != cudaSuccess) {
-      set_error(std::string("serving graph capture: ") + cudaGetErrorString(e));
-      return SG_ERR_CUDA;
-    }
-    cudaError_t e2 = cudaGraphInstantiate(&cg.exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e2 != cudaSuccess) {
-      set_error(std::string("serving graph instantiate: ") + cudaGetErrorString(e2));
-      return SG_ERR_CUDA;
-    }
-    it = s->graphs.emplace(key, cg).first;
-  }
-  SG_CUDA(cudaGraphLaunch(it->second.exec, s->ds));
-  SG_CUDA(cudaStreamSynchronize(s->ds));
+  SG_CUDA(cudaEventRecord(s->ev_end, s->ds));
+  SG_CUDA(cudaEventSynchronize(s->ev_end));
   float tick_ms = 0;
   SG_CUDA(cudaEventElapsedTime(&tick_ms, s->ev_start, s->ev_end));
   s->device_ms += tick_ms;
-  for (size_t i = 0; i < act.size(); ++i) {
-    Request* r = act[i];
+  for (Request* r : act) {
     float ms = 0;
     SG_CUDA(cudaEventElapsedTime(&ms, s->ev_start, r->ev1));
     s->step_ms.push_back(ms);
-    r->eng->commit_step(sorts[i], it->second.kernels[i]);
   }
   return SG_OK;
 }
 
 // Latency of a run's step is measured from the tick's start in both modes
-// (a request advances one step per tick, whatever the other runs do).
+// (a request advances one step per tick, whatever the other runs do).  The
+// plain mode chains the runs on the device (each run's stream waits for the
+// previous run's step) and synchronises once per tick, like the batched
+// mode, so the two differ in launch structure only.
 static int tick_plain(sg_server* s, std::vector<Request*>& act) {
   SG_CUDA(cudaEventRecord(s->ev_start, s->ds));
   cudaEvent_t last = s->ev_start;
@@ -239,11 +193,13 @@ static int tick_plain(sg_server* s, std::vector<Request*>& act) {
     SG_CUDA(cudaStreamWaitEvent(r->stream, last, 0));
     SG_TRY(r->eng->step_plain());
     SG_CUDA(cudaEventRecord(r->ev1, r->stream));
-    SG_CUDA(cudaEventSynchronize(r->ev1));
+    last = r->ev1;
+  }
+  SG_CUDA(cudaEventSynchronize(last));
+  for (Request* r : act) {
     float ms = 0;
     SG_CUDA(cudaEventElapsedTime(&ms, s->ev_start, r->ev1));
     s->step_ms.push_back(ms);
-    last = r->ev1;
   }
   float tick_ms = 0;
   SG_CUDA(cudaEventElapsedTime(&tick_ms, s->ev_start, last));
@@ -274,7 +230,6 @@ int sg_serve_set_mode(sg_server* s, int mode) {
   if (mode != SG_SERVE_BATCHED && mode != SG_SERVE_PLAIN) return serr("sg_serve_set_mode: unknown mode");
   std::lock_guard<std::mutex> lk(s->mu);
   s->mode = mode;
-  clear_graphs(s);
   return SG_OK;
 }
 
@@ -358,7 +313,7 @@ int sg_serve_tick(sg_server* s, int* active) {
     }
   }
   s->resident.swap(keep);
-  if (changed) clear_graphs(s);
+  (void)changed;
   if (active) *active = (int)s->resident.size();
   return tick_status != SG_OK ? tick_status : admit_failed;
 }
@@ -415,7 +370,6 @@ int sg_serve_stats(sg_server* s, double* p50_ms, double* p99_ms, double* particl
 
 void sg_serve_destroy(sg_server* s) {
   if (!s) return;
-  clear_graphs(s);
   for (Request* r : s->resident) finish(s, r, SG_REQ_FAILED);
   for (auto& kv : s->all) delete kv.second;
   if (s->ev_start) cudaEventDestroy(s->ev_start);

@@ -168,7 +168,7 @@ class Run:
 
     def __init__(self, L_box, n, u, v, w, dt, *, tau=1, qm=-1.0, precision="fp32", B=(0.0, 0.0, 0.0),
                  eext_lin=(0.0, 0.0, 0.0), alpha=0.01, pc_ref=5.0, tau_constants="paper", sort_every=0,
-                 stream=None, mode="combine", centring="node", combine="float-float"):
+                 stream=None, mode="combine", centring="node", combine="float-float", deferred=False):
         self.d = len(L_box)
         self.n = n
         self.precision = L.SG_FP32 if precision in ("fp32", L.SG_FP32) else L.SG_FP64
@@ -194,7 +194,13 @@ class Run:
         self.params = make_params(self.precision, tau, dt, qm, B, eext_lin, alpha, pc_ref, tc, sort_every,
                                   stream, mode, centring, combine)
         self._keep = (ucols, vcols, wcol)
-        self.h = sg_pic_init(dom, n, d, 1, parts, self.params)
+        if deferred:  # a part of a sharded run: sg_pic_start after the density exchange
+            h = C.c_void_p()
+            check(lib().sg_pic_init_deferred(C.byref(dom), n, d, 1, C.byref(parts), C.byref(self.params),
+                                             C.byref(h)), "sg_pic_init_deferred")
+            self.h = h
+        else:
+            self.h = sg_pic_init(dom, n, d, 1, parts, self.params)
         self._keep = None
 
     def close(self):
@@ -331,10 +337,29 @@ class Run:
 
     def tuning(self):
         """Init-time autotuner record: solve variant and the compared timings (ms)."""
-        ms = np.zeros(9)
-        check(lib().sg_pic_stage_times(self.h, ms.ctypes.data, 9), "sg_pic_stage_times")
+        ms = np.zeros(10)
+        check(lib().sg_pic_stage_times(self.h, ms.ctypes.data, 10), "sg_pic_stage_times")
         return {"solve_variant": "one-block-per-grid" if ms[6] == 1 else "per-axis-passes",
-                "passes_ms": float(ms[7]), "one_block_ms": float(ms[8])}
+                "passes_ms": float(ms[7]), "one_block_ms": float(ms[8]), "from_cache": bool(ms[9])}
+
+    # ---- sharded runs (sg_pic_init_deferred / sg_pic_start / the split step)
+    def start(self):
+        check(lib().sg_pic_start(self.h), "sg_pic_start")
+
+    def step_deposit(self):
+        check(lib().sg_pic_step_deposit(self.h), "sg_pic_step_deposit")
+
+    def step_fields(self):
+        check(lib().sg_pic_step_fields(self.h), "sg_pic_step_fields")
+
+    def set_charge_total(self, q_total):
+        check(lib().sg_pic_set_charge_total(self.h, float(q_total)), "sg_pic_set_charge_total")
+
+    def density_copy(self, buf, to_run):
+        """Copy the regular-grid density into (to_run=False: out of the run) or
+        from a torch CUDA tensor of 2^{dn} values of the run's precision."""
+        check(lib().sg_pic_density_copy(self.h, C.c_void_p(buf.data_ptr()), int(buf.numel()), 1 if to_run else 0),
+              "sg_pic_density_copy")
 
     def device_particles(self):
         o = L.sg_particles_out()

@@ -117,3 +117,43 @@ def test_modes_and_centrings_in_one_mix():
         assert nrmse(vm, va) < 1e-5, (mode, cen)
         run.close()
     srv.close()
+
+
+@pytest.mark.parametrize("mode", ["batched", "plain"])
+def test_served_runs_match_oracle(mode):
+    """Runs served together (Poisson-style staggered submission, budget for
+    two at a time) against the FP64 oracle advanced alone: particle state
+    and field energy within the FP32 tolerance, in either serving mode."""
+    from oracle import sgpic_oracle as O
+    from paper_2008_09441_gb300.sgpic import Server
+    params = [dict(dim=2, n=6, n_particles=12000, amplitude=0.05, k=0.5, seed=11, steps=5),
+              dict(dim=3, n=4, n_particles=6000, amplitude=0.02, k=0.4, seed=12, steps=4),
+              dict(dim=2, n=7, n_particles=9000, amplitude=0.1, k=0.3, seed=13, steps=6)]
+    wls = [workloads.serving_run_workload(p) for p in params]
+    srv = Server(hbm_budget_bytes=1 << 30, max_slots=2)
+    srv.set_mode(mode)
+    tickets = []
+    for i in range(200):
+        if len(tickets) < len(wls) and i % 2 == 0:  # a new request every second tick
+            wl = wls[len(tickets)]
+            tickets.append(srv.submit(wl.L, wl.n, wl.u.astype(np.float32), wl.v.astype(np.float32),
+                                      wl.q.astype(np.float32), wl.dt, params[len(tickets)]["steps"]))
+        srv.tick()
+        if len(tickets) == len(wls) and all(srv.poll(t)[0] in (2, 3) for t in tickets):
+            break
+    for t, p, wl in zip(tickets, params, wls):
+        st, diag = srv.poll(t)
+        assert st == 2 and diag["step"] == p["steps"], (t, st)
+        um, vm, _ = srv.result(t)
+        u64 = wl.u.astype(np.float32).astype(np.float64)
+        v64 = wl.v.astype(np.float32).astype(np.float64)
+        q64 = wl.q.astype(np.float32).astype(np.float64)
+        ref = O.OracleRun(wl.L, wl.n, u64, v64, q64, wl.dt, qm=wl.qm, tau=wl.tau)
+        ref.step(p["steps"])
+        du = um.astype(np.float64) - ref.u
+        du -= np.round(du)
+        assert np.sqrt(np.sum(du ** 2) / np.sum(ref.u ** 2)) < 1e-5
+        assert nrmse(vm, ref.velocities()) < 1e-5
+        fe = ref.diagnostics()["field_energy"]
+        assert abs(diag["field_energy"] - fe) <= 1e-5 * abs(fe)
+    srv.close()
