@@ -387,6 +387,88 @@ def run_serving(args, world, rank, local):
         print(json.dumps(out))
 
 
+def run_diocotron_paper(args, world, rank, local):
+    """The paper's Section 5.1 experiment on the GPU: the 2D diocotron
+    instability (Gaussian or uniform weighted sampling) with tau chosen by
+    Algorithm 1 every step, against regular PIC (tau = n) at the same
+    particles per cell and fixed tau in Algorithm 1's range; the error of
+    the charge density and of the field (eq. error_def, NRMSE over the
+    regular nodes) at eight instants of [0, T] against the mean of an
+    ensemble of regular-PIC runs with more particles per cell, and the tau
+    history of the adaptive run."""
+    import torch
+    from paper_2008_09441_gb300 import Run, workloads
+    from paper_2008_09441_gb300._lib import SG_TAU_ADAPTIVE
+    torch.cuda.set_device(local)
+    n, pc, smp = args.dio_n, args.dio_pc, args.dio_sampling
+    steps = args.dio_steps
+    wl = workloads.diocotron_paper(n=n, pc=pc, sampling=smp, steps=steps)
+    marks = sorted(set(int(round(k * steps / 7)) for k in range(8)))
+    kw = dict(precision="fp32", mode=args.mode, centring=args.centring, B=wl.B, alpha=wl.extra["alpha"],
+              pc_ref=wl.extra["pc_ref"])
+
+    def trajectory(w, tau, history=False):
+        t0 = time.perf_counter()
+        run = Run(w.L, w.n, w.u.astype(np.float32), w.v.astype(np.float32), w.q.astype(np.float32), w.dt, tau=tau,
+                  **kw)
+        rho, E, taus = {}, {}, []
+        done = 0
+        for m in marks:
+            if history:
+                for _ in range(m - done):
+                    run.step(1)
+                    taus.append(run.diagnostics()["tau"])
+            else:
+                run.step(m - done)
+            done = m
+            rho[m] = run.density()
+            E[m] = run.field()
+        run.close()
+        return rho, E, taus, time.perf_counter() - t0
+
+    def nrmse(a, ref):
+        return float(np.sqrt(np.sum((a - ref) ** 2) / np.sum(ref * ref)))
+
+    # reference: mean over an ensemble of regular-PIC runs (tau = n) with more particles per cell
+    ref_rho = {m: 0.0 for m in marks}
+    ref_E = {m: 0.0 for m in marks}
+    t_ref = 0.0
+    for i in range(args.dio_ensemble):
+        w = workloads.diocotron_paper(n=n, pc=args.dio_pc_ref, sampling=smp, steps=steps,
+                                      seed=workloads.SEED_BASE + 600 + i)
+        r, e, _, t = trajectory(w, n)
+        t_ref += t
+        for m in marks:
+            ref_rho[m] = ref_rho[m] + r[m] / args.dio_ensemble
+            ref_E[m] = ref_E[m] + e[m] / args.dio_ensemble
+    runs = {"adaptive": SG_TAU_ADAPTIVE, "regular": n}
+    for t in range(1, n - 2):
+        runs[f"tau={t}"] = t
+    out_runs = {}
+    for name, tau in runs.items():
+        r, e, taus, t = trajectory(wl, tau, history=(name == "adaptive"))
+        out_runs[name] = {"rho_error": [nrmse(r[m], ref_rho[m]) for m in marks],
+                          "E_error": [nrmse(e[m], ref_E[m]) for m in marks], "seconds": t}
+        if taus:
+            hist = {}
+            for x in taus:
+                hist[x] = hist.get(x, 0) + 1
+            changes = [(i + 1, taus[i]) for i in range(len(taus)) if i == 0 or taus[i] != taus[i - 1]]
+            out_runs[name]["tau_histogram"] = {str(k): v for k, v in sorted(hist.items())}
+            out_runs[name]["tau_changes"] = changes[:200]
+    out = {"metric": "diocotron (Section 5.1): NRMSE of rho and E against a regular-PIC ensemble mean",
+           "config": {"workload": f"diocotron_paper n={n} ({1 << n}^2), P_c={pc}, {smp} sampling, "
+                                  f"{wl.n_particles} FP32 particles, dt={wl.dt}, {steps} steps (T={steps * wl.dt:g})",
+                      "mode": args.mode, "centring": args.centring, "alpha": wl.extra["alpha"],
+                      "pc_ref": wl.extra["pc_ref"],
+                      "reference": f"mean of {args.dio_ensemble} regular-PIC runs (tau = n), P_c = {args.dio_pc_ref}, "
+                                   "same mesh, independent seeds",
+                      "instants_t": [m * wl.dt for m in marks]},
+           "runs": out_runs, "reference_seconds": t_ref, "data": "synthetic (seeded)"}
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -412,11 +494,17 @@ def main():
     ap.add_argument("--ref-budget-s", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="landau", choices=list(WORKLOAD_NAMES) + ["serving"],
+    ap.add_argument("--workload", default="landau", choices=list(WORKLOAD_NAMES) + ["serving", "diocotron-paper"],
                     help="landau: the 2D n=10 Landau run (the default line); twostream3d (3D, n=7, "
                          "16,777,216 particles), diocotron2d (n=9, 8,388,608, Boris), penning3d (n=7, "
                          "2,097,152, Boris + quadrupole field): the paper's other workloads; serving: the "
                          "serving mix")
+    ap.add_argument("--dio-n", type=int, default=9, help="diocotron-paper: level n (mesh 2^n x 2^n)")
+    ap.add_argument("--dio-pc", type=int, default=5, help="diocotron-paper: particles per cell")
+    ap.add_argument("--dio-sampling", default="gauss", choices=["gauss", "uniform"])
+    ap.add_argument("--dio-steps", type=int, default=875, help="diocotron-paper: steps (875 = T 17.5)")
+    ap.add_argument("--dio-ensemble", type=int, default=4, help="diocotron-paper: regular-PIC reference runs")
+    ap.add_argument("--dio-pc-ref", type=int, default=80, help="diocotron-paper: particles per cell of the reference")
     ap.add_argument("--serving-runs", type=int, default=128)
     ap.add_argument("--serving-max-log2", type=int, default=23)
     args = ap.parse_args()
@@ -424,6 +512,9 @@ def main():
     world, rank, local, pg = dist_setup(args)
     if args.workload == "serving":
         run_serving(args, world, rank, local)
+        return
+    if args.workload == "diocotron-paper":
+        run_diocotron_paper(args, world, rank, local)
         return
     if args.impl == "reference":
         run_reference(args, world, rank, pg)

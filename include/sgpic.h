@@ -210,6 +210,13 @@ int sg_pic_get_grid_field(sg_pic* h, double* E, size_t cap);
  * deposit used by Algorithm 1), FP64 host buffer of 2^(d n) values. */
 int sg_pic_get_regular_charge(sg_pic* h, double* rho, size_t cap);
 
+/* The charge density the field comes from, on the regular nodes (FP64 host
+ * buffer of 2^(d n) values): sum_i c_i P_i rho_i, the sparse-grid density of
+ * eq. sparse_filter (Section 4.1) -- in SG_MODE_FILTER the filtered density
+ * its regular-grid solve used, in SG_MODE_COMBINE the same combination of
+ * the component densities (whose fields the run combines). */
+int sg_pic_get_density(sg_pic* h, double* rho, size_t cap);
+
 /* Grid set in use: *n_grids receives the count; levels (3 ints per grid,
  * unused axes 0) and coeffs receive up to cap grids. */
 int sg_pic_get_grids(sg_pic* h, int* n_grids, int* levels, int* coeffs, int cap);

@@ -94,6 +94,7 @@ SIGNATURES = {
     "sg_pic_get_grid_charge": (C.c_int, [_P, _P, _SZ]),
     "sg_pic_get_grid_field": (C.c_int, [_P, _P, _SZ]),
     "sg_pic_get_regular_charge": (C.c_int, [_P, _P, _SZ]),
+    "sg_pic_get_density": (C.c_int, [_P, _P, _SZ]),
     "sg_pic_get_grids": (C.c_int, [_P, C.POINTER(C.c_int), _P, _P, C.c_int]),
     "sg_pic_save": (C.c_int, [_P, _P, C.POINTER(_SZ)]),
     "sg_pic_load": (C.c_int, [_P, _P, _SZ]),

@@ -260,6 +260,12 @@ int sg_pic_get_regular_charge(sg_pic* h, double* rho, size_t cap) {
   return h->e->get_regular_charge(rho, cap);
 }
 
+int sg_pic_get_density(sg_pic* h, double* rho, size_t cap) {
+  SG_H(h);
+  if (!rho) return invalid("sg_pic_get_density: NULL buffer");
+  return h->e->get_density(rho, cap);
+}
+
 int sg_pic_get_grids(sg_pic* h, int* n_grids, int* levels, int* coeffs, int cap) {
   SG_H(h);
   return h->e->get_grids(n_grids, levels, coeffs, cap);

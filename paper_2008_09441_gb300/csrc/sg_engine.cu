@@ -574,6 +574,23 @@ class Engine final : public EngineBase {
     return copy_to_host_double(rho_reg_, rho, ND_);
   }
 
+  // The density the field comes from, on the regular nodes: the combination
+  // sum_i c_i P_i rho_i of the component densities (eq. sparse_filter; in
+  // the filter mode the density its regular-grid solve used).
+  int get_density(double* rho, size_t cap) override {
+    if (cap < ND_) return size_error("sg_pic_get_density");
+    if (filter_) return copy_to_host_double(rho_f_, rho, ND_);
+    real* tmp = nullptr;
+    SG_TRY(alloc((void**)&tmp, ND_ * sizeof(real)));
+    CombineFinal off;
+    std::memset(&off, 0, sizeof(off));
+    int st = launch_combine<real, D>(grids_dev_, levels_, lmin_, rho_arena_, S_, n_, tmp, nullptr, fe_partials_, off,
+                                     stream_, 1, cfg_.cell, cfg_.combine_fp64);
+    if (st == SG_OK) st = copy_to_host_double(tmp, rho, ND_);
+    free_one(tmp);
+    return st;
+  }
+
   int get_grids(int* n_grids, int* levels, int* coeffs, int cap) override {
     if (n_grids) *n_grids = ngrids_;
     for (int g = 0; g < ngrids_ && g < cap; ++g) {

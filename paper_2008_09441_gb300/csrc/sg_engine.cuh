@@ -54,6 +54,7 @@ class EngineBase {
   virtual int get_grid_charge(double* rho, size_t cap) = 0;
   virtual int get_grid_field(double* E, size_t cap) = 0;
   virtual int get_regular_charge(double* rho, size_t cap) = 0;
+  virtual int get_density(double* rho, size_t cap) = 0;
   virtual int get_grids(int* n_grids, int* levels, int* coeffs, int cap) = 0;
   virtual int save(void* buf, size_t* size) = 0;
   virtual int load(const void* buf, size_t size) = 0;

@@ -281,6 +281,13 @@ class Run:
         check(lib().sg_pic_get_regular_charge(self.h, e.ctypes.data, e.size), "sg_pic_get_regular_charge")
         return _flat_to_axes(e[None], [self.n] * self.d)[0]
 
+    def density(self):
+        """sum_i c_i P_i rho_i on the regular nodes (the filter mode's rho_f), indexed [i_1, .., i_d]."""
+        N = 1 << self.n
+        e = np.empty(N ** self.d)
+        check(lib().sg_pic_get_density(self.h, e.ctypes.data, e.size), "sg_pic_get_density")
+        return _flat_to_axes(e[None], [self.n] * self.d)[0]
+
     def grid_charges(self):
         """{levels: rho array indexed [i_1, .., i_d]} of the component grids."""
         gs = self.grids()

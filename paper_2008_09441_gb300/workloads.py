@@ -26,6 +26,16 @@ dataset is involved):
   standard deviations (0.15, 0.05, 0.2) L (wrapped into the box), v ~ N(0, 1)
   per axis, total charge -1562.5 shared equally, dt = 0.05; the paper's
   estimator settings are (P_c)_ref = 1 and alpha = 0.005.
+* ``diocotron_paper`` - the paper's 2D diocotron instability (Section 5.1):
+  periodic [0, 22]^2, B = (0, 0, 5), no external E, total electron charge
+  -400, dt = 0.02, T = 17.5; hollow profile
+  f ~ exp(-|v|^2/2) exp(-(r - L/4)^2 / (2 (0.03 L)^2)) about the box
+  centre.  ``sampling="gauss"``: r ~ N(L/4, 0.03 L), theta uniform,
+  v ~ N(0, 1) per axis, equal charges; estimator settings (P_c)_ref = 5,
+  alpha = 0.01.  ``sampling="uniform"``: x uniform in the box, v uniform in
+  [-6, 6]^2, each particle's charge proportional to f at its phase-space
+  point (normalised to the total charge), particles whose charge is below
+  1e-9 in magnitude dropped; alpha = 0.03.  N_p = P_c 2^(2n) draws.
 * ``serving_mix`` - parameters of independent runs (dimension, level,
   particle count, amplitude, wavenumber, arrival time).
 """
@@ -112,6 +122,36 @@ def diocotron2d(n_particles=1 << 23, n=9, tau=1, r_in=0.3, r_out=0.4, amplitude=
     v = np.stack([Ey / Bz, -Ex / Bz], axis=1)  # E x B / B^2 with B = Bz z
     return Workload("diocotron2d", 2, (L, L), n, tau, u, v, q, dt, B=(0.0, 0.0, Bz), steps=steps,
                     extra={"mode": mode, "amplitude": amplitude})
+
+
+def diocotron_paper(n=9, pc=5, sampling="gauss", tau=1, Q=-400.0, Bz=5.0, dt=0.02, steps=875, seed=None):
+    rng = np.random.default_rng(SEED_BASE + 6 if seed is None else seed)
+    L = 22.0
+    npart = int(pc) << (2 * n)
+    r0, sr = 0.25 * L, 0.03 * L
+    if sampling == "gauss":
+        r = rng.normal(r0, sr, npart)
+        th = rng.uniform(0.0, 2.0 * math.pi, npart)
+        x = np.stack([0.5 * L + r * np.cos(th), 0.5 * L + r * np.sin(th)], axis=1)
+        v = rng.normal(0.0, 1.0, (npart, 2))
+        q = np.full(npart, Q / npart)
+        alpha = 0.01
+    elif sampling == "uniform":
+        x = rng.uniform(0.0, L, (npart, 2))
+        v = rng.uniform(-6.0, 6.0, (npart, 2))
+        r = np.hypot(x[:, 0] - 0.5 * L, x[:, 1] - 0.5 * L)
+        f = np.exp(-0.5 * np.sum(v * v, axis=1)) * np.exp(-((r - r0) ** 2) / (2.0 * sr * sr))
+        q = Q * f / np.sum(f)
+        keep = np.abs(q) >= 1e-9
+        x, v, q = x[keep], v[keep], q[keep] * (Q / np.sum(q[keep]))
+        alpha = 0.03
+    else:
+        raise ValueError("sampling must be 'gauss' or 'uniform'")
+    u = x / L
+    u = u - np.floor(u)
+    u[u >= 1.0] = 0.0
+    return Workload("diocotron_paper", 2, (L, L), n, tau, u, v, q, dt, B=(0.0, 0.0, Bz), steps=steps,
+                    extra={"alpha": alpha, "pc_ref": 5.0, "sampling": sampling, "pc": pc})
 
 
 def penning3d(n_particles=1 << 21, n=7, tau=1, Q=-1562.5, Bz=5.0, dt=0.05, steps=300, seed=None):
