@@ -267,16 +267,21 @@ __device__ void fft_axis_inplace(cplx<real>* buf, const int* logs, int S, int ax
   }
   __syncthreads();
   const int halfN = len >> 1;
+  // Butterfly j of a stage: consecutive j take consecutive inner indices
+  // (the axes below ax, contiguous in the buffer), then the butterflies of
+  // one line, then the outer lines, so that a warp's accesses are
+  // contiguous along every axis (the line itself strides by 2^ls).
   for (int s = 1; s <= logn; ++s) {
     const int half = 1 << (s - 1);
     const int tshift = log_nmax - s;
     for (int j = threadIdx.x; j < (S >> 1); j += blockDim.x) {
-      const int L = j >> (logn - 1);
-      const int jj = j & (halfN - 1);
-      const int pos = jj & (half - 1);
-      const int grp = jj >> (s - 1);
+      const int i = j & smask;
+      const int p = (j >> ls) & (halfN - 1);
+      const int o = j >> (ls + logn - 1);
+      const int pos = p & (half - 1);
+      const int grp = p >> (s - 1);
       const int t0 = grp * 2 * half + pos;
-      const int i0 = (L & smask) + ((t0 + ((L >> ls) << logn)) << ls);
+      const int i0 = (((o << logn) + t0) << ls) + i;
       const int i1 = i0 + (half << ls);
       cplx<real> w = tw[pos << tshift];
       if (inverse) w.y = -w.y;
@@ -308,34 +313,53 @@ __global__ void __launch_bounds__(1024) k_solve_small(SolveArena<real> a, int ma
   for (int ax = 0; ax < D; ++ax) fft_axis_inplace<real>(A, logs, S, ax, false, tws, a.log_nmax);
   const real norm = (real)1 / (real)S;
   const int n0 = 1 << logs[0], n1 = 1 << logs[1];
-  for (int m = 0; m < D; ++m) {
+  // Field components in pairs: B = E^_a + i E^_b, one inverse transform,
+  // E_a its real part and E_b its imaginary part (both fields are real).
+  for (int pr = 0; 2 * pr < D; ++pr) {
+    const int ma = 2 * pr, mb = 2 * pr + 1;
     for (int e = threadIdx.x; e < S; e += blockDim.x) {
       int idx[3];
       idx[0] = e & (n0 - 1);
       idx[1] = (e >> logs[0]) & (n1 - 1);
       idx[2] = D == 3 ? (e >> (logs[0] + logs[1])) : 0;
-      real k2 = 0, km = 0;
-      bool nyq_m = false;
+      real k2 = 0, ka = 0, kb = 0;
+      bool nyq_a = false, nyq_b = false;
       for (int q = 0; q < D; ++q) {
         const int Nq = 1 << logs[q];
         const real kq = (real)g.kfac[q] * (real)sfreq(idx[q], Nq);
         k2 += kq * kq;
-        if (q == m) {
-          km = kq;
-          nyq_m = idx[q] == (Nq >> 1);
+        if (q == ma) {
+          ka = kq;
+          nyq_a = idx[q] == (Nq >> 1);
+        }
+        if (q == mb) {
+          kb = kq;
+          nyq_b = idx[q] == (Nq >> 1);
         }
       }
       const cplx<real> r = A[e];
-      if (k2 == (real)0 || nyq_m) {
-        B[e] = {(real)0, (real)0};
-      } else {
-        const real fac = km / k2 * norm;
-        B[e] = {r.y * fac, -r.x * fac};
+      cplx<real> out = {(real)0, (real)0};
+      if (k2 != (real)0) {
+        const real inv = norm / k2;
+        if (!nyq_a) {  // E^_a = -i k_a rho^ / |k|^2
+          const real fa = ka * inv;
+          out.x += r.y * fa;
+          out.y -= r.x * fa;
+        }
+        if (mb < D && !nyq_b) {  // + i E^_b
+          const real fb = kb * inv;
+          out.x += r.x * fb;
+          out.y += r.y * fb;
+        }
       }
+      B[e] = out;
     }
     __syncthreads();
     for (int ax = 0; ax < D; ++ax) fft_axis_inplace<real>(B, logs, S, ax, true, tws, a.log_nmax);
-    for (int e = threadIdx.x; e < S; e += blockDim.x) a.E[(size_t)m * a.S + g.offset + e] = B[e].x;
+    for (int e = threadIdx.x; e < S; e += blockDim.x) {
+      a.E[(size_t)ma * a.S + g.offset + e] = B[e].x;
+      if (mb < D) a.E[(size_t)mb * a.S + g.offset + e] = B[e].y;
+    }
     __syncthreads();
   }
 }

@@ -76,3 +76,59 @@ def test_two_real_components_share_one_inverse():
     np.testing.assert_allclose(both.real, np.real(np.fft.ifft2(Ea)), rtol=0, atol=1e-12)
     np.testing.assert_allclose(both.imag, np.real(np.fft.ifft2(Eb)), rtol=0, atol=1e-12)
     assert np.max(np.abs(np.imag(np.fft.ifft2(Ea)))) < 1e-12  # each alone is real
+
+
+def _bitrev(t, logn):
+    r = 0
+    for b in range(logn):
+        r |= ((t >> b) & 1) << (logn - 1 - b)
+    return r
+
+
+def inplace_axis_fft(buf, logs, ax, inverse, log_nmax):
+    """The one-block solve's in-place transform of a flat grid (x fastest)
+    along axis ax, restated: bit-reversal swap along the axis, then radix-2
+    stages whose butterfly j takes inner index j mod 2^ls (the axes below
+    ax), butterfly p = (j >> ls) mod 2^(logn-1) of its line and outer line
+    o = j >> (ls + logn - 1); twiddle exp(-+2 pi i pos 2^(log_nmax - s) / Nmax)."""
+    S = buf.size
+    logn = logs[ax]
+    ls = sum(logs[:ax])
+    length = 1 << logn
+    for e in range(S):
+        t = (e >> ls) & (length - 1)
+        r = _bitrev(t, logn)
+        if r > t:
+            e2 = e + ((r - t) << ls)
+            buf[e], buf[e2] = buf[e2], buf[e]
+    nmax = 1 << log_nmax
+    half_n = length >> 1
+    for s in range(1, logn + 1):
+        half = 1 << (s - 1)
+        for j in range(S >> 1):
+            i = j & ((1 << ls) - 1)
+            p = (j >> ls) & (half_n - 1) if half_n > 0 else 0
+            o = j >> (ls + logn - 1)
+            pos = p & (half - 1)
+            grp = p >> (s - 1)
+            t0 = grp * 2 * half + pos
+            i0 = (((o << logn) + t0) << ls) + i
+            i1 = i0 + (half << ls)
+            w = np.exp(-2j * np.pi * (pos << (log_nmax - s)) / nmax)
+            if inverse:
+                w = np.conj(w)
+            x0, x1 = buf[i0], buf[i1] * w
+            buf[i0], buf[i1] = x0 + x1, x0 - x1
+
+
+@pytest.mark.parametrize("logs", [(3, 2), (1, 4), (2, 1, 3), (4, 1, 1)])
+def test_one_block_axis_mapping_equals_numpy_fft(logs):
+    rng = np.random.default_rng(sum(logs))
+    shape = tuple(1 << l for l in reversed(logs))  # numpy order [.., i_2, i_1] for an x-fastest flat array
+    x = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+    for inverse in (False, True):
+        buf = x.ravel().copy()
+        for ax in range(len(logs)):
+            inplace_axis_fft(buf, list(logs), ax, inverse, max(logs))
+        ref = np.fft.fftn(x) if not inverse else np.fft.ifftn(x) * x.size
+        np.testing.assert_allclose(buf.reshape(shape), ref, atol=1e-9)
