@@ -146,7 +146,7 @@ __global__ void k_max_abs(const real* __restrict__ x, size_t n, unsigned long lo
 template <typename real>
 int max_abs_host(const real* x, size_t n, double* out, cudaStream_t s) {
   unsigned long long* d = nullptr;
-  SG_CUDA(cudaMalloc((void**)&d, sizeof(unsigned long long)));
+  SG_CUDA(cudaMallocAsync((void**)&d, sizeof(unsigned long long), s));
   int st = SG_OK;
   unsigned long long h = 0;
   if (cudaMemsetAsync(d, 0, sizeof(h), s) != cudaSuccess) st = SG_ERR_CUDA;
@@ -156,8 +156,8 @@ int max_abs_host(const real* x, size_t n, double* out, cudaStream_t s) {
     count_launch();
   }
   if (st == SG_OK && cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) st = SG_ERR_CUDA;
+  cudaFreeAsync(d, s);
   if (st == SG_OK && cudaStreamSynchronize(s) != cudaSuccess) st = SG_ERR_CUDA;
-  cudaFree(d);
   if (st != SG_OK) {
     set_error("max_abs: CUDA error");
     return st;

@@ -755,23 +755,42 @@ class Engine final : public EngineBase {
 
  private:
   // ------------------------------------------------------------ memory
+  // Device memory comes from the stream-ordered allocator on the run's
+  // stream: freeing does not synchronise the device (a server retiring one
+  // run does not stall the others), and the device's pool keeps freed
+  // memory for the next run instead of returning it to the driver.
   int alloc(void** p, size_t bytes) {
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
+    keep_pool_memory();
+    cudaError_t e = cudaMallocAsync(p, bytes, stream_);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+      set_error(std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
       return SG_ERR_OOM;
     }
     bufs_.push_back({*p, bytes});
     bytes_ += bytes;
     return SG_OK;
   }
+  // Once per device in the process: the default pool keeps up to 16 GB of
+  // freed memory for reuse (process-local, released at exit).
+  static void keep_pool_memory() {
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      unsigned long long keep = 16ull << 30;  // the attribute is a 64-bit unsigned value
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+  }
   void free_one(void* p) {
     if (!p) return;
     for (size_t i = 0; i < bufs_.size(); ++i)
       if (bufs_[i].p == p) {
-        cudaFree(p);
+        cudaFreeAsync(p, stream_);
         bytes_ -= bufs_[i].bytes;
         bufs_.erase(bufs_.begin() + i);
         return;
@@ -780,7 +799,8 @@ class Engine final : public EngineBase {
   void release() {
     invalidate_graphs();
     if (stream_) cudaStreamSynchronize(stream_);
-    for (auto& b : bufs_) cudaFree(b.p);
+    for (auto& b : bufs_) cudaFreeAsync(b.p, stream_);
+    if (stream_) cudaStreamSynchronize(stream_);
     bufs_.clear();
     if (diag_host_) cudaFreeHost(diag_host_);
     diag_host_ = nullptr;
