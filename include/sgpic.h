@@ -166,6 +166,22 @@ int sg_pic_step(sg_pic* h, int nsteps);
 /* Synchronise the run's stream and return its FP64 diagnostics. */
 int sg_pic_diagnostics(sg_pic* h, sg_diag* out);
 
+/* Pipelined diagnostics, for monitoring a run without stalling its stream.
+ * sg_pic_diagnostics_post enqueues on the run's stream the read-back of the
+ * FP64 diagnostics as they stand after every step launched so far, into one
+ * of SG_DIAG_RING pinned host slots owned by the run, and returns without
+ * waiting.  sg_pic_diagnostics_collect waits for the OLDEST posted record and
+ * returns it: the values sg_pic_diagnostics would have returned at that post
+ * (step, tau and grid set included, even if sg_pic_set_tau changed them since).
+ * Errors: post with SG_DIAG_RING records pending, or collect with none, gives
+ * SG_ERR_STATE; collect gives SG_ERR_NONFINITE (with *out filled) when the
+ * record saw a non-finite particle state.  sg_pic_destroy drops records
+ * left pending.  sg_pic_diagnostics may be called in between; it does not
+ * touch the slots. */
+#define SG_DIAG_RING 4
+int sg_pic_diagnostics_post(sg_pic* h);
+int sg_pic_diagnostics_collect(sg_pic* h, sg_diag* out);
+
 /* Algorithm 1 (tauEstimator, Section 4.3.3) on the current regular-grid
  * density: FFT, hard threshold (eq. denoising) with
  * eps = alpha sqrt(pc_ref / P_c) max|rho^|, constants (params.tau_constants),

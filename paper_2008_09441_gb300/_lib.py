@@ -33,6 +33,7 @@ SG_MODE_COMBINE, SG_MODE_FILTER = 0, 1
 SG_NODE_CENTRED, SG_CELL_CENTRED = 0, 1
 SG_COMBINE_FLOAT_FLOAT, SG_COMBINE_FP64 = 0, 1
 SG_SOLVE_AUTO, SG_SOLVE_PASSES, SG_SOLVE_ONE_BLOCK = -1, 0, 1
+SG_DIAG_RING = 4
 
 
 class sg_domain(C.Structure):
@@ -86,6 +87,8 @@ SIGNATURES = {
     "sg_pic_density_copy": (C.c_int, [_P, _P, _SZ, C.c_int]),
     "sg_pic_step": (C.c_int, [_P, C.c_int]),
     "sg_pic_diagnostics": (C.c_int, [_P, C.POINTER(sg_diag)]),
+    "sg_pic_diagnostics_post": (C.c_int, [_P]),
+    "sg_pic_diagnostics_collect": (C.c_int, [_P, C.POINTER(sg_diag)]),
     "sg_pic_select_tau": (C.c_int, [_P, C.POINTER(C.c_int), _P, _P, C.c_int]),
     "sg_pic_set_tau": (C.c_int, [_P, C.c_int]),
     "sg_pic_get_particles": (C.c_int, [_P, C.POINTER(sg_particles_out)]),

@@ -214,6 +214,17 @@ int sg_pic_diagnostics(sg_pic* h, sg_diag* out) {
   return h->e->diagnostics(out);
 }
 
+int sg_pic_diagnostics_post(sg_pic* h) {
+  SG_H(h);
+  return h->e->diagnostics_post();
+}
+
+int sg_pic_diagnostics_collect(sg_pic* h, sg_diag* out) {
+  SG_H(h);
+  if (!out) return invalid("sg_pic_diagnostics_collect: out is NULL");
+  return h->e->diagnostics_collect(out);
+}
+
 int sg_pic_select_tau(sg_pic* h, int* tau, double* est_grid, double* est_noise, int cap) {
   SG_H(h);
   if (!tau) return invalid("sg_pic_select_tau: tau is NULL");

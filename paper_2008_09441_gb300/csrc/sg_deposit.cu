@@ -19,11 +19,11 @@ namespace sg {
 //
 // FP32 path: 32-bit fixed point, so the window uses native integer shared
 // atomics and its sums do not depend on the order of the adds.  The scale is
-// the power of two 2^(19 - E) with max_p |q_p| / V < 2^E over the run's
-// particles (set at upload): one contribution is below 2^19 in magnitude,
-// and DEP_CHUNK = 2^11 of them stay below 2^30, so no node overflows.  A
-// contribution is rounded once, to 2^-19 of the largest charge (the same
-// resolution a float has for a sum of 2^5 such charges).  Because |x| < 2^22, x + 1.5 * 2^23 lands in
+// the power of two 2^(20 - E) with max_p |q_p| / V <= 2^E (1 - 2^-11) over
+// the run's particles (set at upload): one contribution rounds to at most
+// 2^20 - 2^9 in magnitude, and DEP_CHUNK = 2^11 of them stay below
+// 2^31 - 2^20, so no node overflows.  A contribution is rounded once, to
+// 2^-20 of the largest charge.  Because |x| < 2^22, x + 1.5 * 2^23 lands in
 // [2^23, 2^24), where the float spacing is 1: its low mantissa bits are
 // round-to-nearest-even(x), with no conversion instruction.
 //
@@ -83,9 +83,9 @@ __device__ __forceinline__ void cell_frac(double s, int mask, int& c, double& f)
 // most a few steps after a sort, when the particles of a chunk have spread
 // and the touched box has grown.  FP64: one atomic add per non-zero node.
 //
-// FP32: WinAcc fixed point with the run's scale 2^(19 - E), max_p |q_p|/V <
-// 2^E (set at upload; charges do not change), so a window of at most 2^11
-// particles cannot overflow.  FP64: plain double, scale 1.
+// FP32: WinAcc fixed point with the run's scale 2^(20 - E), max_p |q_p|/V <=
+// 2^E (1 - 2^-11) (set at upload; charges do not change), so a window of at
+// most 2^11 particles cannot overflow.  FP64: plain double, scale 1.
 template <typename real, int D>
 __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, size_t np, int n,
                                                          real inv_cell_vol, real* __restrict__ rho, int side,
@@ -448,7 +448,7 @@ __device__ __forceinline__ void rj_load_run(const real* p, real* v) {
 }
 
 template <typename real, int VPL, bool CELL>
-__global__ void __launch_bounds__(256) k_restrict_warp(const LineJob* __restrict__ jobs, int njobs) {
+__global__ void __launch_bounds__(256) k_restrict_warp(const LineJob* __restrict__ jobs, int njobs, real mean) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* tile = reinterpret_cast<real*>(smem_raw);
   pdl_trigger();
@@ -548,6 +548,10 @@ __global__ void __launch_bounds__(256) k_restrict_warp(const LineJob* __restrict
     }
   }
   if (!active) return;  // no block-wide barrier follows
+  if (J->sub_mean) {
+#pragma unroll
+    for (int k = 0; k < VPL; ++k) v[k] -= mean;
+  }
   const RjOut<real> e{J, o, i, lane};
   int level = top;
   const int tmin = J->tmin;
@@ -593,7 +597,7 @@ __global__ void __launch_bounds__(256) k_restrict_warp(const LineJob* __restrict
 
 template <typename real>
 int launch_restrict_pass(const LineJob* jobs_dev, int njobs, int nblocks, int lines_per_block, int vpl,
-                         int smem_bytes, bool cell, cudaStream_t s) {
+                         int smem_bytes, bool cell, real mean, cudaStream_t s) {
   if (njobs == 0 || nblocks == 0) return SG_OK;
   const unsigned threads = 32u * (unsigned)lines_per_block;
 #define SG_RJ_LAUNCH(V, C)                                                                                   \
@@ -605,7 +609,7 @@ int launch_restrict_pass(const LineJob* jobs_dev, int njobs, int nblocks, int li
       attr_set = true;                                                                                       \
     }                                                                                                        \
     SG_CUDA(launch_pdl(k_restrict_warp<real, V, C>, dim3(nblocks), dim3(threads), smem_bytes, s, jobs_dev,   \
-                       njobs));                                                                              \
+                       njobs, mean));                                                                        \
   }
 #define SG_RJ_CASE(V)            \
   case V:                        \
@@ -641,7 +645,7 @@ SG_INST_DEP(float, 2)
 SG_INST_DEP(float, 3)
 SG_INST_DEP(double, 2)
 SG_INST_DEP(double, 3)
-template int launch_restrict_pass<float>(const LineJob*, int, int, int, int, int, bool, cudaStream_t);
-template int launch_restrict_pass<double>(const LineJob*, int, int, int, int, int, bool, cudaStream_t);
+template int launch_restrict_pass<float>(const LineJob*, int, int, int, int, int, bool, float, cudaStream_t);
+template int launch_restrict_pass<double>(const LineJob*, int, int, int, int, int, bool, double, cudaStream_t);
 
 }  // namespace sg

@@ -77,7 +77,9 @@ int launch_finalize_step(const double* fe_partials, int n_fe, const double* ke_p
   return SG_OK;
 }
 
-// Charge of every component grid: V_i sum_k rho_i(x_k), in FP64.
+// V_i sum_k rho_i(x_k) of every component grid's stored density, in FP64.
+// The grids hold deviations from the mean density: the host adds the mean's
+// charge to obtain each grid's charge.
 template <typename real>
 __global__ void k_grid_charges(const GridDesc* grids, const real* rho, double* charges) {
   __shared__ double red[32];

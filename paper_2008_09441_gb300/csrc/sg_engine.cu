@@ -266,6 +266,7 @@ class Engine final : public EngineBase {
       return SG_ERR_INVALID;
     }
     charge_total_ = q;
+    invalidate_graphs();  // the restriction's mean is a launch argument
     return SG_OK;
   }
   int density_copy(void* dev_buf, size_t n, int to_run) override {
@@ -307,43 +308,72 @@ class Engine final : public EngineBase {
     return SG_OK;
   }
 
-  int diagnostics(sg_diag* out) override {
+  // Diagnostics read-back in pinned memory: the device record, the count
+  // checksum, the status word, then one FP64 charge per component grid.
+  static size_t diag_off_cks() { return (sizeof(DevDiag) + 15) / 16 * 16; }
+  size_t diag_bytes() const { return diag_off_cks() + 16 + (size_t)ngrids_ * sizeof(double); }
+
+  // Host-side state a record is read against, taken when its copies are
+  // enqueued (the grid set may change before the record is read).
+  struct DiagMeta {
+    long long step = 0;
+    int tau = 0;
+    double charge_total = 0;
+    double mean_charge = 0;  // the charge of the mean density the grids are stored without
+    std::vector<double> coeff;
+  };
+  DiagMeta diag_meta() const {
+    DiagMeta m;
+    m.step = step_;
+    m.tau = tau_;
+    m.charge_total = charge_total_;
+    m.mean_charge = (double)rho_mean() * box_volume();
+    m.coeff.resize(ngrids_);
+    for (int i = 0; i < ngrids_; ++i) m.coeff[i] = (double)grids_[i].coeff;
+    return m;
+  }
+  int ensure_pinned(void** p, size_t* have, size_t need) {
+    if (need <= *have) return SG_OK;
+    if (*p) cudaFreeHost(*p);
+    *p = nullptr;
+    *have = 0;
+    SG_CUDA(cudaHostAlloc(p, need, cudaHostAllocDefault));
+    *have = need;
+    return SG_OK;
+  }
+  // Enqueue the grid charges and the copies of the record into h (stream order).
+  int enqueue_diag(char* h) {
     SG_TRY(launch_grid_charges<real>(grids_dev_, ngrids_, rho_arena_, nullptr, charges_dev_, stream_));
-    // one synchronisation: the device record, the checksum, the status word
-    // and the grid charges land in a pinned staging buffer
-    const size_t o_cks = (sizeof(DevDiag) + 15) / 16 * 16, o_st = o_cks + 8, o_ch = o_cks + 16;
-    const size_t bytes = o_ch + (size_t)ngrids_ * sizeof(double);
-    if (bytes > diag_host_bytes_) {
-      if (diag_host_) cudaFreeHost(diag_host_);
-      diag_host_ = nullptr;
-      diag_host_bytes_ = 0;
-      SG_CUDA(cudaHostAlloc(&diag_host_, bytes, cudaHostAllocDefault));
-      diag_host_bytes_ = bytes;
-    }
-    char* h = static_cast<char*>(diag_host_);
+    const size_t o_cks = diag_off_cks(), o_st = o_cks + 8, o_ch = o_cks + 16;
     SG_CUDA(cudaMemcpyAsync(h, dd_, sizeof(DevDiag), cudaMemcpyDeviceToHost, stream_));
     SG_CUDA(cudaMemcpyAsync(h + o_cks, checksum_, 8, cudaMemcpyDeviceToHost, stream_));
     SG_CUDA(cudaMemcpyAsync(h + o_st, status_, sizeof(unsigned), cudaMemcpyDeviceToHost, stream_));
     SG_CUDA(cudaMemcpyAsync(h + o_ch, charges_dev_, ngrids_ * sizeof(double), cudaMemcpyDeviceToHost, stream_));
-    SG_CUDA(cudaStreamSynchronize(stream_));
+    return SG_OK;
+  }
+  // Convert a landed record (FP64 charge sums over the grids on the host).
+  int read_diag(const char* h, const DiagMeta& m, sg_diag* out) {
+    const size_t o_cks = diag_off_cks(), o_st = o_cks + 8, o_ch = o_cks + 16;
+    const int ng = (int)m.coeff.size();
     DevDiag dd;
     std::memcpy(&dd, h, sizeof(DevDiag));
     unsigned long long cks = 0;
     std::memcpy(&cks, h + o_cks, 8);
     unsigned st = 0;
     std::memcpy(&st, h + o_st, sizeof(unsigned));
-    std::vector<double> ch(ngrids_);
-    std::memcpy(ch.data(), h + o_ch, ngrids_ * sizeof(double));
     std::memset(out, 0, sizeof(*out));
-    out->step = step_;
-    out->t = (double)step_ * cfg_.dt;
-    out->tau = tau_;
-    out->n_grids = ngrids_;
-    out->charge_total = charge_total_;
+    out->step = m.step;
+    out->t = (double)m.step * cfg_.dt;
+    out->tau = m.tau;
+    out->n_grids = ng;
+    out->charge_total = m.charge_total;
     double comb = 0, maxerr = 0;
-    for (int i = 0; i < ngrids_; ++i) {
-      comb += (double)grids_[i].coeff * ch[i];
-      maxerr = std::max(maxerr, std::fabs(ch[i] - charge_total_));
+    for (int i = 0; i < ng; ++i) {
+      double ch;
+      std::memcpy(&ch, h + o_ch + (size_t)i * sizeof(double), sizeof(double));
+      ch += m.mean_charge;
+      comb += m.coeff[i] * ch;
+      maxerr = std::max(maxerr, std::fabs(ch - m.charge_total));
     }
     out->charge_combined = comb;
     out->charge_grid_max_abs_err = maxerr;
@@ -356,6 +386,43 @@ class Engine final : public EngineBase {
       return SG_ERR_NONFINITE;
     }
     return SG_OK;
+  }
+
+  int diagnostics(sg_diag* out) override {
+    // one synchronisation for the whole record
+    SG_TRY(ensure_pinned(&diag_host_, &diag_host_bytes_, diag_bytes()));
+    char* h = static_cast<char*>(diag_host_);
+    SG_TRY(enqueue_diag(h));
+    SG_CUDA(cudaStreamSynchronize(stream_));
+    return read_diag(h, diag_meta(), out);
+  }
+
+  // Pipelined diagnostics: records enqueued into a ring of pinned slots and
+  // read in order, so that a monitor reads step k while step k+1 runs.
+  int diagnostics_post() override {
+    if (ring_count_ == kDiagRing) {
+      set_error("sg_pic_diagnostics_post: every slot holds a record not yet collected");
+      return SG_ERR_STATE;
+    }
+    DiagSlot& s = ring_[(ring_head_ + ring_count_) % kDiagRing];
+    SG_TRY(ensure_pinned(&s.host, &s.bytes, diag_bytes()));
+    if (!s.ev) SG_CUDA(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
+    SG_TRY(enqueue_diag(static_cast<char*>(s.host)));
+    SG_CUDA(cudaEventRecord(s.ev, stream_));
+    s.meta = diag_meta();
+    ++ring_count_;
+    return SG_OK;
+  }
+  int diagnostics_collect(sg_diag* out) override {
+    if (ring_count_ == 0) {
+      set_error("sg_pic_diagnostics_collect: no record was posted");
+      return SG_ERR_STATE;
+    }
+    DiagSlot& s = ring_[ring_head_];
+    ring_head_ = (ring_head_ + 1) % kDiagRing;
+    --ring_count_;
+    SG_CUDA(cudaEventSynchronize(s.ev));
+    return read_diag(static_cast<const char*>(s.host), s.meta, out);
   }
 
   int select_tau(int* tau, double* est_grid, double* est_noise, int cap) override {
@@ -547,7 +614,8 @@ class Engine final : public EngineBase {
 
   int get_grid_charge(double* rho, size_t cap) override {
     if (cap < S_) return size_error("sg_pic_get_grid_charge");
-    return copy_to_host_double(rho_arena_, rho, S_);
+    SG_TRY(copy_to_host_double(rho_arena_, rho, S_));
+    return add_mean(rho, S_);
   }
 
   int get_grid_field(double* E, size_t cap) override {
@@ -579,7 +647,10 @@ class Engine final : public EngineBase {
   // the filter mode the density its regular-grid solve used).
   int get_density(double* rho, size_t cap) override {
     if (cap < ND_) return size_error("sg_pic_get_density");
-    if (filter_) return copy_to_host_double(rho_f_, rho, ND_);
+    if (filter_) {
+      SG_TRY(copy_to_host_double(rho_f_, rho, ND_));
+      return add_mean(rho, ND_);
+    }
     real* tmp = nullptr;
     SG_TRY(alloc((void**)&tmp, ND_ * sizeof(real)));
     CombineFinal off;
@@ -588,6 +659,7 @@ class Engine final : public EngineBase {
                                      stream_, 1, cfg_.cell, cfg_.combine_fp64);
     if (st == SG_OK) st = copy_to_host_double(tmp, rho, ND_);
     free_one(tmp);
+    if (st == SG_OK) add_mean(rho, ND_);
     return st;
   }
 
@@ -805,6 +877,12 @@ class Engine final : public EngineBase {
     if (diag_host_) cudaFreeHost(diag_host_);
     diag_host_ = nullptr;
     diag_host_bytes_ = 0;
+    for (auto& r : ring_) {
+      if (r.host) cudaFreeHost(r.host);
+      if (r.ev) cudaEventDestroy(r.ev);
+      r = DiagSlot();
+    }
+    ring_head_ = ring_count_ = 0;
     for (int i = 0; i < 8; ++i)
       if (ev_[i]) cudaEventDestroy(ev_[i]);
     if (own_stream_ && stream_) cudaStreamDestroy(stream_);
@@ -856,9 +934,10 @@ class Engine final : public EngineBase {
     return set_deposit_scale();
   }
 
-  // Fixed-point scale of the deposit window (FP32 path): with
-  // max_p |q_p| / V < 2^E, contributions are scaled by 2^(19 - E), so each
-  // is below 2^19 and a window of at most 2^11 particles stays below 2^30.
+  // Fixed-point scale of the deposit window (FP32 path): with E the least
+  // integer such that max_p |q_p| / V <= 2^E (1 - 2^-11), contributions are
+  // scaled by 2^(20 - E), so each rounds to at most 2^20 - 2^9 in magnitude
+  // and a window of at most 2^11 particles stays below 2^31 - 2^20.
   // Charges do not change during a run; load() recomputes it.
   int set_deposit_scale() {
     dep_scale_ = 1.0;
@@ -868,7 +947,8 @@ class Engine final : public EngineBase {
       qmax *= (double)inv_cell_vol();
       int E = 0;
       if (qmax > 0) std::frexp(qmax, &E);  // qmax < 2^E
-      const int k = std::max(-126, std::min(127, 19 - E));
+      if (qmax > std::ldexp(1.0 - 1.0 / 2048.0, E)) ++E;
+      const int k = std::max(-126, std::min(127, 20 - E));
       dep_scale_ = std::ldexp(1.0, k);
     }
     return SG_OK;
@@ -977,6 +1057,7 @@ class Engine final : public EngineBase {
         LineJob J;
         std::memset(&J, 0, sizeof(J));
         J.src = prev.at(kv.first);
+        J.sub_mean = J.src == rho_reg_ ? 1 : 0;
         J.top = n_;
         long long inner = 1, outer = 1;
         for (int m = 0; m < a; ++m) inner <<= kv.first[m];
@@ -1131,11 +1212,20 @@ class Engine final : public EngineBase {
   }
   // Mean charge density Q / |box|: the mean of every component density and
   // of the filtered density (the transfer operators and the deposit conserve
-  // the total charge), subtracted before the forward transforms.
-  real rho_mean() const {
+  // the total charge).  The restriction subtracts it as it reads the regular
+  // grid, so the component densities and the filtered density are stored as
+  // deviations from it; the getters and the charge diagnostics add the
+  // same value back in FP64.
+  real rho_mean() const { return (real)(charge_total_ / box_volume()); }
+  double box_volume() const {
     double vol = 1;
     for (int m = 0; m < D; ++m) vol *= cfg_.L[m];
-    return (real)(charge_total_ / vol);
+    return vol;
+  }
+  int add_mean(double* rho, size_t n) const {
+    const double mean = (double)rho_mean();
+    for (size_t i = 0; i < n; ++i) rho[i] += mean;
+    return SG_OK;
   }
   real inv_cell_vol() const {
     double hd = 1;
@@ -1206,7 +1296,8 @@ class Engine final : public EngineBase {
 
   int enqueue_restrict() {
     for (auto& P : rpasses_)
-      SG_TRY(launch_restrict_pass<real>(P.dev, P.njobs, P.nblocks, P.lpb, P.vpl, P.smem, cfg_.cell, stream_));
+      SG_TRY(launch_restrict_pass<real>(P.dev, P.njobs, P.nblocks, P.lpb, P.vpl, P.smem, cfg_.cell, rho_mean(),
+                                        stream_));
     return SG_OK;
   }
 
@@ -1221,7 +1312,6 @@ class Engine final : public EngineBase {
     a.tw = tw_;
     a.log_nmax = n_;
     a.dim = D;
-    a.rho_mean = rho_mean();
     int maxsize = 0;
     for (auto& g : gdesc_) maxsize = std::max(maxsize, g.size);
     const bool small_ok = maxsize <= small_solve_max<real>();
@@ -1320,7 +1410,7 @@ class Engine final : public EngineBase {
                                    stream_, 1, cfg_.cell, cfg_.combine_fp64);
   }
   int enqueue_regular_solve(const double* ke) {
-    SG_TRY(launch_regular_solve<real>(rho_f_, rho_mean(), regA_, regB_, ktab_, tw_, D, n_, Ehi_, Elo_,
+    SG_TRY(launch_regular_solve<real>(rho_f_, regA_, regB_, ktab_, tw_, D, n_, Ehi_, Elo_,
                                       ec_stride<D>(), reg_partials_, reg_blocks_, stream_));
     return launch_finalize_step(reg_partials_, reg_blocks_ * ((D + 1) / 2), ke, ke ? nke_ : 0, fe_scale(), dd_,
                                 stream_);
@@ -1495,6 +1585,15 @@ class Engine final : public EngineBase {
   double* charges_dev_ = nullptr;
   void* diag_host_ = nullptr;  // pinned staging of the diagnostics read-back
   size_t diag_host_bytes_ = 0;
+  static constexpr int kDiagRing = SG_DIAG_RING;
+  struct DiagSlot {
+    void* host = nullptr;  // pinned record (diag_bytes() at the post)
+    size_t bytes = 0;
+    cudaEvent_t ev = nullptr;  // recorded after the record's copies
+    DiagMeta meta;
+  };
+  DiagSlot ring_[kDiagRing];
+  int ring_head_ = 0, ring_count_ = 0;
   real* rho_arena_ = nullptr;
   cplx<real>* A_ = nullptr;
   cplx<real>* B_ = nullptr;

@@ -46,6 +46,8 @@ class EngineBase {
   virtual int init(const EngineConfig& cfg, const sg_particles* p, cudaStream_t stream) = 0;
   virtual int step(int nsteps) = 0;
   virtual int diagnostics(sg_diag* out) = 0;
+  virtual int diagnostics_post() = 0;
+  virtual int diagnostics_collect(sg_diag* out) = 0;
   virtual int select_tau(int* tau, double* est_grid, double* est_noise, int cap) = 0;
   virtual int set_tau(int tau) = 0;
   virtual int get_particles(const sg_particles_out* out) = 0;

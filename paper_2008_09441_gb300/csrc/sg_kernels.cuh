@@ -82,6 +82,7 @@ struct LineJob {
   int tile_stride;       // reals per tile row in shared memory (inner > 1)
   int tmask;             // bit l set: level l is written
   int tmin;              // lowest level written
+  int sub_mean;          // 1: the source is the regular grid; the mean is subtracted as it is read
   void* dst[RJ_LEVELS];  // level l: [outer][2^l][inner]
 };
 
@@ -109,10 +110,15 @@ __device__ __forceinline__ int find_job(const Job* __restrict__ jobs, int njobs)
 // Restriction along one axis of every job's lines (full weighting 1/4,
 // 1/2, 1/4 per level halving, the exact form of R along one axis for nested
 // node-centred grids; cell = true: R of cell-centred grids through the
-// face-averaged cascade), outputs in the natural layout.
+// face-averaged cascade), outputs in the natural layout.  Jobs that read
+// the regular grid subtract `mean` (Q / |box|) from every value they read:
+// the component densities are stored as deviations from the mean, which
+// every R_i preserves (its weights sum to one), so that FP32 rounding in the
+// restriction sums, in storage and in the transforms is relative to the
+// density's fluctuation instead of its much larger uniform part.
 template <typename real>
 int launch_restrict_pass(const LineJob* jobs_dev, int njobs, int nblocks, int lines_per_block, int vpl,
-                         int smem_bytes, bool cell, cudaStream_t s);
+                         int smem_bytes, bool cell, real mean, cudaStream_t s);
 
 // FFT passes over the component grids.
 enum FftKind { FFT_FWD_FIRST = 0, FFT_FWD_MID = 1, FFT_LAST = 2, FFT_INV_MID = 3, FFT_INV_LAST = 4 };
@@ -139,12 +145,6 @@ struct SolveArena {
   const cplx<real>* tw;  // twiddles exp(-2 pi i k / Nmax), k < Nmax/2
   int log_nmax;
   int dim;
-  // Mean density Q / |box| of every component grid (the deposit's partition
-  // of unity gives each grid the total charge).  It is subtracted before the
-  // forward transform: the k = 0 mode is dropped by the solve anyway, and
-  // without the mean the transform's rounding is relative to the density's
-  // fluctuation instead of its (much larger) uniform part.
-  real rho_mean;
 };
 
 // Complex values per block of a transform pass (whole lines, at least one
@@ -165,8 +165,10 @@ constexpr int small_solve_max() { return sizeof(real) == 4 ? 4096 : 2048; }
 // The filter mode's regular-grid solve: rho_f -> E on the regular nodes
 // (E_hi node-interleaved with `stride`, FP32 low planes zeroed), per-block
 // field-energy partials at partials[pair * blocks + block] (ceil(dim/2) pairs).
+// rho_f is the combination of the component densities, a deviation from the
+// mean like them.
 template <typename real>
-int launch_regular_solve(const real* rho_f, real rho_mean, cplx<real>* A, cplx<real>* B, const real* ktab,
+int launch_regular_solve(const real* rho_f, cplx<real>* A, cplx<real>* B, const real* ktab,
                          const cplx<real>* tw, int dim, int n, real* Ehi, float* Elo, int stride, double* partials,
                          int blocks, cudaStream_t s);
 

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(FFT_BLOCK_VALUES / 2) k_fft_pass(int kind, Sol
     const long long off = line_addr(line0 + li, t, ls, logn);
     cplx<real> v;
     if (kind == FFT_FWD_FIRST) {
-      v.x = a.rho[g.offset + off] - a.rho_mean;
+      v.x = a.rho[g.offset + off];
       v.y = (real)0;
     } else if (kind == FFT_FWD_MID || kind == FFT_LAST) {
       v = a.A[g.offset + off];
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(1024) k_solve_small(SolveArena<real> a, int ma
   cplx<real>* tws = B + max_size;  // twiddle table staged in shared memory
   const int ntw = 1 << (a.log_nmax - 1);
   for (int e = threadIdx.x; e < ntw; e += blockDim.x) tws[e] = a.tw[e];
-  for (int e = threadIdx.x; e < S; e += blockDim.x) A[e] = {a.rho[g.offset + e] - a.rho_mean, (real)0};
+  for (int e = threadIdx.x; e < S; e += blockDim.x) A[e] = {a.rho[g.offset + e], (real)0};
   __syncthreads();
   for (int ax = 0; ax < D; ++ax) fft_axis_inplace<real>(A, logs, S, ax, false, tws, a.log_nmax);
   const real norm = (real)1 / (real)S;
@@ -444,9 +444,9 @@ int launch_fft_array_axis(cplx<real>* data, int D, int logn, int axis, bool inve
 // along every axis, and the real / imaginary parts as E_a / E_b.
 
 template <typename real>
-__global__ void k_regular_pack(const real* __restrict__ rho, real rho_mean, cplx<real>* __restrict__ a, size_t nd) {
+__global__ void k_regular_pack(const real* __restrict__ rho, cplx<real>* __restrict__ a, size_t nd) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += (size_t)gridDim.x * blockDim.x)
-    a[i] = {rho[i] - rho_mean, (real)0};  // the mean (k = 0) is dropped by the solve: see SolveArena::rho_mean
+    a[i] = {rho[i], (real)0};
 }
 
 // ktab[m * N + i] = 2 pi / L_m * (i < N/2 ? i : i - N), in the run's precision.
@@ -517,11 +517,11 @@ __global__ void __launch_bounds__(256) k_regular_field_out(const cplx<real>* __r
 }
 
 template <typename real>
-int launch_regular_solve(const real* rho_f, real rho_mean, cplx<real>* A, cplx<real>* B, const real* ktab,
+int launch_regular_solve(const real* rho_f, cplx<real>* A, cplx<real>* B, const real* ktab,
                          const cplx<real>* tw, int dim, int n, real* Ehi, float* Elo, int stride, double* partials,
                          int blocks, cudaStream_t s) {
   const size_t nd = (size_t)1 << (dim * n);
-  k_regular_pack<real><<<blocks, 256, 0, s>>>(rho_f, rho_mean, A, nd);
+  k_regular_pack<real><<<blocks, 256, 0, s>>>(rho_f, A, nd);
   SG_CHECK_LAUNCH();
   for (int ax = 0; ax < dim; ++ax) SG_TRY(launch_fft_array_axis<real>(A, dim, n, ax, false, tw, n, s));
   const real norm = (real)(1.0 / (double)nd);
@@ -534,10 +534,10 @@ int launch_regular_solve(const real* rho_f, real rho_mean, cplx<real>* A, cplx<r
   }
   return SG_OK;
 }
-template int launch_regular_solve<float>(const float*, float, cplx<float>*, cplx<float>*, const float*,
+template int launch_regular_solve<float>(const float*, cplx<float>*, cplx<float>*, const float*,
                                          const cplx<float>*, int, int, float*, float*, int, double*, int,
                                          cudaStream_t);
-template int launch_regular_solve<double>(const double*, double, cplx<double>*, cplx<double>*, const double*,
+template int launch_regular_solve<double>(const double*, cplx<double>*, cplx<double>*, const double*,
                                           const cplx<double>*, int, int, double*, float*, int, double*, int,
                                           cudaStream_t);
 

@@ -93,6 +93,16 @@ def sg_pic_diagnostics(h):
     return d.as_dict()
 
 
+def sg_pic_diagnostics_post(h):
+    return check(lib().sg_pic_diagnostics_post(h), "sg_pic_diagnostics_post")
+
+
+def sg_pic_diagnostics_collect(h):
+    d = L.sg_diag()
+    check(lib().sg_pic_diagnostics_collect(h, C.byref(d)), "sg_pic_diagnostics_collect")
+    return d.as_dict()
+
+
 def sg_pic_select_tau(h, cap=32):
     t = C.c_int()
     g = np.zeros(cap)
@@ -219,6 +229,14 @@ class Run:
 
     def diagnostics(self):
         return sg_pic_diagnostics(self.h)
+
+    def post_diagnostics(self):
+        """Enqueue the read-back of the current diagnostics (no wait)."""
+        sg_pic_diagnostics_post(self.h)
+
+    def collect_diagnostics(self):
+        """Wait for the oldest posted diagnostics record and return it."""
+        return sg_pic_diagnostics_collect(self.h)
 
     def select_tau(self, cap=32):
         return sg_pic_select_tau(self.h, cap)

@@ -1,23 +1,31 @@
-"""The benchmark's own workload at full size, in the launch configuration
-bench.py times (2D Landau damping, n = 10, tau = 1, 19 component grids,
-4,194,304 FP32 particles on the device, sort every 4 steps, graph-launched
-steps), against the FP64 oracle: integer work bit for bit, densities and
-fields in full or at sampled nodes, and the particles' first step on a
-sample the oracle advances one by one."""
+"""The benchmark workloads at full size, in the launch configuration
+bench.py times (FP32 particles on the device, sort every 4 steps,
+graph-launched steps), against the FP64 oracle: integer work bit for bit,
+densities and fields in full or at sampled nodes, and the particles' first
+step on a sample the oracle advances one by one.  Then the same
+configurations over several steps on fewer particles, which the oracle
+advances in full.  Workloads: 2D Landau damping (n = 10, tau = 1, 19
+component grids, 4,194,304 particles), 3D two-stream (n = 7, tau = 1, 64
+component grids, 16,777,216 particles) and the 2D diocotron annulus with the
+Boris push (n = 9, tau = 1, 17 component grids, 8,388,608 particles)."""
 import numpy as np
 import pytest
 
 from oracle import sgpic_oracle as O
 from paper_2008_09441_gb300 import workloads
-from test_gpu_parity import TOL, make_run, nrmse, nrmse_periodic, torch_cuda  # noqa: F401
+from test_gpu_parity import TOL, make_run, nrmse, nrmse_periodic, relerr, torch_cuda  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
+FULL = {"landau2d_n10_fp32": (4194304, 10, 19), "twostream3d_n7_fp32": (16777216, 7, 64),
+        "diocotron2d_n9_fp32": (8388608, 9, 17)}
 
-def test_fullsize_landau_bench_configuration(torch_cuda):
-    wl = workloads.make("landau2d_n10_fp32")
+
+@pytest.mark.parametrize("name", list(FULL))
+def test_fullsize_bench_configuration(torch_cuda, name):
+    wl = workloads.make(name)
     n, d = wl.n, wl.dim
-    assert wl.n_particles == 4194304 and n == 10 and wl.tau == 1
+    assert (wl.n_particles, n, len(O.combination_grids(d, n, wl.tau))) == FULL[name] and wl.tau == 1
     run, (u64, v64, q64) = make_run(wl, "fp32", torch_cuda, sort_every=4)
     u64 = O.wrap_unit(u64)
     tol = TOL["fp32"]
@@ -45,7 +53,7 @@ def test_fullsize_landau_bench_configuration(torch_cuda):
     Eg = run.field()
     for m in range(d):
         ref = sum(c * O.prolong_at(E[m], n, l, idx) for l, c, rho, E in comps)
-        assert nrmse(Eg[m][idx[:, 0], idx[:, 1]], ref) < tol, m
+        assert nrmse(Eg[m][tuple(idx.T)], ref) < tol, m
 
     # first step on a sample: backward half kick at init, then kick and drift
     # with the initial field (both use E(x^0))
@@ -75,21 +83,22 @@ def test_fullsize_landau_bench_configuration(torch_cuda):
     run.close()
 
 
-def test_landau_n10_fp32_ten_steps(torch_cuda):
-    """The benchmark's configuration (2D Landau damping, n = 10, tau = 1, 19
-    component grids, FP32, sort every 4 steps, graph-launched steps) over 10
-    steps on 262,144 particles, which the oracle advances in full: the
-    particle state after every step (steps 2-4 and 6-8 are the ones where
-    particles have drifted since the last sort and the deposit's windows
-    take their slow path), then the combined field, the component charges
-    and the energies and charges of the diagnostics at the end."""
-    from test_gpu_parity import relerr
-    wl = workloads.make("landau2d_n10_fp32", n_particles=1 << 18, steps=10)
+@pytest.mark.parametrize("name,n_particles,steps", [("landau2d_n10_fp32", 1 << 18, 10),
+                                                    ("twostream3d_n7_fp32", 1 << 15, 5),
+                                                    ("diocotron2d_n9_fp32", 1 << 18, 10)])
+def test_bench_configuration_steps(torch_cuda, name, n_particles, steps):
+    """Each benchmark configuration over several steps on fewer particles,
+    which the oracle advances in full: the particle state after every step
+    (the steps between sorts are the ones where particles have drifted since
+    the last sort and the deposit's windows take their slow path), then the
+    combined field, the component charges and the energies and charges of
+    the diagnostics at the end."""
+    wl = workloads.make(name, n_particles=n_particles, steps=steps)
     n, d = wl.n, wl.dim
     run, (u64, v64, q64) = make_run(wl, "fp32", torch_cuda, sort_every=4)
-    ref = O.OracleRun(wl.L, n, u64, v64, q64, wl.dt, qm=wl.qm, tau=wl.tau)
+    ref = O.OracleRun(wl.L, n, u64, v64, q64, wl.dt, qm=wl.qm, tau=wl.tau, B=wl.B, eext_lin=wl.eext_lin)
     tol = TOL["fp32"]
-    for s in range(10):
+    for s in range(steps):
         run.step(1)
         ref.step(1)
         ug, vg, _ = run.particles()
@@ -104,7 +113,7 @@ def test_landau_n10_fp32_ten_steps(torch_cuda):
     for l, c, rho, E in ref.comps:
         assert nrmse(gq[l], rho) < tol, l
     dg, rd = run.diagnostics(), ref.diagnostics()
-    assert dg["step"] == 10 and dg["tau"] == 1
+    assert dg["step"] == steps and dg["tau"] == 1
     for key in ("field_energy", "field_energy_prev", "kinetic_energy"):
         assert relerr(dg[key], rd[key]) <= tol, (key, dg[key], rd[key])
     assert relerr(dg["charge_combined"], rd["charge_combined"]) <= tol

@@ -392,6 +392,52 @@ def test_adaptive_tau_runs(torch_cuda):
     run.close()
 
 
+def test_pipelined_diagnostics(torch_cuda):
+    """Records posted after every step and collected up to two steps later
+    are the oracle's diagnostics at the step of their post; a full ring and
+    an empty ring are refused; a record keeps the grid set of its post."""
+    from paper_2008_09441_gb300._lib import SG_DIAG_RING, SG_ERR_STATE, SGError
+    wl = workloads.landau2d(n_particles=9000, n=6, tau=1, seed=141)
+    run, (u64, v64, q64) = make_run(wl, "fp64", torch_cuda)
+    ref = O.OracleRun(wl.L, wl.n, u64, v64, q64, wl.dt, qm=wl.qm, tau=wl.tau, B=wl.B, eext_lin=wl.eext_lin)
+    tol = TOL["fp64"]
+    want, got = [], []
+    for s in range(7):
+        run.step(1)
+        run.post_diagnostics()
+        ref.step(1)
+        want.append(ref.diagnostics())
+        if s >= 2:
+            got.append(run.collect_diagnostics())
+    while len(got) < len(want):
+        got.append(run.collect_diagnostics())
+    for s, (d, rd) in enumerate(zip(got, want)):
+        assert d["step"] == s + 1 and d["tau"] == wl.tau and d["t"] == pytest.approx((s + 1) * wl.dt)
+        for key in ("field_energy", "field_energy_prev", "kinetic_energy"):
+            assert relerr(d[key], rd[key]) <= tol, (s, key, d[key], rd[key])
+        assert abs(d["charge_combined"] - rd["charge_combined"]) <= 1e-10 * abs(rd["charge_total"])
+    for _ in range(SG_DIAG_RING):
+        run.post_diagnostics()
+    with pytest.raises(SGError) as e:
+        run.post_diagnostics()
+    assert e.value.status == SG_ERR_STATE
+    for _ in range(SG_DIAG_RING):
+        assert run.collect_diagnostics()["step"] == 7
+    with pytest.raises(SGError) as e:
+        run.collect_diagnostics()
+    assert e.value.status == SG_ERR_STATE
+    run.post_diagnostics()
+    run.set_tau(3)
+    run.post_diagnostics()
+    d0, d1 = run.collect_diagnostics(), run.collect_diagnostics()
+    assert d0["tau"] == 1 and d0["n_grids"] == len(O.combination_grids(2, 6, 1))
+    assert d1["tau"] == 3 and d1["n_grids"] == len(O.combination_grids(2, 6, 3))
+    sync = run.diagnostics()
+    for key in ("field_energy", "charge_combined", "kinetic_energy"):
+        assert relerr(sync[key], d1[key]) <= 1e-14, key
+    run.close()
+
+
 # ------------------------------------------------------------ checkpoint, errors
 
 
