@@ -127,12 +127,7 @@ class Engine final : public EngineBase {
     SG_TRY(alloc((void**)&comb_counter_, sizeof(unsigned)));
     SG_CUDA(cudaMemsetAsync(comb_counter_, 0, sizeof(unsigned), stream_));
     {
-      std::vector<cplx<real>> tw(std::max(1, N_ / 2));
-      for (int k = 0; k < N_ / 2; ++k) {
-        double a = 2.0 * M_PI * (double)k / (double)N_;
-        tw[k].x = (real)std::cos(a);
-        tw[k].y = (real)(-std::sin(a));
-      }
+      const std::vector<cplx<real>> tw = make_twiddles<real>(n_);
       SG_TRY(alloc((void**)&tw_, tw.size() * sizeof(cplx<real>)));
       SG_CUDA(cudaMemcpyAsync(tw_, tw.data(), tw.size() * sizeof(cplx<real>), cudaMemcpyHostToDevice, stream_));
       SG_CUDA(cudaStreamSynchronize(stream_));
@@ -1193,12 +1188,7 @@ class Engine final : public EngineBase {
     SG_TRY(alloc((void**)&est_z_, ND_ * sizeof(cplx<double>)));
     SG_TRY(alloc((void**)&est_w_, ND_ * sizeof(cplx<double>)));
     SG_TRY(alloc((void**)&est_scalar_, 16 * sizeof(double)));
-    std::vector<cplx<double>> tw(std::max(1, N_ / 2));
-    for (int k = 0; k < N_ / 2; ++k) {
-      double a = 2.0 * M_PI * (double)k / (double)N_;
-      tw[k].x = std::cos(a);
-      tw[k].y = -std::sin(a);
-    }
+    const std::vector<cplx<double>> tw = make_twiddles<double>(n_);
     SG_TRY(alloc((void**)&tw64_, tw.size() * sizeof(cplx<double>)));
     SG_CUDA(cudaMemcpyAsync(tw64_, tw.data(), tw.size() * sizeof(cplx<double>), cudaMemcpyHostToDevice, stream_));
     return SG_OK;

@@ -2,6 +2,9 @@
 // enqueues on the given stream and returns an SG_* status.
 #pragma once
 
+#include <cmath>
+#include <vector>
+
 #include "sg_common.cuh"
 
 namespace sg {
@@ -134,6 +137,24 @@ struct FftJob {
   int comp;          // inverse passes: component pair (2 comp, 2 comp + 1)
 };
 
+// FFT twiddles, stage-major: the butterflies of span 2h (h = 1, 2, 4, ...)
+// use W_{2h}^p = exp(-2 pi i p / (2h)) for p < h, stored at h - 1 + p, so
+// that consecutive butterflies of a stage read consecutive entries.  A table
+// for transforms of up to 2^L points holds 2^L - 1 entries.
+__host__ __device__ constexpr int twiddle_index(int h, int p) { return h - 1 + p; }
+__host__ __device__ constexpr int twiddle_count(int L) { return L < 1 ? 1 : (1 << L) - 1; }
+template <typename real>
+std::vector<cplx<real>> make_twiddles(int L) {
+  std::vector<cplx<real>> tw((size_t)twiddle_count(L));
+  tw[0] = {(real)1, (real)0};
+  for (int h = 1; h < (1 << L); h <<= 1)
+    for (int p = 0; p < h; ++p) {
+      const double a = M_PI * (double)p / (double)h;
+      tw[(size_t)twiddle_index(h, p)] = {(real)std::cos(a), (real)(-std::sin(a))};
+    }
+  return tw;
+}
+
 template <typename real>
 struct SolveArena {
   const GridDesc* grids;
@@ -142,7 +163,7 @@ struct SolveArena {
   cplx<real>* B;       // D * S
   real* E;             // D * S
   size_t S;
-  const cplx<real>* tw;  // twiddles exp(-2 pi i k / Nmax), k < Nmax/2
+  const cplx<real>* tw;  // make_twiddles(log_nmax)
   int log_nmax;
   int dim;
 };

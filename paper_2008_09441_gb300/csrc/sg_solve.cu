@@ -30,23 +30,26 @@ __device__ __forceinline__ cplx<real> cmul(cplx<real> a, cplx<real> w) {
 __device__ __forceinline__ int fpad(int x) { return x + (x >> 5); }
 __host__ __device__ constexpr size_t fpad_size(size_t n) { return n + (n >> 5); }
 
+// Twiddles are stage-major (twiddle_index): the lanes of a warp read
+// consecutive entries in every stage, free of bank conflicts.
 template <typename real>
 __device__ __forceinline__ void fft_smem(cplx<real>* buf, int nl, int logn, bool inverse,
-                                         const cplx<real>* __restrict__ tw, int log_nmax) {
+                                         const cplx<real>* __restrict__ tw) {
   const int len = 1 << logn;
   const int halfN = len >> 1;
   int s0 = 1;
   for (; s0 + 1 <= logn; s0 += 2) {
     const int h = 1 << (s0 - 1);
     const int quarter = len >> 2;
-    const int t1 = log_nmax - s0, t2 = log_nmax - s0 - 1;
     for (int j = threadIdx.x; j < nl * quarter; j += blockDim.x) {
       const int li = j >> (logn - 2);
       const int jj = j & (quarter - 1);
       const int pos = jj & (h - 1);
       const int grp = jj >> (s0 - 1);
       const int i0 = li * len + grp * 4 * h + pos;
-      cplx<real> w1 = tw[pos << t1], w2 = tw[pos << t2], w3 = tw[(pos + h) << t2];
+      // W_{2h}^pos, W_{4h}^pos and W_{4h}^(pos + h)
+      cplx<real> w1 = tw[twiddle_index(h, pos)], w2 = tw[twiddle_index(2 * h, pos)],
+                 w3 = tw[twiddle_index(2 * h, pos + h)];
       if (inverse) {
         w1.y = -w1.y;
         w2.y = -w2.y;
@@ -67,7 +70,6 @@ __device__ __forceinline__ void fft_smem(cplx<real>* buf, int nl, int logn, bool
   }
   for (int s = s0; s <= logn; ++s) {
     const int half = 1 << (s - 1);
-    const int tshift = log_nmax - s;
     for (int j = threadIdx.x; j < nl * halfN; j += blockDim.x) {
       int li = j >> (logn - 1);
       int jj = j & (halfN - 1);
@@ -75,7 +77,7 @@ __device__ __forceinline__ void fft_smem(cplx<real>* buf, int nl, int logn, bool
       int grp = jj >> (s - 1);
       int i0 = li * len + grp * 2 * half + pos;
       int i1 = i0 + half;
-      cplx<real> w = tw[pos << tshift];
+      cplx<real> w = tw[twiddle_index(half, pos)];
       if (inverse) w.y = -w.y;
       cplx<real> a = buf[fpad(i0)], b = buf[fpad(i1)];
       real bx = b.x * w.x - b.y * w.y;
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(FFT_BLOCK_VALUES / 2) k_fft_pass(int kind, Sol
   const int nl = C;
   // twiddles staged in shared memory, then the two line buffers
   cplx<real>* tws = reinterpret_cast<cplx<real>*>(smem_raw);
-  const int ntw = 1 << (a.log_nmax - 1);
+  const int ntw = twiddle_count(a.log_nmax);
   for (int e = threadIdx.x; e < ntw; e += blockDim.x) tws[e] = a.tw[e];
   pdl_wait();  // the previous pass's output
   cplx<real>* buf0 = tws + ntw;
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(FFT_BLOCK_VALUES / 2) k_fft_pass(int kind, Sol
   }
   __syncthreads();
   const bool inverse = (kind == FFT_INV_MID || kind == FFT_INV_LAST);
-  fft_smem<real>(buf0, nl, logn, inverse, tws, a.log_nmax);
+  fft_smem<real>(buf0, nl, logn, inverse, tws);
 
   if (kind == FFT_LAST) {
     const int D = a.dim;
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(FFT_BLOCK_VALUES / 2) k_fft_pass(int kind, Sol
         buf1[fpad((li << logn) + bitrev(t, logn))] = out;
       }
       __syncthreads();
-      fft_smem<real>(buf1, nl, logn, true, tws, a.log_nmax);
+      fft_smem<real>(buf1, nl, logn, true, tws);
       for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int li = contiguous ? (e >> logn) : (e & (nl - 1));
         const int t = contiguous ? (e & (len - 1)) : (e >> logC);
@@ -236,7 +238,8 @@ int launch_fft_pass(int kind, const SolveArena<real>& a, const FftJob* jobs_dev,
     attr_set = true;
   }
   SG_CUDA(launch_pdl(k_fft_pass<real>, dim3(nblocks), dim3(FFT_BLOCK_VALUES / 2),
-                     smem_bytes + ((size_t)1 << (a.log_nmax - 1)) * sizeof(cplx<real>), s, kind, a, jobs_dev, njobs));
+                     smem_bytes + (size_t)twiddle_count(a.log_nmax) * sizeof(cplx<real>), s, kind, a, jobs_dev,
+                     njobs));
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
@@ -249,7 +252,7 @@ int launch_fft_pass(int kind, const SolveArena<real>& a, const FftJob* jobs_dev,
 // butterfly stages), forms each E^_m and transforms it back.
 template <typename real>
 __device__ void fft_axis_inplace(cplx<real>* buf, const int* logs, int S, int ax, bool inverse,
-                                 const cplx<real>* __restrict__ tw, int log_nmax) {
+                                 const cplx<real>* __restrict__ tw) {
   const int logn = logs[ax];
   const int len = 1 << logn;
   int ls = 0;
@@ -273,7 +276,6 @@ __device__ void fft_axis_inplace(cplx<real>* buf, const int* logs, int S, int ax
   // contiguous along every axis (the line itself strides by 2^ls).
   for (int s = 1; s <= logn; ++s) {
     const int half = 1 << (s - 1);
-    const int tshift = log_nmax - s;
     for (int j = threadIdx.x; j < (S >> 1); j += blockDim.x) {
       const int i = j & smask;
       const int p = (j >> ls) & (halfN - 1);
@@ -283,7 +285,7 @@ __device__ void fft_axis_inplace(cplx<real>* buf, const int* logs, int S, int ax
       const int t0 = grp * 2 * half + pos;
       const int i0 = (((o << logn) + t0) << ls) + i;
       const int i1 = i0 + (half << ls);
-      cplx<real> w = tw[pos << tshift];
+      cplx<real> w = tw[twiddle_index(half, pos)];
       if (inverse) w.y = -w.y;
       const cplx<real> x0 = buf[i0], x1 = buf[i1];
       const real bx = x1.x * w.x - x1.y * w.y;
@@ -306,11 +308,11 @@ __global__ void __launch_bounds__(1024) k_solve_small(SolveArena<real> a, int ma
   cplx<real>* A = reinterpret_cast<cplx<real>*>(smem_raw);
   cplx<real>* B = A + max_size;
   cplx<real>* tws = B + max_size;  // twiddle table staged in shared memory
-  const int ntw = 1 << (a.log_nmax - 1);
+  const int ntw = twiddle_count(a.log_nmax);
   for (int e = threadIdx.x; e < ntw; e += blockDim.x) tws[e] = a.tw[e];
   for (int e = threadIdx.x; e < S; e += blockDim.x) A[e] = {a.rho[g.offset + e], (real)0};
   __syncthreads();
-  for (int ax = 0; ax < D; ++ax) fft_axis_inplace<real>(A, logs, S, ax, false, tws, a.log_nmax);
+  for (int ax = 0; ax < D; ++ax) fft_axis_inplace<real>(A, logs, S, ax, false, tws);
   const real norm = (real)1 / (real)S;
   const int n0 = 1 << logs[0], n1 = 1 << logs[1];
   // Field components in pairs: B = E^_a + i E^_b, one inverse transform,
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(1024) k_solve_small(SolveArena<real> a, int ma
       B[e] = out;
     }
     __syncthreads();
-    for (int ax = 0; ax < D; ++ax) fft_axis_inplace<real>(B, logs, S, ax, true, tws, a.log_nmax);
+    for (int ax = 0; ax < D; ++ax) fft_axis_inplace<real>(B, logs, S, ax, true, tws);
     for (int e = threadIdx.x; e < S; e += blockDim.x) {
       a.E[(size_t)ma * a.S + g.offset + e] = B[e].x;
       if (mb < D) a.E[(size_t)mb * a.S + g.offset + e] = B[e].y;
@@ -369,7 +371,7 @@ int launch_solve_small(const SolveArena<real>& a, int ngrids, int max_size, cuda
   if (ngrids == 0) return SG_OK;
   int threads = max_size / 2;
   threads = threads < 64 ? 64 : (threads > 1024 ? 1024 : threads);
-  size_t smem = ((size_t)2 * max_size + ((size_t)1 << (a.log_nmax - 1))) * sizeof(cplx<real>);
+  size_t smem = ((size_t)2 * max_size + (size_t)twiddle_count(a.log_nmax)) * sizeof(cplx<real>);
   static bool attr_set = false;
   if (!attr_set) {
     SG_CUDA(cudaFuncSetAttribute(k_solve_small<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -390,7 +392,7 @@ __global__ void __launch_bounds__(256) k_fft_array(cplx<real>* data, int D, int 
   extern __shared__ unsigned char smem_raw[];
   // twiddles staged in shared memory, then the lines
   cplx<real>* tws = reinterpret_cast<cplx<real>*>(smem_raw);
-  const int ntw = 1 << (log_nmax - 1);
+  const int ntw = twiddle_count(log_nmax);
   for (int e = threadIdx.x; e < ntw; e += blockDim.x) tws[e] = tw[e];
   cplx<real>* buf = tws + ntw;
   const int len = 1 << logn;
@@ -405,7 +407,7 @@ __global__ void __launch_bounds__(256) k_fft_array(cplx<real>* data, int D, int 
     buf[fpad((li << logn) + bitrev(t, logn))] = data[line_addr(line0 + li, t, ls, logn)];
   }
   __syncthreads();
-  fft_smem<real>(buf, nl, logn, inverse != 0, tws, log_nmax);
+  fft_smem<real>(buf, nl, logn, inverse != 0, tws);
   for (int e = threadIdx.x; e < (nl << logn); e += blockDim.x) {
     const int li = contiguous ? (e >> logn) : (e & (nl - 1));
     const int t = contiguous ? (e & (len - 1)) : (e >> logC);
@@ -423,7 +425,7 @@ int launch_fft_array_axis(cplx<real>* data, int D, int logn, int axis, bool inve
   long long lines = 1;
   for (int m = 0; m < D - 1; ++m) lines *= len;
   if (C > lines) C = (int)lines;
-  size_t smem = (fpad_size((size_t)C * len) + ((size_t)1 << (log_nmax - 1))) * sizeof(cplx<real>);
+  size_t smem = (fpad_size((size_t)C * len) + (size_t)twiddle_count(log_nmax)) * sizeof(cplx<real>);
   static bool attr_set = false;
   if (!attr_set) {
     SG_CUDA(cudaFuncSetAttribute(k_fft_array<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));

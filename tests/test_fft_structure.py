@@ -2,9 +2,11 @@
 (CPU only): input in bit-reversed order, decimation-in-time stages taken in
 pairs (radix 2^2: four elements i, i+h, i+2h, i+3h, the butterflies of stage
 s with span 2h and of stage s+1 with span 4h) with an odd last stage as a
-plain radix-2 pass, twiddles tw[k] = exp(-2 pi i k / 2^nmax) indexed
-pos << (nmax - s); the inverse conjugates them.  Checked against numpy.fft.
-Also the pairing of two real field components in one inverse transform."""
+plain radix-2 pass, twiddles in a stage-major table (the butterflies of
+span 2h read W_{2h}^p = exp(-2 pi i p / 2h), p < h, at entry h - 1 + p,
+2^nmax - 1 entries); the inverse conjugates them.  Checked against
+numpy.fft.  Also the pairing of two real field components in one inverse
+transform."""
 import numpy as np
 import pytest
 
@@ -13,9 +15,27 @@ def bitrev(t, logn):
     return int(format(t, f"0{logn}b")[::-1], 2) if logn else 0
 
 
+def stage_twiddles(log_nmax):
+    """Entry h - 1 + p holds exp(-2 pi i p / (2h)) for h = 1, 2, ..., 2^(nmax-1), p < h."""
+    tw = np.empty((1 << log_nmax) - 1, dtype=complex)
+    h = 1
+    while h < (1 << log_nmax):
+        tw[h - 1:2 * h - 1] = np.exp(-1j * np.pi * np.arange(h) / h)
+        h *= 2
+    return tw
+
+
+def test_stage_twiddles_table():
+    tw = stage_twiddles(4)
+    assert tw.size == 15 and tw[0] == 1
+    # span 16 (h = 8): the 16th roots of unity, p < 8; span 4: 1, -i
+    np.testing.assert_allclose(tw[7:15], np.exp(-2j * np.pi * np.arange(8) / 16), atol=1e-15)
+    np.testing.assert_allclose(tw[1:3], [1, -1j], atol=1e-15)
+
+
 def fft_pairs(x, logn, log_nmax, inverse=False):
     n = 1 << logn
-    tw = np.exp(-2j * np.pi * np.arange(1 << (log_nmax - 1)) / (1 << log_nmax))
+    tw = stage_twiddles(log_nmax)
     if inverse:
         tw = np.conj(tw)
     buf = np.empty(n, dtype=complex)
@@ -24,12 +44,11 @@ def fft_pairs(x, logn, log_nmax, inverse=False):
     s0 = 1
     while s0 + 1 <= logn:
         h = 1 << (s0 - 1)
-        t1, t2 = log_nmax - s0, log_nmax - s0 - 1
         for jj in range(n >> 2):
             pos = jj & (h - 1)
             grp = jj >> (s0 - 1)
             i0 = grp * 4 * h + pos
-            w1, w2, w3 = tw[pos << t1], tw[pos << t2], tw[(pos + h) << t2]
+            w1, w2, w3 = tw[h - 1 + pos], tw[2 * h - 1 + pos], tw[2 * h - 1 + pos + h]
             a0, a1, a2, a3 = buf[i0], buf[i0 + h], buf[i0 + 2 * h], buf[i0 + 3 * h]
             m1, m3 = a1 * w1, a3 * w1
             b0, b1, b2, b3 = a0 + m1, a0 - m1, a2 + m3, a2 - m3
@@ -43,7 +62,7 @@ def fft_pairs(x, logn, log_nmax, inverse=False):
             pos = jj & (half - 1)
             grp = jj >> (s - 1)
             i0 = grp * 2 * half + pos
-            w = tw[pos << (log_nmax - s)]
+            w = tw[half - 1 + pos]
             a, b = buf[i0], buf[i0 + half] * w
             buf[i0], buf[i0 + half] = a + b, a - b
     return buf
@@ -90,7 +109,8 @@ def inplace_axis_fft(buf, logs, ax, inverse, log_nmax):
     along axis ax, restated: bit-reversal swap along the axis, then radix-2
     stages whose butterfly j takes inner index j mod 2^ls (the axes below
     ax), butterfly p = (j >> ls) mod 2^(logn-1) of its line and outer line
-    o = j >> (ls + logn - 1); twiddle exp(-+2 pi i pos 2^(log_nmax - s) / Nmax)."""
+    o = j >> (ls + logn - 1); twiddle entry half - 1 + pos of the stage-major
+    table (conjugated for the inverse)."""
     S = buf.size
     logn = logs[ax]
     ls = sum(logs[:ax])
@@ -101,7 +121,7 @@ def inplace_axis_fft(buf, logs, ax, inverse, log_nmax):
         if r > t:
             e2 = e + ((r - t) << ls)
             buf[e], buf[e2] = buf[e2], buf[e]
-    nmax = 1 << log_nmax
+    tw = stage_twiddles(log_nmax)
     half_n = length >> 1
     for s in range(1, logn + 1):
         half = 1 << (s - 1)
@@ -114,7 +134,7 @@ def inplace_axis_fft(buf, logs, ax, inverse, log_nmax):
             t0 = grp * 2 * half + pos
             i0 = (((o << logn) + t0) << ls) + i
             i1 = i0 + (half << ls)
-            w = np.exp(-2j * np.pi * (pos << (log_nmax - s)) / nmax)
+            w = tw[half - 1 + pos]
             if inverse:
                 w = np.conj(w)
             x0, x1 = buf[i0], buf[i1] * w
