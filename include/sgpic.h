@@ -264,7 +264,18 @@ int sg_pic_kernel_launches(sg_pic* h, unsigned long long* count);
  * passes, 1 one block per grid) and the two timings (ms) it compared; with
  * cap >= 10 entry 9 is 1 when those timings came from an earlier run of the
  * same precision, dimension, level and tau in this process (the tuner's
- * cache), 0 when this run measured them. */
+ * cache), 0 when this run measured them.  With cap >= 21, entries 10..20
+ * report the particle-pass tuner, which times, on the run's own particles
+ * at init, the push with half, one and two resident waves of blocks (the
+ * particles per block; a zero time step, which leaves every particle as it
+ * is) and the deposit with windows of 4096, 6144, 8192 and 12288 nodes of
+ * 64-bit capacity (the window's side and the windows per SM), and keeps
+ * the defaults (one wave, 8192) unless a candidate is 3% faster: 10 push
+ * blocks in use, 11 blocks of one resident wave, 12..14 the three push
+ * timings, 15 the window capacity in use, 16..19 the four deposit timings,
+ * 20 whether they came from an earlier run of the same shape (precision,
+ * dimension, level, log2 of the particle count, centring, push kind).
+ * Runs created with sg_pic_init_deferred keep the defaults. */
 int sg_pic_set_profiling(sg_pic* h, int on);
 int sg_pic_stage_times(sg_pic* h, double* ms, int cap);
 

@@ -298,13 +298,32 @@ int launch_deposit(const PArrays<real, D>& p, size_t np, int n, real inv_cell_vo
   long long nodes = 1;
   for (int m = 0; m < D; ++m) nodes *= side;
   const size_t smem = ((size_t)nodes * sizeof(T) + 15) / 16 * 16;  // zeroed in 16-byte words
-  static int per_sm = 0;
-  if (!per_sm) {
-    if (smem > 48 * 1024)
-      SG_CUDA(cudaFuncSetAttribute(k_deposit<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  if (smem > 200 * 1024) {
+    set_error("deposit: window capacity above 200 KB of shared memory");
+    return SG_ERR_UNSUPPORTED;
+  }
+  // resident blocks per SM for each window size met so far (the autotuner
+  // tries several capacities; the answer depends on the window's bytes)
+  static bool attr_set = false;
+  static size_t known_smem[8];
+  static int known_per_sm[8];
+  static int nknown = 0;
+  if (!attr_set) {
+    SG_CUDA(cudaFuncSetAttribute(k_deposit<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     SG_CUDA(cudaFuncSetAttribute(k_deposit<real, D>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    attr_set = true;
+  }
+  int per_sm = 0;
+  for (int i = 0; i < nknown; ++i)
+    if (known_smem[i] == smem) per_sm = known_per_sm[i];
+  if (!per_sm) {
     SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deposit<real, D>, DEP_THREADS, smem));
     if (per_sm < 1) per_sm = 1;
+    if (nknown < 8) {
+      known_smem[nknown] = smem;
+      known_per_sm[nknown] = per_sm;
+      ++nknown;
+    }
   }
   static int sms = 0;
   if (!sms) {

@@ -59,6 +59,28 @@ std::mutex& tune_mu() {
   return m;
 }
 
+// Process-wide record of the particle-pass tuner, by the run's shape: the
+// precision, dimension, level, particle count (log2 bucket), centring and
+// push kind.
+constexpr int kPushCands = 3;   // push grids: half, one and two resident waves
+constexpr int kDepCands = 4;    // deposit window capacities (64-bit-equivalent nodes)
+constexpr int kDepCap[kDepCands] = {4096, 6144, 8192, 12288};
+struct PartKey {
+  int real_bytes, dim, n, np_log2, cell, boris;
+  bool operator<(const PartKey& o) const {
+    return std::tie(real_bytes, dim, n, np_log2, cell, boris) <
+           std::tie(o.real_bytes, o.dim, o.n, o.np_log2, o.cell, o.boris);
+  }
+};
+struct PartEntry {
+  int push_pick, dep_pick;
+  float push_ms[kPushCands], dep_ms[kDepCands];
+};
+std::map<PartKey, PartEntry>& part_cache() {
+  static std::map<PartKey, PartEntry> m;
+  return m;
+}
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -114,9 +136,14 @@ class Engine final : public EngineBase {
     SG_TRY(alloc((void**)&tile_count_, ntiles_ * 4));
     SG_TRY(alloc((void**)&cursor_, ntiles_ * 4));
     SG_TRY(alloc((void**)&scan_sums_, scan_block_sums_words(ntiles_) * 4));
-    nke_ = push_blocks<real, D>(np_);
-    SG_TRY(alloc((void**)&ke_partials_, (size_t)nke_ * sizeof(double)));
-    SG_CUDA(cudaMemsetAsync(ke_partials_, 0, (size_t)nke_ * sizeof(double), stream_));
+    // push grid: one resident wave by default; the tuner may take half or two
+    // waves, so the kinetic-energy partials (one per block) fit two waves
+    push_wave_ = push_blocks<real, D>(np_);
+    push_blocks_ = push_wave_;
+    nke_ = push_blocks_;
+    win_cap_ = cfg_.win_cap;
+    SG_TRY(alloc((void**)&ke_partials_, (size_t)2 * push_wave_ * sizeof(double)));
+    SG_CUDA(cudaMemsetAsync(ke_partials_, 0, (size_t)2 * push_wave_ * sizeof(double), stream_));
 
     // ---- regular grid, combined field, twiddles
     SG_TRY(alloc((void**)&rho_reg_, ND_ * sizeof(real)));
@@ -187,6 +214,7 @@ class Engine final : public EngineBase {
       SG_TRY(tune_solve());
       SG_TRY(enqueue_combine(false));
     }
+    SG_TRY(tune_particles());
     SG_TRY(enqueue_push(-0.5 * cfg_.dt, false, nullptr));
     SG_CUDA(cudaStreamSynchronize(stream_));
     step_ = 0;
@@ -799,6 +827,17 @@ class Engine final : public EngineBase {
     if (cap > 7) ms[7] = solve_ms_[0];
     if (cap > 8) ms[8] = solve_ms_[1];
     if (cap > 9) ms[9] = tuned_from_cache_ ? 1.0 : 0.0;
+    // particle-pass tuner: push grid in use, one resident wave, the three
+    // push timings (half, one, two waves), the window capacity in use, the
+    // four deposit timings, and whether they came from the cache
+    if (cap > 10) ms[10] = push_blocks_;
+    if (cap > 11) ms[11] = push_wave_;
+    for (int c = 0; c < kPushCands; ++c)
+      if (cap > 12 + c) ms[12 + c] = push_ms_[c];
+    if (cap > 15) ms[15] = win_cap_;
+    for (int c = 0; c < kDepCands; ++c)
+      if (cap > 16 + c) ms[16 + c] = dep_ms_[c];
+    if (cap > 20) ms[20] = part_from_cache_ ? 1.0 : 0.0;
     return SG_OK;
   }
 
@@ -1246,7 +1285,7 @@ class Engine final : public EngineBase {
       SG_TRY(sort_reset());
       sf = sort_fuse();
     }
-    return launch_push<real, D>(P_[cur_], np_, n_, Ehi_, pp, ke, status_, sf, stream_);
+    return launch_push<real, D>(P_[cur_], np_, n_, Ehi_, pp, ke, status_, sf, stream_, push_blocks_);
   }
 
   // Step sort: counting sort of the particles by tile key (the Morton key of
@@ -1280,7 +1319,7 @@ class Engine final : public EngineBase {
 
   int enqueue_deposit() {
     SG_CUDA(cudaMemsetAsync(rho_reg_, 0, ND_ * sizeof(real), stream_));
-    return launch_deposit<real, D>(P_[cur_], np_, n_, inv_cell_vol(), rho_reg_, cfg_.win_cap, (real)dep_scale_,
+    return launch_deposit<real, D>(P_[cur_], np_, n_, inv_cell_vol(), rho_reg_, win_cap_, (real)dep_scale_,
                                    (real)(1.0 / dep_scale_), cfg_.cell ? (real)0.5 : (real)0, stream_);
   }
 
@@ -1372,6 +1411,93 @@ class Engine final : public EngineBase {
     solve_ms_[1] = best[1];
     std::lock_guard<std::mutex> lk(tune_mu());
     tune_cache()[key] = TuneEntry{solve_mode_, {best[0], best[1]}};
+    return SG_OK;
+  }
+
+  // Particle-pass autotuner, run once per run shape in the process (the
+  // choice is cached like the solve variant's): the push's grid -- half,
+  // one or two resident waves of blocks, i.e. the particles per block -- and
+  // the deposit's window capacity, which sets the window's side (its tile
+  // of the regular grid) and how many windows fit on an SM.  Both are timed
+  // on the run's own particles and leave the state as it was: the push runs
+  // with dt = 0 (every increment is an exact zero, so the particles stay
+  // bit for bit), the deposit recomputes the regular-grid density of the
+  // same particles.  The deposit is timed on freshly sorted particles (its
+  // best case).  A candidate replaces the default only when it is at least
+  // 3% faster, so that timing noise does not move the choice.
+  int tune_particles() {
+    if (np_ == 0) return SG_OK;
+    bool boris = false;
+    for (int m = 0; m < 3; ++m) boris |= cfg_.B[m] != 0.0;
+    int lg = 0;
+    while (((size_t)1 << (lg + 1)) <= np_) ++lg;
+    const PartKey key{(int)sizeof(real), D, n_, lg, cfg_.cell ? 1 : 0, boris ? 1 : 0};
+    const int pcand[kPushCands] = {std::max(1, push_wave_ / 2), push_wave_, 2 * push_wave_};
+    auto apply = [&](int pp, int dp) {
+      push_pick_ = pp;
+      dep_pick_ = dp;
+      push_blocks_ = pcand[pp];
+      nke_ = push_blocks_;
+      win_cap_ = kDepCap[dp];
+    };
+    {
+      std::lock_guard<std::mutex> lk(tune_mu());
+      auto it = part_cache().find(key);
+      if (it != part_cache().end()) {
+        for (int c = 0; c < kPushCands; ++c) push_ms_[c] = it->second.push_ms[c];
+        for (int c = 0; c < kDepCands; ++c) dep_ms_[c] = it->second.dep_ms[c];
+        apply(it->second.push_pick, it->second.dep_pick);
+        part_from_cache_ = true;
+        return SG_OK;
+      }
+    }
+    part_from_cache_ = false;
+    cudaEvent_t e0, e1;
+    SG_CUDA(cudaEventCreate(&e0));
+    SG_CUDA(cudaEventCreate(&e1));
+    auto timed = [&](auto&& enqueue, float* best) -> int {
+      SG_CUDA(cudaEventRecord(e0, stream_));
+      SG_TRY(enqueue());
+      SG_CUDA(cudaEventRecord(e1, stream_));
+      SG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      SG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      *best = std::min(*best, ms);
+      return SG_OK;
+    };
+    float pms[kPushCands], dms[kDepCands];
+    for (int rep = 0; rep < 4; ++rep) {  // the first round warms up
+      for (int c = 0; c < kPushCands; ++c) {
+        if (rep == 0) pms[c] = 1e30f;
+        push_blocks_ = pcand[c];
+        float warm = 1e30f;
+        SG_TRY(timed([&] { return enqueue_push(0.0, true, ke_partials_); }, rep ? &pms[c] : &warm));
+      }
+      for (int c = 0; c < kDepCands; ++c) {
+        if (rep == 0) dms[c] = 1e30f;
+        win_cap_ = kDepCap[c];
+        float warm = 1e30f;
+        SG_TRY(timed([&] { return enqueue_deposit(); }, rep ? &dms[c] : &warm));
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int pp = 1, dp = 2;  // the defaults: one wave, 8192 nodes
+    for (int c = 0; c < kPushCands; ++c)
+      if (pms[c] < 0.97f * pms[pp]) pp = c;
+    for (int c = 0; c < kDepCands; ++c)
+      if (dms[c] < 0.97f * dms[dp]) dp = c;
+    for (int c = 0; c < kPushCands; ++c) push_ms_[c] = pms[c];
+    for (int c = 0; c < kDepCands; ++c) dep_ms_[c] = dms[c];
+    apply(pp, dp);
+    SG_TRY(enqueue_deposit());  // the regular-grid density from the chosen window
+    PartEntry ent;
+    ent.push_pick = pp;
+    ent.dep_pick = dp;
+    for (int c = 0; c < kPushCands; ++c) ent.push_ms[c] = pms[c];
+    for (int c = 0; c < kDepCands; ++c) ent.dep_ms[c] = dms[c];
+    std::lock_guard<std::mutex> lk(tune_mu());
+    part_cache()[key] = ent;
     return SG_OK;
   }
 
@@ -1556,6 +1682,12 @@ class Engine final : public EngineBase {
   double* reg_partials_ = nullptr;
   int reg_blocks_ = 0;
   int nke_ = 0, nrows_ = 0;
+  // particle-pass tuner: the push grid (one resident wave, and the count in
+  // use), the deposit window capacity in use, the compared timings (ms)
+  int push_wave_ = 1, push_blocks_ = 1, win_cap_ = 8192;
+  int push_pick_ = 1, dep_pick_ = 2;
+  float push_ms_[kPushCands] = {}, dep_ms_[kDepCands] = {};
+  bool part_from_cache_ = false;
 
   real* rho_reg_ = nullptr;
   real* Ehi_ = nullptr;

@@ -240,7 +240,7 @@ struct SortFuse {
 
 template <typename real, int D>
 int launch_push(const PArrays<real, D>& p, size_t np, int n, const real* Ecomb, PushParams<real> pp,
-                double* ke_partials, unsigned* status, const SortFuse& sf, cudaStream_t s);
+                double* ke_partials, unsigned* status, const SortFuse& sf, cudaStream_t s, int blocks = 0);
 template <typename real, int D>
 int push_blocks(size_t np);  // grid of the push (size of its kinetic-energy partials)
 

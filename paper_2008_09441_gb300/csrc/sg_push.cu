@@ -288,8 +288,8 @@ int push_blocks(size_t np) {
 
 template <typename real, int D>
 int launch_push(const PArrays<real, D>& p, size_t np, int n, const real* Ecomb, PushParams<real> pp,
-                double* ke_partials, unsigned* status, const SortFuse& sf, cudaStream_t s) {
-  int blocks = push_blocks<real, D>(np);
+                double* ke_partials, unsigned* status, const SortFuse& sf, cudaStream_t s, int blocks) {
+  if (blocks <= 0) blocks = push_blocks<real, D>(np);
   if (sf.keys)  // sort steps: memsets precede the push
     k_push<real, D><<<blocks, 256, 0, s>>>(p, np, n, Ecomb, pp, ke_partials, status, sf);
   else
@@ -300,7 +300,7 @@ int launch_push(const PArrays<real, D>& p, size_t np, int n, const real* Ecomb, 
 
 #define SG_INST_PUSH(real, D)                                                                           \
   template int launch_push<real, D>(const PArrays<real, D>&, size_t, int, const real*, PushParams<real>, \
-                                    double*, unsigned*, const SortFuse&, cudaStream_t);                  \
+                                    double*, unsigned*, const SortFuse&, cudaStream_t, int);             \
   template int push_blocks<real, D>(size_t);
 SG_INST_PUSH(float, 2)
 SG_INST_PUSH(float, 3)

@@ -488,6 +488,32 @@ def test_kernel_launch_count_reported(torch_cuda):
     run.close()
 
 
+def test_particle_tuner_record(torch_cuda):
+    """The init-time particle-pass tuner picks among its candidates (push
+    grids of half, one and two resident waves; deposit windows of 4096, 6144,
+    8192 and 12288 nodes), reports positive timings, and a second run of the
+    same shape takes the cached choice; both runs follow the oracle."""
+    wl = workloads.landau2d(n_particles=150000, n=7, tau=1, seed=151)
+    runs = []
+    for _ in range(2):
+        run, (u64, v64, q64) = make_run(wl, "fp32", torch_cuda)
+        runs.append(run)
+    t0, t1 = runs[0].tuning(), runs[1].tuning()
+    wave = t0["push_wave_blocks"]
+    assert t0["push_blocks"] in (max(1, wave // 2), wave, 2 * wave)
+    assert t0["deposit_window_nodes"] in (4096, 6144, 8192, 12288)
+    assert all(x > 0 for x in t0["push_ms_half_one_two_waves"] + t0["deposit_ms_4096_6144_8192_12288"])
+    assert t1["particles_from_cache"] and (t1["push_blocks"], t1["deposit_window_nodes"]) == \
+        (t0["push_blocks"], t0["deposit_window_nodes"])
+    ref = O.OracleRun(wl.L, wl.n, u64, v64, q64, wl.dt, qm=wl.qm, tau=wl.tau)
+    ref.step(3)
+    for run in runs:
+        run.step(3)
+        ug, vg, _ = run.particles()
+        assert nrmse_periodic(ug, ref.u) < TOL["fp32"] and nrmse(vg, ref.velocities()) < TOL["fp32"]
+        run.close()
+
+
 def test_stage_profiling_mode_same_results(torch_cuda):
     wl = workloads.landau2d(n_particles=10000, n=5, tau=1, seed=161)
     r1, _ = make_run(wl, "fp64", torch_cuda)
