@@ -334,12 +334,12 @@ __device__ __forceinline__ void combine_finalize(const double* partials, int n_p
 }
 
 // Lines per block of the warp-per-line kernel (one warp per line and
-// component) and the bytes of its per-warp row-term tables.
+// component) and the bytes of its row-term tables (one per line).
 template <int D>
 constexpr int combine_rows_per_block() { return 4; }  // 3D: 2 rows measured 16% slower
 template <typename real, int D, int NC>
 __host__ __device__ constexpr size_t combine_table_bytes(int ngl) {
-  return ((size_t)combine_rows_per_block<D>() * NC * ngl * sizeof(RowTerm<real, D>) + 15) / 16 * 16;
+  return ((size_t)combine_rows_per_block<D>() * ngl * sizeof(RowTerm<real, D>) + 15) / 16 * 16;
 }
 // Stride of the output between nodes: NC = D fields are stored
 // node-interleaved (ec_stride), a single density plainly.
@@ -371,35 +371,56 @@ __global__ void __launch_bounds__(32 * combine_rows_per_block<D>() * NC) k_combi
   const int ngl = ll.start[17];
   constexpr int RPB = combine_rows_per_block<D>();  // the block's lines: all NC components of each
   constexpr int DP = combine_out_stride<D, NC>();
-  RowTerm<real, D>* rt_tab = reinterpret_cast<RowTerm<real, D>*>(smem_raw) + (size_t)wib * ngl;
+  // one row-term table per line, shared by the line's NC component warps
+  RowTerm<real, D>* rt_all = reinterpret_cast<RowTerm<real, D>*>(smem_raw);
+  RowTerm<real, D>* rt_tab = rt_all + (size_t)(wib / NC) * ngl;
   // [RPB][N][DP] with one padding word after every V nodes (a lane's run), so
   // that the lanes' stores of one step fall in distinct banks
   real* stage = reinterpret_cast<real*>(smem_raw + combine_table_bytes<real, D, NC>(ngl));
   const int row0 = blockIdx.x * RPB;
   pdl_trigger();
-  for (int gi = lane; gi < ngl; gi += 32) rt_tab[gi] = row_term<real, D, CELL>(grids[ll.grid[gi]], n, y, z);
+  for (int e = threadIdx.x; e < RPB * ngl; e += blockDim.x) {
+    const int r = e / ngl, gi = e - r * ngl;
+    const int rr = row0 + r;  // the block's line r
+    rt_all[e] = row_term<real, D, CELL>(grids[ll.grid[gi]], n, rr & (N - 1), D == 3 ? (rr >> n) : 0);
+  }
   __syncthreads();
   pdl_wait();  // the solve's fields
   real energy = (real)0;
   double energy_d = 0.0;  // FP64 accumulation: the squares of the double results
   if (row < rows) {
     AC T[V];
-    // coarse phase: one value on 2^level lanes, up to 32 values; the terms
-    // of all coarse levels are read first (independent loads).  Cell-centred
-    // grids enter one level higher.
+    // coarse phase: one value on 2^level lanes, up to 32 values.  The terms
+    // of every coarse level, pairs (l, x) with l in [level, ltop] and
+    // x < 2^l, numbered p = 2^l - 2^level + x (at most 62), are computed
+    // first, two pairs per lane (p = lane and lane + 32) so that every lane
+    // works, and are handed to lane x of level l by shuffles.  Each term sums
+    // its level's grids in the same order as before.  Cell-centred grids
+    // enter one level higher.
     int level = min(CELL ? lmin + 1 : lmin, min(n, 5));
     const int ltop = min(n, 5);
-    AC sc[6];
+    const int p0 = 1 << level;
+    const int npairs = (2 << ltop) - p0;
+    AC pv[2];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      const int l = level + j;
-      if (l <= ltop && lane < (1 << l))
-        sc[j] = CELL ? cell_term1<real, D, AC>(rt_tab, s_start, l, Em, lane)
-                     : level_term1<real, D, AC>(rt_tab, s_start, l, Em, lane);
-      else
-        sc[j] = AC::zero();
+    for (int sl = 0; sl < 2; ++sl) {
+      const int p = lane + 32 * sl;
+      if (p < npairs) {
+        const int l = 31 - __clz(p + p0);
+        const int x = p + p0 - (1 << l);
+        pv[sl] = CELL ? cell_term1<real, D, AC>(rt_tab, s_start, l, Em, x)
+                      : level_term1<real, D, AC>(rt_tab, s_start, l, Em, x);
+      } else {
+        pv[sl] = AC::zero();
+      }
     }
-    T[0] = sc[0];
+    // the level-l term of this lane's x (zero beyond 2^l); every lane shuffles
+    auto coarse = [&](int l) {
+      const int p = (1 << l) - p0 + lane;
+      const AC a = pv[0].shfl(p & 31), b = pv[1].shfl(p & 31);
+      return lane < (1 << l) ? ((p >> 5) ? b : a) : AC::zero();
+    };
+    T[0] = coarse(level);
 #pragma unroll
     for (int j = 1; j < 6; ++j) {
       if (level < ltop) {
@@ -409,7 +430,8 @@ __global__ void __launch_bounds__(32 * combine_rows_per_block<D>() * NC) k_combi
         const AC b = T[0].shfl((k + 1) & (h - 1));
         T[0] = (lane & 1) ? AC::avg(a, b) : a;
         ++level;
-        if (lane < (1 << level)) T[0] = AC::add(T[0], sc[j]);
+        const AC c = coarse(level);
+        if (lane < (1 << level)) T[0] = AC::add(T[0], c);
       }
     }
     // register phase: 2^level / 32 consecutive values per lane
