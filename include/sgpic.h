@@ -386,11 +386,19 @@ int sg_pic_density_copy(sg_pic* h, void* dev_buf, size_t n, int to_run);
 
 /* ---- serving: independent runs admitted as memory allows -----------------
  * A server keeps many independent runs resident on one GPU and advances all
- * of them together: in batched mode a tick launches every resident run's own
- * cached CUDA graph of one step on the run's own stream (the runs' kernels
- * overlap on the device; no graph is captured again when runs arrive or
- * leave), in plain mode the runs are stepped in turn with direct launches
- * and one solve launch per component grid.  Requests are admitted in arrival
+ * of them together.  In batched mode a tick forks every resident run onto
+ * its own stream.  Runs of the combination mode with a fixed tau whose
+ * component grids fit one block's shared memory (a solve of the one-block
+ * kind) and at most 2^20 particles take their step in three parts (the
+ * shared solve waits for the slowest of them; larger runs are not bound by
+ * launch latency and keep their own solve): the run's cached graph up to its
+ * solve (push, sort when due, deposit, restriction); ONE launch per
+ * precision that solves the component grids of all of them, one block per
+ * (run, grid), from a job table of the runs' arenas; the run's cached graph
+ * of the combination.  Other runs replay their cached graph of the whole
+ * step.  The runs' kernels overlap on the device, and no graph is captured
+ * again when runs arrive or leave.  In plain mode the runs are stepped in
+ * turn with direct launches and one solve launch per component grid.  Requests are admitted in arrival
  * order while their estimated device footprint fits hbm_budget_bytes and a
  * slot is free; finished runs retire and free their memory. */
 typedef struct sg_server sg_server;
@@ -409,7 +417,7 @@ typedef struct {
 #define SG_REQ_DONE 2
 #define SG_REQ_FAILED 3
 
-#define SG_SERVE_BATCHED 0 /* every resident run's cached step graph, on its own stream */
+#define SG_SERVE_BATCHED 0 /* cached per-run graphs on the runs' streams, one cross-run solve launch */
 #define SG_SERVE_PLAIN 1   /* runs stepped in turn, direct launches, one solve launch per grid */
 
 int sg_serve_create(size_t hbm_budget_bytes, int max_slots, sg_server** out);
@@ -426,6 +434,10 @@ int sg_serve_poll(sg_server* s, unsigned long long ticket, int* state, sg_diag* 
 int sg_serve_result(sg_server* s, unsigned long long ticket, const sg_particles_out* out);
 /* Per-step latency percentiles (ms) over all steps served so far and
  * aggregate particle-steps per second of device time. */
+/* Cross-run solves of the batched mode so far: the launches and the
+ * component grids they solved (summed over the launches).  Either pointer
+ * may be NULL. */
+int sg_serve_solve_stats(sg_server* s, unsigned long long* launches, unsigned long long* grids);
 int sg_serve_stats(sg_server* s, double* p50_ms, double* p99_ms, double* particle_steps_per_s,
                    unsigned long long* steps_served);
 void sg_serve_destroy(sg_server* s);

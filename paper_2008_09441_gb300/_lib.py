@@ -122,6 +122,7 @@ SIGNATURES = {
     "sg_serve_result": (C.c_int, [_P, C.c_ulonglong, C.POINTER(sg_particles_out)]),
     "sg_serve_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(C.c_ulonglong)]),
+    "sg_serve_solve_stats": (C.c_int, [_P, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)]),
     "sg_serve_destroy": (None, [_P]),
 }
 

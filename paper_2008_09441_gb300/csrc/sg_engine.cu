@@ -1330,7 +1330,7 @@ class Engine final : public EngineBase {
     return SG_OK;
   }
 
-  int enqueue_solve() {
+  SolveArena<real> solve_arena() const {
     SolveArena<real> a;
     a.grids = grids_dev_;
     a.rho = rho_arena_;
@@ -1341,6 +1341,10 @@ class Engine final : public EngineBase {
     a.tw = tw_;
     a.log_nmax = n_;
     a.dim = D;
+    return a;
+  }
+  int enqueue_solve() {
+    const SolveArena<real> a = solve_arena();
     int maxsize = 0;
     for (auto& g : gdesc_) maxsize = std::max(maxsize, g.size);
     const bool small_ok = maxsize <= small_solve_max<real>();
@@ -1584,11 +1588,104 @@ class Engine final : public EngineBase {
   }
 
   void invalidate_graphs() {
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i) {
       if (gexec_[i]) {
         cudaGraphExecDestroy(gexec_[i]);
         gexec_[i] = nullptr;
       }
+      if (gpre_[i]) {
+        cudaGraphExecDestroy(gpre_[i]);
+        gpre_[i] = nullptr;
+      }
+    }
+    if (gpost_) {
+      cudaGraphExecDestroy(gpost_);
+      gpost_ = nullptr;
+    }
+  }
+
+  // Captures what `enqueue` launches on the run's stream into an executable
+  // graph; *launches receives the kernel count.
+  template <typename F>
+  int capture(F&& enqueue, cudaGraphExec_t* exec, unsigned long long* launches) {
+    const int cur_before = cur_;
+    const unsigned long long l0 = launches_so_far();
+    cudaGraph_t g;
+    SG_CUDA(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
+    const int st = enqueue();
+    const cudaError_t e = cudaStreamEndCapture(stream_, &g);
+    cur_ = cur_before;  // the capture did not run anything
+    if (st != SG_OK) return st;
+    if (e != cudaSuccess) {
+      set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+      return SG_ERR_CUDA;
+    }
+    SG_CUDA(cudaGraphInstantiate(exec, g, 0));
+    cudaGraphDestroy(g);
+    *launches = launches_so_far() - l0;
+    return SG_OK;
+  }
+
+  // ------------------------------------------------------------ cross-run solve
+  // The step split around the component solves, so that a server can solve
+  // the grids of all its resident runs in one launch (launch_solve_batch):
+  // step_pre (push, sort when due, deposit, restriction), the caller's
+  // solve over solve_jobs, then step_post (combination and the step's FP64
+  // bookkeeping).  Runs of the combination mode with a fixed tau whose grids
+  // all fit one block take part.
+  bool solve_batchable() const override {
+    return !adaptive_ && !filter_ && !profiling_ && phase_ == kReady && small_solve_fits();
+  }
+  int real_bytes() const override { return (int)sizeof(real); }
+  int enqueue_step_pre(bool do_sort) {
+    SG_TRY(enqueue_push(cfg_.dt, true, ke_partials_, do_sort));
+    if (do_sort) SG_TRY(sort_finish());
+    SG_TRY(enqueue_deposit());
+    return enqueue_restrict();
+  }
+  int step_pre() override {
+    if (!solve_batchable()) {
+      set_error("step_pre: the run cannot take part in a cross-run solve");
+      return SG_ERR_STATE;
+    }
+    const bool do_sort = next_step_sorts();
+    const int vi = cur_ * 2 + (do_sort ? 1 : 0);
+    if (!gpre_[vi]) SG_TRY(capture([&] { return enqueue_step_pre(do_sort); }, &gpre_[vi], &gpre_launches_[vi]));
+    SG_CUDA(cudaGraphLaunch(gpre_[vi], stream_));
+    launches_ += gpre_launches_[vi];
+    if (do_sort) cur_ ^= 1;
+    phase_ = kPreSolve;
+    return SG_OK;
+  }
+  int solve_jobs(std::vector<unsigned char>& out, int* max_size, int* max_log) override {
+    if (phase_ != kPreSolve) {
+      set_error("solve_jobs: step_pre must come first");
+      return SG_ERR_STATE;
+    }
+    const SolveArena<real> a = solve_arena();
+    for (int g = 0; g < ngrids_; ++g) {
+      SolveJob<real> j;
+      std::memset(&j, 0, sizeof(j));
+      j.a = a;
+      j.grid = g;
+      const unsigned char* b = reinterpret_cast<const unsigned char*>(&j);
+      out.insert(out.end(), b, b + sizeof(j));
+      *max_size = std::max(*max_size, gdesc_[g].size);
+    }
+    *max_log = std::max(*max_log, n_);
+    return SG_OK;
+  }
+  int step_post() override {
+    if (phase_ != kPreSolve) {
+      set_error("step_post: step_pre must come first");
+      return SG_ERR_STATE;
+    }
+    if (!gpost_) SG_TRY(capture([&] { return enqueue_combine(true, ke_partials_); }, &gpost_, &gpost_launches_));
+    SG_CUDA(cudaGraphLaunch(gpost_, stream_));
+    launches_ += gpost_launches_ + 1;  // and this run's share of the cross-run solve
+    ++step_;
+    phase_ = kReady;
+    return SG_OK;
   }
 
   // Same sequence as enqueue_step with events between the stages:
@@ -1643,7 +1740,7 @@ class Engine final : public EngineBase {
   }
 
   // ------------------------------------------------------------ state
-  enum Phase { kReady = 0, kAwaitStart = 1, kHalfStep = 2 };
+  enum Phase { kReady = 0, kAwaitStart = 1, kHalfStep = 2, kPreSolve = 3 };
   Phase phase_ = kReady;
   EngineConfig cfg_;
   int n_ = 0, N_ = 0;
@@ -1731,6 +1828,12 @@ class Engine final : public EngineBase {
 
   cudaGraphExec_t gexec_[4] = {nullptr, nullptr, nullptr, nullptr};
   unsigned long long glaunches_[4] = {0, 0, 0, 0};
+  // the step split around the cross-run solve: (particle set, sort) before
+  // the solve, the combination after it
+  cudaGraphExec_t gpre_[4] = {nullptr, nullptr, nullptr, nullptr};
+  unsigned long long gpre_launches_[4] = {0, 0, 0, 0};
+  cudaGraphExec_t gpost_ = nullptr;
+  unsigned long long gpost_launches_ = 0;
   unsigned long long launches_ = 0;
   bool profiling_ = false;
   cudaEvent_t ev_[8] = {};

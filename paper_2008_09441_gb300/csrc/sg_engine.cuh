@@ -77,6 +77,13 @@ class EngineBase {
   virtual int step_fields() = 0;
   virtual int set_charge_total(double q) = 0;
   virtual int density_copy(void* dev_buf, size_t n, int to_run) = 0;
+  // cross-run solve (batched serving): the step split around the component
+  // solves; solve_jobs appends this run's jobs as raw SolveJob<real> bytes
+  virtual bool solve_batchable() const = 0;
+  virtual int real_bytes() const = 0;
+  virtual int step_pre() = 0;
+  virtual int solve_jobs(std::vector<unsigned char>& out, int* max_size, int* max_log) = 0;
+  virtual int step_post() = 0;
 };
 
 EngineBase* make_engine(int precision, int dim);

@@ -183,6 +183,19 @@ int launch_solve_small(const SolveArena<real>& a, int ngrids, int max_size, cuda
 template <typename real>
 constexpr int small_solve_max() { return sizeof(real) == 4 ? 4096 : 2048; }
 
+// One component grid of one run for the cross-run solve: the run's arena
+// and the grid's index in it.  A launch over a table of these solves the
+// component grids of every run in it, one block per (run, grid).
+template <typename real>
+struct SolveJob {
+  SolveArena<real> a;
+  int grid;
+  int pad;
+};
+// max_size: largest grid of the table (points); max_log: largest log_nmax.
+template <typename real>
+int launch_solve_batch(const SolveJob<real>* jobs, int njobs, int max_size, int max_log, cudaStream_t s);
+
 // The filter mode's regular-grid solve: rho_f -> E on the regular nodes
 // (E_hi node-interleaved with `stride`, FP32 low planes zeroed), per-block
 // field-energy partials at partials[pair * blocks + block] (ceil(dim/2) pairs).

@@ -53,6 +53,13 @@ struct sg_server {
   cudaStream_t ds = nullptr;
   cudaEvent_t ev_start = nullptr, ev_end = nullptr;  // timing
   cudaEvent_t fork = nullptr;                        // start of a tick for the runs' streams (not timed)
+  cudaEvent_t solved = nullptr;                      // the cross-run solve of a tick is done (not timed)
+  // cross-run solve: job tables per precision (0 FP32, 1 FP64), staged in
+  // pinned memory and copied to the device on the server's stream
+  void* jobs_dev[2] = {nullptr, nullptr};
+  void* jobs_host[2] = {nullptr, nullptr};
+  size_t jobs_cap[2] = {0, 0};
+  unsigned long long solve_launches = 0, solve_grids = 0;
   std::mutex mu;
 };
 
@@ -159,15 +166,79 @@ static int admit(sg_server* s, bool* changed, int* failed) {
 // parity and sort phase) on its own stream, all forked from the server's
 // stream and joined back, so the runs' kernels overlap on the device and
 // no graph is captured again when the resident set changes.
+// The job table of one precision to the device (on the server's stream;
+// the pinned copy stays untouched until the tick's end synchronises).
+static int stage_jobs(sg_server* s, int pi, const std::vector<unsigned char>& jobs) {
+  const size_t bytes = jobs.size();
+  if (bytes > s->jobs_cap[pi]) {
+    if (s->jobs_dev[pi]) SG_CUDA(cudaFreeAsync(s->jobs_dev[pi], s->ds));
+    if (s->jobs_host[pi]) cudaFreeHost(s->jobs_host[pi]);
+    s->jobs_dev[pi] = s->jobs_host[pi] = nullptr;
+    s->jobs_cap[pi] = 0;
+    const size_t cap = bytes * 2;
+    SG_CUDA(cudaMallocAsync(&s->jobs_dev[pi], cap, s->ds));
+    SG_CUDA(cudaHostAlloc(&s->jobs_host[pi], cap, cudaHostAllocDefault));
+    s->jobs_cap[pi] = cap;
+  }
+  std::memcpy(s->jobs_host[pi], jobs.data(), bytes);
+  SG_CUDA(cudaMemcpyAsync(s->jobs_dev[pi], s->jobs_host[pi], bytes, cudaMemcpyHostToDevice, s->ds));
+  return SG_OK;
+}
+
+// Batched tick.  Runs of the combination mode with a fixed tau, grids that
+// fit one block and at most kCrossRunMaxParticles particles take their step
+// in three parts: each run's graph up to its solve on its own stream; one
+// launch per precision solving the component grids of all of them (one
+// block per (run, grid)); each run's combination graph.  Other runs replay
+// their whole step graph.  Every stream forks from the server's stream and
+// joins it again.  The shared solve waits for the slowest run's particle
+// stages, so larger runs, whose step is not bound by launch latency, keep
+// their own solve.
+constexpr size_t kCrossRunMaxParticles = (size_t)1 << 20;
 static int tick_batched(sg_server* s, std::vector<Request*>& act) {
   SG_CUDA(cudaEventRecord(s->ev_start, s->ds));
   SG_CUDA(cudaEventRecord(s->fork, s->ds));
-  for (Request* r : act) {
+  std::vector<Request*> grp, rest;
+  for (Request* r : act)
+    (r->eng->solve_batchable() && r->eng->n_particles() <= kCrossRunMaxParticles ? grp : rest).push_back(r);
+  for (Request* r : rest) {
     SG_CUDA(cudaStreamWaitEvent(r->stream, s->fork, 0));
     SG_TRY(r->eng->step(1));
     SG_CUDA(cudaEventRecord(r->ev1, r->stream));
-    SG_CUDA(cudaStreamWaitEvent(s->ds, r->ev1, 0));
   }
+  std::vector<unsigned char> jobs[2];
+  int max_size[2] = {0, 0}, max_log[2] = {0, 0};
+  for (Request* r : grp) {
+    SG_CUDA(cudaStreamWaitEvent(r->stream, s->fork, 0));
+    SG_TRY(r->eng->step_pre());
+    SG_CUDA(cudaEventRecord(r->ev0, r->stream));
+    SG_CUDA(cudaStreamWaitEvent(s->ds, r->ev0, 0));
+    const int pi = r->eng->real_bytes() == 8 ? 1 : 0;
+    SG_TRY(r->eng->solve_jobs(jobs[pi], &max_size[pi], &max_log[pi]));
+  }
+  for (int pi = 0; pi < 2; ++pi) {
+    if (jobs[pi].empty()) continue;
+    SG_TRY(stage_jobs(s, pi, jobs[pi]));
+    int nj;
+    if (pi == 0) {
+      nj = (int)(jobs[pi].size() / sizeof(SolveJob<float>));
+      SG_TRY(launch_solve_batch<float>(static_cast<const SolveJob<float>*>(s->jobs_dev[pi]), nj, max_size[pi],
+                                       max_log[pi], s->ds));
+    } else {
+      nj = (int)(jobs[pi].size() / sizeof(SolveJob<double>));
+      SG_TRY(launch_solve_batch<double>(static_cast<const SolveJob<double>*>(s->jobs_dev[pi]), nj, max_size[pi],
+                                        max_log[pi], s->ds));
+    }
+    ++s->solve_launches;
+    s->solve_grids += (unsigned long long)nj;
+  }
+  SG_CUDA(cudaEventRecord(s->solved, s->ds));
+  for (Request* r : grp) {
+    SG_CUDA(cudaStreamWaitEvent(r->stream, s->solved, 0));
+    SG_TRY(r->eng->step_post());
+    SG_CUDA(cudaEventRecord(r->ev1, r->stream));
+  }
+  for (Request* r : act) SG_CUDA(cudaStreamWaitEvent(s->ds, r->ev1, 0));
   SG_CUDA(cudaEventRecord(s->ev_end, s->ds));
   SG_CUDA(cudaEventSynchronize(s->ev_end));
   float tick_ms = 0;
@@ -217,7 +288,8 @@ int sg_serve_create(size_t hbm_budget_bytes, int max_slots, sg_server** out) {
   s->max_slots = max_slots;
   if (cudaStreamCreateWithFlags(&s->ds, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreate(&s->ev_start) != cudaSuccess || cudaEventCreate(&s->ev_end) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->solved, cudaEventDisableTiming) != cudaSuccess) {
     delete s;
     return serr("sg_serve_create: stream/event creation failed", SG_ERR_CUDA);
   }
@@ -368,13 +440,27 @@ int sg_serve_stats(sg_server* s, double* p50_ms, double* p99_ms, double* particl
   return SG_OK;
 }
 
+int sg_serve_solve_stats(sg_server* s, unsigned long long* launches, unsigned long long* grids) {
+  if (!s) return serr("sg_serve_solve_stats: NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (launches) *launches = s->solve_launches;
+  if (grids) *grids = s->solve_grids;
+  return SG_OK;
+}
+
 void sg_serve_destroy(sg_server* s) {
   if (!s) return;
   for (Request* r : s->resident) finish(s, r, SG_REQ_FAILED);
   for (auto& kv : s->all) delete kv.second;
+  for (int pi = 0; pi < 2; ++pi) {
+    if (s->jobs_dev[pi]) cudaFreeAsync(s->jobs_dev[pi], s->ds);
+    if (s->jobs_host[pi]) cudaFreeHost(s->jobs_host[pi]);
+  }
+  if (s->ds) cudaStreamSynchronize(s->ds);
   if (s->ev_start) cudaEventDestroy(s->ev_start);
   if (s->ev_end) cudaEventDestroy(s->ev_end);
   if (s->fork) cudaEventDestroy(s->fork);
+  if (s->solved) cudaEventDestroy(s->solved);
   if (s->ds) cudaStreamDestroy(s->ds);
   delete s;
 }

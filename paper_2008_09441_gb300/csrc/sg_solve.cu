@@ -297,10 +297,12 @@ __device__ void fft_axis_inplace(cplx<real>* buf, const int* logs, int S, int ax
   }
 }
 
+// One block solves grid gi of arena a: load, forward transforms, E^_m,
+// paired inverse transforms, store.
 template <typename real>
-__global__ void __launch_bounds__(1024) k_solve_small(SolveArena<real> a, int max_size, int grid0) {
+__device__ __forceinline__ void solve_grid_block(const SolveArena<real>& a, int gi, int max_size) {
   extern __shared__ unsigned char smem_raw[];
-  const GridDesc g = a.grids[grid0 + blockIdx.x];
+  const GridDesc g = a.grids[gi];
   const int D = a.dim;
   int logs[3] = {0, 0, 0};
   for (int m = 0; m < D; ++m) logs[m] = g.l[m];
@@ -367,6 +369,19 @@ __global__ void __launch_bounds__(1024) k_solve_small(SolveArena<real> a, int ma
 }
 
 template <typename real>
+__global__ void __launch_bounds__(1024) k_solve_small(SolveArena<real> a, int max_size, int grid0) {
+  solve_grid_block<real>(a, grid0 + blockIdx.x, max_size);
+}
+
+// The cross-run solve: block b takes job b, a grid of one of the runs.
+template <typename real>
+__global__ void __launch_bounds__(1024) k_solve_batch(const SolveJob<real>* __restrict__ jobs, int max_size) {
+  const SolveJob<real>& J = jobs[blockIdx.x];
+  const SolveArena<real> a = J.a;
+  solve_grid_block<real>(a, J.grid, max_size);
+}
+
+template <typename real>
 int launch_solve_small(const SolveArena<real>& a, int ngrids, int max_size, cudaStream_t s, int grid0) {
   if (ngrids == 0) return SG_OK;
   int threads = max_size / 2;
@@ -384,6 +399,28 @@ int launch_solve_small(const SolveArena<real>& a, int ngrids, int max_size, cuda
 
 template int launch_solve_small<float>(const SolveArena<float>&, int, int, cudaStream_t, int);
 template int launch_solve_small<double>(const SolveArena<double>&, int, int, cudaStream_t, int);
+
+template <typename real>
+int launch_solve_batch(const SolveJob<real>* jobs, int njobs, int max_size, int max_log, cudaStream_t s) {
+  if (njobs == 0) return SG_OK;
+  if (max_size > small_solve_max<real>()) {
+    set_error("cross-run solve: a component grid is larger than one block's shared memory takes");
+    return SG_ERR_UNSUPPORTED;
+  }
+  int threads = max_size / 2;
+  threads = threads < 64 ? 64 : (threads > 1024 ? 1024 : threads);
+  const size_t smem = ((size_t)2 * max_size + (size_t)twiddle_count(max_log)) * sizeof(cplx<real>);
+  static bool attr_set = false;
+  if (!attr_set) {
+    SG_CUDA(cudaFuncSetAttribute(k_solve_batch<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  k_solve_batch<real><<<njobs, threads, smem, s>>>(jobs, max_size);
+  SG_CHECK_LAUNCH();
+  return SG_OK;
+}
+template int launch_solve_batch<float>(const SolveJob<float>*, int, int, int, cudaStream_t);
+template int launch_solve_batch<double>(const SolveJob<double>*, int, int, int, cudaStream_t);
 
 // In-place FFT of a whole N^D complex array along one axis (regular grid).
 template <typename real>

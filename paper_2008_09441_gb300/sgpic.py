@@ -481,6 +481,12 @@ class Server:
         check(lib().sg_serve_stats(self.h, C.byref(p50), C.byref(p99), C.byref(pst), C.byref(n)), "sg_serve_stats")
         return {"p50_ms": p50.value, "p99_ms": p99.value, "particle_steps_per_s": pst.value, "steps": n.value}
 
+    def solve_stats(self):
+        """Cross-run solves of the batched mode: launches and grids solved."""
+        a, b = C.c_ulonglong(), C.c_ulonglong()
+        check(lib().sg_serve_solve_stats(self.h, C.byref(a), C.byref(b)), "sg_serve_solve_stats")
+        return {"launches": a.value, "grids": b.value}
+
     def close(self):
         if getattr(self, "h", None):
             lib().sg_serve_destroy(self.h)

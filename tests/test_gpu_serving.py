@@ -156,4 +156,53 @@ def test_served_runs_match_oracle(mode):
         assert nrmse(vm, ref.velocities()) < 1e-5
         fe = ref.diagnostics()["field_energy"]
         assert abs(diag["field_energy"] - fe) <= 1e-5 * abs(fe)
+    ss = srv.solve_stats()
+    if mode == "batched":  # every run here takes part in the cross-run solve
+        assert ss["launches"] > 0 and ss["grids"] > ss["launches"]
+    else:
+        assert ss["launches"] == 0
+    srv.close()
+
+
+def test_cross_run_solve_mixed_runs():
+    """Batched serving of runs that take part in the cross-run solve (FP32
+    2D and 3D, and FP64: one launch per precision each tick) beside a
+    filter-mode run, which replays its whole step graph: every run against
+    the FP64 oracle advanced alone, at its precision's tolerance."""
+    from oracle import sgpic_oracle as O
+    from paper_2008_09441_gb300.sgpic import Server
+    params = [dict(dim=2, n=6, n_particles=12000, amplitude=0.05, k=0.5, seed=21, steps=5),
+              dict(dim=3, n=4, n_particles=6000, amplitude=0.02, k=0.4, seed=22, steps=5),
+              dict(dim=2, n=5, n_particles=5000, amplitude=0.1, k=0.3, seed=23, steps=5),
+              dict(dim=2, n=6, n_particles=8000, amplitude=0.1, k=0.5, seed=24, steps=5)]
+    extra = [dict(), dict(), dict(precision="fp64"), dict(mode="filter")]
+    wls = [workloads.serving_run_workload(p) for p in params]
+    srv = Server(hbm_budget_bytes=1 << 30, max_slots=4)
+    tickets = []
+    for wl, p, x in zip(wls, params, extra):
+        dt = np.float64 if x.get("precision") == "fp64" else np.float32
+        tickets.append(srv.submit(wl.L, wl.n, wl.u.astype(dt), wl.v.astype(dt), wl.q.astype(dt), wl.dt,
+                                  p["steps"], **x))
+    for _ in range(20):
+        srv.tick()
+        if all(srv.poll(t)[0] in (2, 3) for t in tickets):
+            break
+    ss = srv.solve_stats()
+    # five ticks, two precisions each, the filter run outside
+    assert ss["launches"] == 10, ss
+    for t, p, wl, x in zip(tickets, params, wls, extra):
+        st, diag = srv.poll(t)
+        assert st == 2 and diag["step"] == p["steps"], (t, st)
+        um, vm, _ = srv.result(t)
+        dt = np.float64 if x.get("precision") == "fp64" else np.float32
+        tol = 1e-12 if x.get("precision") == "fp64" else 1e-5
+        ref = O.OracleRun(wl.L, wl.n, *(a.astype(dt).astype(np.float64) for a in (wl.u, wl.v, wl.q)), wl.dt,
+                          qm=wl.qm, tau=wl.tau, mode=x.get("mode", "combine"))
+        ref.step(p["steps"])
+        du = um.astype(np.float64) - ref.u
+        du -= np.round(du)
+        assert np.sqrt(np.sum(du ** 2) / np.sum(ref.u ** 2)) < tol, t
+        assert nrmse(vm, ref.velocities()) < tol, t
+        fe = ref.diagnostics()["field_energy"]
+        assert abs(diag["field_energy"] - fe) <= tol * abs(fe), t
     srv.close()
