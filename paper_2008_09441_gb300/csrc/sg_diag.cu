@@ -77,27 +77,44 @@ int launch_finalize_step(const double* fe_partials, int n_fe, const double* ke_p
   return SG_OK;
 }
 
-// V_i sum_k rho_i(x_k) of every component grid's stored density, in FP64.
-// The grids hold deviations from the mean density: the host adds the mean's
-// charge to obtain each grid's charge.
+// The diagnostics record: the device record, the checksum, the status word
+// and V_i sum_k rho_i(x_k) of every component grid's stored density, in
+// FP64.  The grids hold deviations from the mean density: the host adds the
+// mean's charge to obtain each grid's charge.
 template <typename real>
-__global__ void k_grid_charges(const GridDesc* grids, const real* rho, double* charges) {
+__global__ void k_diag_record(const GridDesc* grids, const real* rho, const DevDiag* dd,
+                              const unsigned long long* cks, const unsigned* st, unsigned char* out, size_t o_cks,
+                              size_t o_ch) {
   __shared__ double red[32];
   const GridDesc g = grids[blockIdx.x];
   double acc = 0.0;
   for (int k = threadIdx.x; k < g.size; k += blockDim.x) acc += (double)rho[g.offset + k];
-  double t = block_sum_double(acc, red);
-  if (threadIdx.x == 0) charges[blockIdx.x] = t * g.vol;
+  const double t = block_sum_double(acc, red);
+  if (threadIdx.x == 0) {
+    reinterpret_cast<double*>(out + o_ch)[blockIdx.x] = t * g.vol;
+    if (blockIdx.x == 0) {
+      *reinterpret_cast<DevDiag*>(out) = *dd;
+      *reinterpret_cast<unsigned long long*>(out + o_cks) = *cks;
+      *reinterpret_cast<unsigned*>(out + o_cks + 8) = *st;
+    }
+  }
 }
 
 template <typename real>
-int launch_grid_charges(const GridDesc* grids, int ngrids, const real* rho, const double*, double* charges,
-                        cudaStream_t s) {
-  if (ngrids == 0) return SG_OK;
-  k_grid_charges<real><<<ngrids, 256, 0, s>>>(grids, rho, charges);
+int launch_diag_record(const GridDesc* grids, int ngrids, const real* rho, const DevDiag* dd,
+                       const unsigned long long* cks, const unsigned* st, void* out, size_t o_cks, size_t o_ch,
+                       cudaStream_t s) {
+  if (ngrids < 1) return SG_OK;
+  k_diag_record<real><<<ngrids, 256, 0, s>>>(grids, rho, dd, cks, st, static_cast<unsigned char*>(out), o_cks,
+                                              o_ch);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
+template int launch_diag_record<float>(const GridDesc*, int, const float*, const DevDiag*, const unsigned long long*,
+                                       const unsigned*, void*, size_t, size_t, cudaStream_t);
+template int launch_diag_record<double>(const GridDesc*, int, const double*, const DevDiag*,
+                                        const unsigned long long*, const unsigned*, void*, size_t, size_t,
+                                        cudaStream_t);
 
 template <typename real>
 __global__ void k_to_double(const real* src, double* dst, size_t n) {
@@ -325,8 +342,6 @@ SG_INST_DIAG(double, 2)
 SG_INST_DIAG(double, 3)
 template int launch_sum_to_double<float>(const float*, size_t, double*, int, cudaStream_t);
 template int launch_sum_to_double<double>(const double*, size_t, double*, int, cudaStream_t);
-template int launch_grid_charges<float>(const GridDesc*, int, const float*, const double*, double*, cudaStream_t);
-template int launch_grid_charges<double>(const GridDesc*, int, const double*, const double*, double*, cudaStream_t);
 template int launch_to_double<float>(const float*, double*, size_t, cudaStream_t);
 template int launch_to_double<double>(const double*, double*, size_t, cudaStream_t);
 

@@ -355,24 +355,26 @@ class Engine final : public EngineBase {
     for (int i = 0; i < ngrids_; ++i) m.coeff[i] = (double)grids_[i].coeff;
     return m;
   }
+  // Pinned host memory mapped into the device's address space: the record
+  // kernel writes a diagnostics record straight into it.
   int ensure_pinned(void** p, size_t* have, size_t need) {
     if (need <= *have) return SG_OK;
     if (*p) cudaFreeHost(*p);
     *p = nullptr;
     *have = 0;
-    SG_CUDA(cudaHostAlloc(p, need, cudaHostAllocDefault));
+    SG_CUDA(cudaHostAlloc(p, need, cudaHostAllocMapped));
     *have = need;
     return SG_OK;
   }
-  // Enqueue the grid charges and the copies of the record into h (stream order).
+  // Enqueue the kernel that packs the record into the mapped host buffer h
+  // (no copy operation on the stream: a copy after every step cost about
+  // 17 us of stream time between the step's kernels and the next step's).
   int enqueue_diag(char* h) {
-    SG_TRY(launch_grid_charges<real>(grids_dev_, ngrids_, rho_arena_, nullptr, charges_dev_, stream_));
-    const size_t o_cks = diag_off_cks(), o_st = o_cks + 8, o_ch = o_cks + 16;
-    SG_CUDA(cudaMemcpyAsync(h, dd_, sizeof(DevDiag), cudaMemcpyDeviceToHost, stream_));
-    SG_CUDA(cudaMemcpyAsync(h + o_cks, checksum_, 8, cudaMemcpyDeviceToHost, stream_));
-    SG_CUDA(cudaMemcpyAsync(h + o_st, status_, sizeof(unsigned), cudaMemcpyDeviceToHost, stream_));
-    SG_CUDA(cudaMemcpyAsync(h + o_ch, charges_dev_, ngrids_ * sizeof(double), cudaMemcpyDeviceToHost, stream_));
-    return SG_OK;
+    const size_t o_cks = diag_off_cks(), o_ch = o_cks + 16;
+    void* hd = nullptr;
+    SG_CUDA(cudaHostGetDevicePointer(&hd, h, 0));
+    return launch_diag_record<real>(grids_dev_, ngrids_, rho_arena_, dd_, checksum_, status_, hd, o_cks, o_ch,
+                                    stream_);
   }
   // Convert a landed record (FP64 charge sums over the grids on the host).
   int read_diag(const char* h, const DiagMeta& m, sg_diag* out) {
@@ -1021,7 +1023,6 @@ class Engine final : public EngineBase {
     for (void* p : grid_bufs_) free_one(p);
     grid_bufs_.clear();
     SG_TRY(galloc((void**)&grids_dev_, ngrids_ * sizeof(GridDesc)));
-    SG_TRY(galloc((void**)&charges_dev_, ngrids_ * sizeof(double)));
     {  // grids grouped by x level for the combination
       std::vector<int> order;
       std::memset(&levels_, 0, sizeof(levels_));
@@ -1801,7 +1802,6 @@ class Engine final : public EngineBase {
   float solve_ms_[2] = {0, 0};
   bool tuned_from_cache_ = false;
   GridDesc* grids_dev_ = nullptr;
-  double* charges_dev_ = nullptr;
   void* diag_host_ = nullptr;  // pinned staging of the diagnostics read-back
   size_t diag_host_bytes_ = 0;
   static constexpr int kDiagRing = SG_DIAG_RING;

@@ -291,6 +291,14 @@ struct DevDiag {
 int launch_finalize_step(const double* fe_partials, int n_fe, const double* ke_partials, int n_ke,
                          double fe_scale, DevDiag* dd, cudaStream_t s);
 
+// The diagnostics record in one buffer, for one device-to-host copy: *dd at
+// 0, *cks at o_cks, *st at o_cks + 8, and V_i sum_k rho_i(x_k) of every grid
+// (FP64) from o_ch on (one block per grid).
+template <typename real>
+int launch_diag_record(const GridDesc* grids, int ngrids, const real* rho, const DevDiag* dd,
+                       const unsigned long long* cks, const unsigned* st, void* out, size_t o_cks, size_t o_ch,
+                       cudaStream_t s);
+
 // Step bookkeeping closed by the last block of the combination kernel:
 // field energy from the per-row partials (scaled by fe_scale), the previous
 // field energy, and the kinetic energy from the push partials when given.
@@ -309,10 +317,6 @@ int launch_combine(const GridDesc* grids, const LevelLists& ll, int lmin, const 
                    cudaStream_t s, int ncomp,  // ncomp = D: the fields, interleaved; 1: a density, plain
                    bool cell,                  // cell-centred grids
                    bool fp64_acc);             // FP32 path: accumulate in double instead of float-float
-
-template <typename real>
-int launch_grid_charges(const GridDesc* grids, int ngrids, const real* rho, const double* vol,
-                        double* charges, cudaStream_t s);
 
 template <typename real>
 int launch_to_double(const real* src, double* dst, size_t n, cudaStream_t s);
