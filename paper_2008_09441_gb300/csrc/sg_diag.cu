@@ -34,22 +34,44 @@ int launch_wrap_check(const PArrays<real, D>& p, size_t np, unsigned* status, cu
   return SG_OK;
 }
 
+// The upload's statistics in one pass: per block the FP64 sum of the charges
+// (grid-stride over the particles, then the block) at out[b], the largest
+// |q| at out[nb + b], and the status word of the upload check at
+// out[2 nb] (as its bits).
 template <typename real>
-__global__ void k_sum_to_double(const real* x, size_t n, double* partials) {
+__global__ void k_charge_stats(const real* w, size_t n, const unsigned* status, double* out) {
   __shared__ double red[32];
-  double acc = 0.0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    acc += (double)x[i];
-  double t = block_sum_double(acc, red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  __shared__ double wmax[32];
+  double acc = 0.0, mx = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double q = (double)w[i];
+    acc += q;
+    mx = fmax(mx, fabs(q));
+  }
+  const double t = block_sum_double(acc, red);
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, wmax[k]);
+    out[blockIdx.x] = t;
+    out[gridDim.x + blockIdx.x] = m;
+    if (blockIdx.x == 0) {
+      unsigned long long st = *status;
+      out[2 * gridDim.x] = __longlong_as_double((long long)st);
+    }
+  }
 }
 
 template <typename real>
-int launch_sum_to_double(const real* x, size_t n, double* partials, int nblocks, cudaStream_t s) {
-  k_sum_to_double<real><<<nblocks, 256, 0, s>>>(x, n, partials);
+int launch_charge_stats(const real* w, size_t n, const unsigned* status, double* out, int nblocks, cudaStream_t s) {
+  k_charge_stats<real><<<nblocks, 256, 0, s>>>(w, n, status, out);
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
+template int launch_charge_stats<float>(const float*, size_t, const unsigned*, double*, int, cudaStream_t);
+template int launch_charge_stats<double>(const double*, size_t, const unsigned*, double*, int, cudaStream_t);
 
 // End-of-step bookkeeping: field energy of the new combined field, the
 // previous one, and the kinetic energy of the push, all FP64.
@@ -151,42 +173,6 @@ template int launch_field_to_double<float>(const float*, const float*, double*, 
 template int launch_field_to_double<double>(const double*, const float*, double*, size_t, int, int, cudaStream_t);
 
 // max |x| through the float bits' order (non-negative values)
-template <typename real>
-__global__ void k_max_abs(const real* __restrict__ x, size_t n, unsigned long long* out) {
-  unsigned long long mx = 0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double a = fabs((double)x[i]);
-    mx = max(mx, (unsigned long long)__double_as_longlong(a));
-  }
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
-}
-
-template <typename real>
-int max_abs_host(const real* x, size_t n, double* out, cudaStream_t s) {
-  unsigned long long* d = nullptr;
-  SG_CUDA(cudaMallocAsync((void**)&d, sizeof(unsigned long long), s));
-  int st = SG_OK;
-  unsigned long long h = 0;
-  if (cudaMemsetAsync(d, 0, sizeof(h), s) != cudaSuccess) st = SG_ERR_CUDA;
-  if (st == SG_OK && n > 0) {
-    k_max_abs<real><<<152 * 4, 256, 0, s>>>(x, n, d);
-    if (cudaGetLastError() != cudaSuccess) st = SG_ERR_CUDA;
-    count_launch();
-  }
-  if (st == SG_OK && cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) st = SG_ERR_CUDA;
-  cudaFreeAsync(d, s);
-  if (st == SG_OK && cudaStreamSynchronize(s) != cudaSuccess) st = SG_ERR_CUDA;
-  if (st != SG_OK) {
-    set_error("max_abs: CUDA error");
-    return st;
-  }
-  std::memcpy(out, &h, sizeof(double));
-  return SG_OK;
-}
-template int max_abs_host<float>(const float*, size_t, double*, cudaStream_t);
-template int max_abs_host<double>(const double*, size_t, double*, cudaStream_t);
-
 // ---------------------------------------------------------------- Algorithm 1 helpers (FP64)
 __global__ void k_real_to_cplx(const double* src, cplx<double>* dst, size_t n, double scale) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -340,8 +326,6 @@ SG_INST_DIAG(float, 2)
 SG_INST_DIAG(float, 3)
 SG_INST_DIAG(double, 2)
 SG_INST_DIAG(double, 3)
-template int launch_sum_to_double<float>(const float*, size_t, double*, int, cudaStream_t);
-template int launch_sum_to_double<double>(const double*, size_t, double*, int, cudaStream_t);
 template int launch_to_double<float>(const float*, double*, size_t, cudaStream_t);
 template int launch_to_double<double>(const double*, double*, size_t, cudaStream_t);
 

@@ -156,8 +156,8 @@ class Engine final : public EngineBase {
     {
       const std::vector<cplx<real>> tw = make_twiddles<real>(n_);
       SG_TRY(alloc((void**)&tw_, tw.size() * sizeof(cplx<real>)));
+      // pageable source: staged when the call returns, no synchronisation needed
       SG_CUDA(cudaMemcpyAsync(tw_, tw.data(), tw.size() * sizeof(cplx<real>), cudaMemcpyHostToDevice, stream_));
-      SG_CUDA(cudaStreamSynchronize(stream_));
     }
     filter_ = cfg.mode == SG_MODE_FILTER;
     if (filter_) {
@@ -174,13 +174,7 @@ class Engine final : public EngineBase {
       SG_TRY(alloc((void**)&reg_partials_, (size_t)2 * reg_blocks_ * sizeof(double)));
     }
 
-    SG_TRY(compute_charge_total());
-    unsigned st = 0;
-    SG_CUDA(cudaMemcpy(&st, status_, sizeof(unsigned), cudaMemcpyDeviceToHost));
-    if (st & ST_NONFINITE) {
-      set_error("sg_pic_init: non-finite particle position, velocity or charge");
-      return SG_ERR_NONFINITE;
-    }
+    SG_TRY(particle_stats());
 
     SG_TRY(build_grid_set(tau_));
     // Initial state: sort, fields at t = 0, backward half kick.
@@ -221,18 +215,35 @@ class Engine final : public EngineBase {
     return check_status();
   }
 
-  // sum_p q_p in FP64 (fixed while the particles are; recomputed on upload)
-  int compute_charge_total() {
+  // The uploaded particles' statistics, one pass and one synchronisation
+  // (the kernel writes into mapped pinned memory): sum_p q_p in FP64 (fixed
+  // while the particles are), max_p |q_p| for the deposit's fixed-point
+  // scale, and the status word of the upload's finiteness check.
+  int particle_stats() {
     const int nb = 256;
-    double* part = nullptr;
-    SG_TRY(alloc((void**)&part, nb * sizeof(double)));
-    SG_TRY(launch_sum_to_double<real>(P_[cur_].w, np_, part, nb, stream_));
-    std::vector<double> h(nb);
-    SG_CUDA(cudaMemcpyAsync(h.data(), part, nb * sizeof(double), cudaMemcpyDeviceToHost, stream_));
-    SG_CUDA(cudaStreamSynchronize(stream_));
+    SG_TRY(ensure_pinned(&stats_host_, &stats_host_bytes_, (2 * nb + 1) * sizeof(double)));
+    double* h = static_cast<double*>(stats_host_);
+    void* hd = nullptr;
+    SG_CUDA(cudaHostGetDevicePointer(&hd, stats_host_, 0));
+    if (np_ > 0) {
+      SG_TRY(launch_charge_stats<real>(P_[cur_].w, np_, status_, static_cast<double*>(hd), nb, stream_));
+      SG_CUDA(cudaStreamSynchronize(stream_));
+    } else {
+      std::memset(h, 0, (2 * nb + 1) * sizeof(double));
+    }
     charge_total_ = 0;
-    for (double x : h) charge_total_ += x;
-    free_one(part);
+    double qmax = 0;
+    for (int b = 0; b < nb; ++b) {
+      charge_total_ += h[b];
+      qmax = std::max(qmax, h[nb + b]);
+    }
+    unsigned long long stw = 0;
+    std::memcpy(&stw, h + 2 * nb, sizeof(stw));
+    if ((unsigned)stw & ST_NONFINITE) {
+      set_error("non-finite particle position, velocity or charge");
+      return SG_ERR_NONFINITE;
+    }
+    set_deposit_scale(qmax);
     return SG_OK;
   }
 
@@ -771,7 +782,7 @@ class Engine final : public EngineBase {
     SG_CUDA(cudaStreamSynchronize(stream_));
     cur_ = 0;
     SG_TRY(upload_particles(&in));
-    SG_TRY(compute_charge_total());
+    SG_TRY(particle_stats());
     if (hd.tau != tau_) SG_TRY(build_grid_set(hd.tau));
     adaptive_ = hd.adaptive != 0;
     SG_TRY(enqueue_sort());
@@ -913,6 +924,9 @@ class Engine final : public EngineBase {
     if (diag_host_) cudaFreeHost(diag_host_);
     diag_host_ = nullptr;
     diag_host_bytes_ = 0;
+    if (stats_host_) cudaFreeHost(stats_host_);
+    stats_host_ = nullptr;
+    stats_host_bytes_ = 0;
     for (auto& r : ring_) {
       if (r.host) cudaFreeHost(r.host);
       if (r.ev) cudaEventDestroy(r.ev);
@@ -966,8 +980,7 @@ class Engine final : public EngineBase {
       SG_CUDA(cudaMemcpyAsync(P_[cur_].w, parts->w, np_ * sizeof(real), kind, stream_));
       SG_TRY(launch_wrap_check<real, D>(P_[cur_], np_, status_, stream_));
     }
-    SG_CUDA(cudaStreamSynchronize(stream_));
-    return set_deposit_scale();
+    return SG_OK;  // particle_stats() checks the status and sets the deposit scale
   }
 
   // Fixed-point scale of the deposit window (FP32 path): with E the least
@@ -975,11 +988,9 @@ class Engine final : public EngineBase {
   // scaled by 2^(20 - E), so each rounds to at most 2^20 - 2^9 in magnitude
   // and a window of at most 2^11 particles stays below 2^31 - 2^20.
   // Charges do not change during a run; load() recomputes it.
-  int set_deposit_scale() {
+  void set_deposit_scale(double qmax) {
     dep_scale_ = 1.0;
     if (sizeof(real) == 4 && np_ > 0) {
-      double qmax = 0;
-      SG_TRY(max_abs_host<real>(P_[cur_].w, np_, &qmax, stream_));
       qmax *= (double)inv_cell_vol();
       int E = 0;
       if (qmax > 0) std::frexp(qmax, &E);  // qmax < 2^E
@@ -987,7 +998,6 @@ class Engine final : public EngineBase {
       const int k = std::max(-126, std::min(127, 20 - E));
       dep_scale_ = std::ldexp(1.0, k);
     }
-    return SG_OK;
   }
 
   // ------------------------------------------------------------ grid set
@@ -1158,8 +1168,8 @@ class Engine final : public EngineBase {
       P.vpl = std::max(1, N_ / 32);
       P.smem = a == 0 ? 0 : (int)((size_t)lpb * S * sizeof(real));
       SG_TRY(galloc((void**)&P.dev, jobs.size() * sizeof(LineJob)));
+      // pageable source: staged when the call returns, no synchronisation needed
       SG_CUDA(cudaMemcpyAsync(P.dev, jobs.data(), jobs.size() * sizeof(LineJob), cudaMemcpyHostToDevice, stream_));
-      SG_CUDA(cudaStreamSynchronize(stream_));
       rpasses_.push_back(P);
       prev.swap(next);
     }
@@ -1215,8 +1225,8 @@ class Engine final : public EngineBase {
       P.nblocks = blocks;
       P.smem = smem;
       SG_TRY(galloc((void**)&P.dev, jobs.size() * sizeof(FftJob)));
+      // pageable source: staged when the call returns, no synchronisation needed
       SG_CUDA(cudaMemcpyAsync(P.dev, jobs.data(), jobs.size() * sizeof(FftJob), cudaMemcpyHostToDevice, stream_));
-      SG_CUDA(cudaStreamSynchronize(stream_));
       fpasses_.push_back(P);
     }
     return SG_OK;
@@ -1804,6 +1814,8 @@ class Engine final : public EngineBase {
   GridDesc* grids_dev_ = nullptr;
   void* diag_host_ = nullptr;  // pinned staging of the diagnostics read-back
   size_t diag_host_bytes_ = 0;
+  void* stats_host_ = nullptr;  // mapped pinned: the upload's statistics (particle_stats)
+  size_t stats_host_bytes_ = 0;
   static constexpr int kDiagRing = SG_DIAG_RING;
   struct DiagSlot {
     void* host = nullptr;  // pinned record (diag_bytes() at the post)

@@ -69,9 +69,11 @@ template <typename real, int D>
 int launch_deposit(const PArrays<real, D>& p, size_t np, int n, real inv_cell_vol, real* rho,
                    int win_cap_nodes, real scale, real inv_scale, real shift, cudaStream_t s);
 
-// max_i |x_i| on the host (synchronises the stream; set-up use only).
+// The upload's statistics, out[0 .. 2 nb]: per-block FP64 charge sums, per-
+// block max |q|, then the status word (its bits in a double).
 template <typename real>
-int max_abs_host(const real* x, size_t n, double* out, cudaStream_t s);
+int launch_charge_stats(const real* w, size_t n, const unsigned* status, double* out, int nblocks, cudaStream_t s);
+
 
 // ---------------------------------------------------------------- line passes
 // The lines of one array along one axis, processed by one kernel launch
@@ -275,8 +277,6 @@ int launch_tile_scatter(const PArrays<real, D>& src, const PArrays<real, D>& dst
 template <typename real, int D>
 int launch_wrap_check(const PArrays<real, D>& p, size_t np, unsigned* status, cudaStream_t s);
 
-template <typename real>
-int launch_sum_to_double(const real* x, size_t n, double* partials, int nblocks, cudaStream_t s);
 
 // Device diagnostics record updated at the end of each step.
 struct DevDiag {
