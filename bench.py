@@ -313,8 +313,10 @@ def run_serving(args, world, rank, local):
     1e-3..0.1, k uniform 0.3..0.6, `--steps` steps each), arriving as a
     Poisson process whose rate is set to about 80% of the batched server's
     measured capacity, admitted by memory footprint (8 GB budget, 16 slots).
-    The same arrival stream is served batched (one graph per tick) and plain
-    (runs stepped in turn with direct launches, one solve launch per grid).
+    The same arrival stream is served batched (each run's cached graphs on
+    its own stream, and one cross-run solve launch per tick for the runs of
+    at most 2^20 particles) and plain (runs stepped in turn with direct
+    launches, one solve launch per grid).
     Reports per mode: p50 / p99 per-step latency (device), particle-steps/s
     of device time and of wall time, the device's busy fraction, and p50 /
     p99 of the time from a request's arrival to its result."""

@@ -445,7 +445,8 @@ class Server:
         return t.value
 
     def set_mode(self, mode):
-        """"batched" (one graph per tick over all runs) or "plain" (per run, per grid launches)."""
+        """"batched" (each run's cached graphs on its own stream, one cross-run solve launch per tick for
+        the runs that take part) or "plain" (runs in turn, direct launches, one solve launch per grid)."""
         m = L.SG_SERVE_BATCHED if mode in ("batched", L.SG_SERVE_BATCHED) else L.SG_SERVE_PLAIN
         check(lib().sg_serve_set_mode(self.h, m), "sg_serve_set_mode")
 
