@@ -275,7 +275,12 @@ int sg_pic_kernel_launches(sg_pic* h, unsigned long long* count);
  * timings, 15 the window capacity in use, 16..19 the four deposit timings,
  * 20 whether they came from an earlier run of the same shape (precision,
  * dimension, level, log2 of the particle count, centring, push kind).
- * Runs created with sg_pic_init_deferred keep the defaults. */
+ * Just before the run's first sort step (particles drifted for a whole sort
+ * period) the four deposit windows are timed again and the window with the
+ * smallest sum of the two timings is kept (3% rule; a change re-captures
+ * the step graphs); with cap >= 25, entries 21..24 hold those timings (0
+ * before that step, or when the cache held a refined choice).  Runs created
+ * with sg_pic_init_deferred keep the defaults. */
 int sg_pic_set_profiling(sg_pic* h, int on);
 int sg_pic_stage_times(sg_pic* h, double* ms, int cap);
 

@@ -75,6 +75,8 @@ struct PartKey {
 struct PartEntry {
   int push_pick, dep_pick;
   float push_ms[kPushCands], dep_ms[kDepCands];
+  bool refined;                  // the window was re-chosen on drifted particles
+  float dep_drift_ms[kDepCands];  // the deposit timed before the first sort step
 };
 std::map<PartKey, PartEntry>& part_cache() {
   static std::map<PartKey, PartEntry> m;
@@ -335,6 +337,7 @@ class Engine final : public EngineBase {
       } else if (profiling_) {
         SG_TRY(step_profiled(do_sort));
       } else {
+        if (do_sort && refine_pending_) SG_TRY(refine_deposit());
         SG_TRY(step_graph(do_sort));
       }
       ++step_;
@@ -851,6 +854,9 @@ class Engine final : public EngineBase {
     for (int c = 0; c < kDepCands; ++c)
       if (cap > 16 + c) ms[16 + c] = dep_ms_[c];
     if (cap > 20) ms[20] = part_from_cache_ ? 1.0 : 0.0;
+    // the deposit timed again before the first sort step (0 until then)
+    for (int c = 0; c < kDepCands; ++c)
+      if (cap > 21 + c) ms[21 + c] = dep_drift_ms_[c];
     return SG_OK;
   }
 
@@ -1461,8 +1467,10 @@ class Engine final : public EngineBase {
       if (it != part_cache().end()) {
         for (int c = 0; c < kPushCands; ++c) push_ms_[c] = it->second.push_ms[c];
         for (int c = 0; c < kDepCands; ++c) dep_ms_[c] = it->second.dep_ms[c];
+        for (int c = 0; c < kDepCands; ++c) dep_drift_ms_[c] = it->second.dep_drift_ms[c];
         apply(it->second.push_pick, it->second.dep_pick);
         part_from_cache_ = true;
+        refine_pending_ = !it->second.refined;
         return SG_OK;
       }
     }
@@ -1507,12 +1515,77 @@ class Engine final : public EngineBase {
     apply(pp, dp);
     SG_TRY(enqueue_deposit());  // the regular-grid density from the chosen window
     PartEntry ent;
+    std::memset(&ent, 0, sizeof(ent));
     ent.push_pick = pp;
     ent.dep_pick = dp;
     for (int c = 0; c < kPushCands; ++c) ent.push_ms[c] = pms[c];
     for (int c = 0; c < kDepCands; ++c) ent.dep_ms[c] = dms[c];
+    ent.refined = false;
     std::lock_guard<std::mutex> lk(tune_mu());
     part_cache()[key] = ent;
+    refine_pending_ = true;
+    return SG_OK;
+  }
+
+  // The second look at the deposit window, just before the run's first sort
+  // step: the particles have drifted for a whole sort period since the
+  // init sort, the deposit's worst case, where the first timing saw its best.
+  // Every candidate is timed again on the current particles (the regular-grid
+  // density of unchanged positions is recomputed; the next step recomputes
+  // it anyway), and the window minimising the sum of the two timings is
+  // kept (3% rule as before).  A change re-captures the step graphs.  The
+  // refined choice goes to the cache, so runs of the same shape skip this.
+  int refine_deposit() {
+    refine_pending_ = false;
+    if (np_ == 0 || adaptive_ || profiling_) return SG_OK;
+    cudaEvent_t e0, e1;
+    SG_CUDA(cudaEventCreate(&e0));
+    SG_CUDA(cudaEventCreate(&e1));
+    float dms[kDepCands];
+    const int keep = win_cap_;
+    int st = SG_OK;
+    for (int rep = 0; rep < 3 && st == SG_OK; ++rep) {  // the first round warms up
+      for (int c = 0; c < kDepCands && st == SG_OK; ++c) {
+        if (rep == 0) dms[c] = 1e30f;
+        win_cap_ = kDepCap[c];
+        if (cudaEventRecord(e0, stream_) != cudaSuccess) st = SG_ERR_CUDA;
+        if (st == SG_OK) st = enqueue_deposit();
+        if (st == SG_OK && cudaEventRecord(e1, stream_) != cudaSuccess) st = SG_ERR_CUDA;
+        if (st == SG_OK && cudaEventSynchronize(e1) != cudaSuccess) st = SG_ERR_CUDA;
+        float ms = 0;
+        if (st == SG_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = SG_ERR_CUDA;
+        if (st == SG_OK && rep > 0) dms[c] = std::min(dms[c], ms);
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    win_cap_ = keep;
+    if (st != SG_OK) {
+      set_error("deposit window refinement: CUDA error");
+      return st;
+    }
+    int dp = dep_pick_;
+    for (int c = 0; c < kDepCands; ++c)
+      if (dep_ms_[c] + dms[c] < 0.97f * (dep_ms_[dp] + dms[dp])) dp = c;
+    for (int c = 0; c < kDepCands; ++c) dep_drift_ms_[c] = dms[c];
+    if (dp != dep_pick_) {
+      dep_pick_ = dp;
+      win_cap_ = kDepCap[dp];
+      invalidate_graphs();
+    }
+    SG_TRY(enqueue_deposit());  // the regular-grid density from the chosen window
+    bool boris = false;
+    for (int m = 0; m < 3; ++m) boris |= cfg_.B[m] != 0.0;
+    int lg = 0;
+    while (((size_t)1 << (lg + 1)) <= np_) ++lg;
+    const PartKey key{(int)sizeof(real), D, n_, lg, cfg_.cell ? 1 : 0, boris ? 1 : 0};
+    std::lock_guard<std::mutex> lk(tune_mu());
+    auto it = part_cache().find(key);
+    if (it != part_cache().end()) {
+      it->second.dep_pick = dp;
+      it->second.refined = true;
+      for (int c = 0; c < kDepCands; ++c) it->second.dep_drift_ms[c] = dms[c];
+    }
     return SG_OK;
   }
 
@@ -1796,6 +1869,8 @@ class Engine final : public EngineBase {
   int push_pick_ = 1, dep_pick_ = 2;
   float push_ms_[kPushCands] = {}, dep_ms_[kDepCands] = {};
   bool part_from_cache_ = false;
+  bool refine_pending_ = false;  // the deposit window is re-timed before the first sort step
+  float dep_drift_ms_[kDepCands] = {};
 
   real* rho_reg_ = nullptr;
   real* Ehi_ = nullptr;

@@ -363,15 +363,16 @@ class Run:
     def tuning(self):
         """Init-time autotuner record: solve variant, push grid and deposit
         window in use, and the timings (ms) they were chosen from."""
-        ms = np.zeros(21)
-        check(lib().sg_pic_stage_times(self.h, ms.ctypes.data, 21), "sg_pic_stage_times")
+        ms = np.zeros(25)
+        check(lib().sg_pic_stage_times(self.h, ms.ctypes.data, 25), "sg_pic_stage_times")
         return {"solve_variant": "one-block-per-grid" if ms[6] == 1 else "per-axis-passes",
                 "passes_ms": float(ms[7]), "one_block_ms": float(ms[8]), "from_cache": bool(ms[9]),
                 "push_blocks": int(ms[10]), "push_wave_blocks": int(ms[11]),
                 "push_ms_half_one_two_waves": [float(x) for x in ms[12:15]],
                 "deposit_window_nodes": int(ms[15]),
                 "deposit_ms_4096_6144_8192_12288": [float(x) for x in ms[16:20]],
-                "particles_from_cache": bool(ms[20])}
+                "particles_from_cache": bool(ms[20]),
+                "deposit_ms_drifted": [float(x) for x in ms[21:25]]}
 
     # ---- sharded runs (sg_pic_init_deferred / sg_pic_start / the split step)
     def start(self):

@@ -505,12 +505,24 @@ def test_particle_tuner_record(torch_cuda):
     assert all(x > 0 for x in t0["push_ms_half_one_two_waves"] + t0["deposit_ms_4096_6144_8192_12288"])
     assert t1["particles_from_cache"] and (t1["push_blocks"], t1["deposit_window_nodes"]) == \
         (t0["push_blocks"], t0["deposit_window_nodes"])
+    assert all(x == 0 for x in t0["deposit_ms_drifted"])  # not before the first sort step
+    # past the first sort step (sort every 4): the window was timed again on
+    # drifted particles, and a later run of the same shape starts from that
     ref = O.OracleRun(wl.L, wl.n, u64, v64, q64, wl.dt, qm=wl.qm, tau=wl.tau)
-    ref.step(3)
+    ref.step(5)
     for run in runs:
-        run.step(3)
+        run.step(5)
         ug, vg, _ = run.particles()
         assert nrmse_periodic(ug, ref.u) < TOL["fp32"] and nrmse(vg, ref.velocities()) < TOL["fp32"]
+    t0 = runs[0].tuning()
+    assert all(x > 0 for x in t0["deposit_ms_drifted"])
+    assert t0["deposit_window_nodes"] in (4096, 6144, 8192, 12288)
+    run2, _ = make_run(wl, "fp32", torch_cuda)
+    t2 = run2.tuning()
+    assert t2["particles_from_cache"] and all(x > 0 for x in t2["deposit_ms_drifted"])
+    assert t2["deposit_window_nodes"] == runs[1].tuning()["deposit_window_nodes"]
+    run2.close()
+    for run in runs:
         run.close()
 
 
