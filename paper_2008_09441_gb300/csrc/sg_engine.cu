@@ -107,6 +107,9 @@ class Engine final : public EngineBase {
       SG_CUDA(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
       own_stream_ = true;
     }
+    SG_CUDA(cudaStreamCreateWithFlags(&sort_stream_, cudaStreamNonBlocking));
+    SG_CUDA(cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming));
+    SG_CUDA(cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming));
     sort_every_ = cfg.sort_every > 0 ? cfg.sort_every : kDefaultSortEvery;
     tau_ = cfg.tau == SG_TAU_ADAPTIVE ? 1 : cfg.tau;
     adaptive_ = cfg.tau == SG_TAU_ADAPTIVE;
@@ -941,6 +944,11 @@ class Engine final : public EngineBase {
     ring_head_ = ring_count_ = 0;
     for (int i = 0; i < 8; ++i)
       if (ev_[i]) cudaEventDestroy(ev_[i]);
+    if (ev_fork_) cudaEventDestroy(ev_fork_);
+    if (ev_join_) cudaEventDestroy(ev_join_);
+    if (sort_stream_) cudaStreamDestroy(sort_stream_);
+    ev_fork_ = ev_join_ = nullptr;
+    sort_stream_ = nullptr;
     if (own_stream_ && stream_) cudaStreamDestroy(stream_);
     stream_ = nullptr;
   }
@@ -1321,10 +1329,11 @@ class Engine final : public EngineBase {
     SG_CUDA(cudaMemsetAsync(tile_count_, 0, ntiles_ * sizeof(uint32_t), stream_));
     return SG_OK;
   }
-  int sort_finish() {
-    SG_TRY(launch_tile_hist(keys_, np_, tile_count_, stream_));
-    SG_TRY(exclusive_scan_u32(tile_count_, cursor_, ntiles_, scan_sums_, stream_));
-    SG_TRY(launch_tile_scatter<real, D>(P_[cur_], P_[cur_ ^ 1], keys_, cursor_, np_, stream_));
+  int sort_finish(cudaStream_t s = nullptr) {
+    if (!s) s = stream_;
+    SG_TRY(launch_tile_hist(keys_, np_, tile_count_, s));
+    SG_TRY(exclusive_scan_u32(tile_count_, cursor_, ntiles_, scan_sums_, s));
+    SG_TRY(launch_tile_scatter<real, D>(P_[cur_], P_[cur_ ^ 1], keys_, cursor_, np_, s));
     cur_ ^= 1;
     return SG_OK;
   }
@@ -1639,10 +1648,23 @@ class Engine final : public EngineBase {
     return enqueue_restrict_solve_combine(ke);
   }
 
+  // A sort step deposits the particles in their current order; then a
+  // second stream sorts them into the other buffer (tile counts, scan,
+  // scatter: memory-bound) while the latency-bound grid stages, which leave
+  // most SMs idle, run on the run's stream; the next step starts from the
+  // sorted buffer.  The deposit needs no sorted input: the sort only makes
+  // later deposits and gathers faster.
   int enqueue_step(bool do_sort) {
     SG_TRY(enqueue_push(cfg_.dt, true, ke_partials_, do_sort));
-    if (do_sort) SG_TRY(sort_finish());
-    return enqueue_fields(ke_partials_);
+    if (!do_sort) return enqueue_fields(ke_partials_);
+    SG_TRY(enqueue_deposit());  // P_[cur_]: before sort_finish switches cur_
+    SG_CUDA(cudaEventRecord(ev_fork_, stream_));
+    SG_CUDA(cudaStreamWaitEvent(sort_stream_, ev_fork_, 0));
+    SG_TRY(sort_finish(sort_stream_));  // P_[cur_] -> P_[cur_ ^ 1]
+    SG_CUDA(cudaEventRecord(ev_join_, sort_stream_));
+    SG_TRY(enqueue_restrict_solve_combine(ke_partials_));
+    SG_CUDA(cudaStreamWaitEvent(stream_, ev_join_, 0));
+    return SG_OK;
   }
 
   // Graph variants: (current particle set, sort or not).
@@ -1870,6 +1892,10 @@ class Engine final : public EngineBase {
   float push_ms_[kPushCands] = {}, dep_ms_[kDepCands] = {};
   bool part_from_cache_ = false;
   bool refine_pending_ = false;  // the deposit window is re-timed before the first sort step
+  // the sort of a sort step runs on its own stream, forked from and joined
+  // to the run's stream (captured into the step graph with it)
+  cudaStream_t sort_stream_ = nullptr;
+  cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
   float dep_drift_ms_[kDepCands] = {};
 
   real* rho_reg_ = nullptr;
