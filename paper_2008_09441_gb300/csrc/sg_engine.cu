@@ -1,4 +1,15 @@
-// Engine<real, D>: one sparse-grid PIC run on one GPU.
+// Engine<real, D>: one sparse-grid PIC run on one GPU, the host runtime
+// around the kernels:
+// - device buffers from the stream-ordered allocator (freed memory stays in
+//   the pool for the next run);
+// - the step as CUDA graphs, one per (particle buffer, sort or not); a sort
+//   step's counting sort runs on a second stream beside the grid stages;
+// - the step split for the cross-run solve of batched serving, and for
+//   sharded runs around the exchange of the regular-grid density;
+// - the init-time autotuner (solve variant, push grid, deposit window) with
+//   a process-wide cache per run shape;
+// - FP64 diagnostics written by one kernel into mapped pinned records,
+//   blocking or pipelined.
 #include <algorithm>
 #include <climits>
 #include <cmath>
