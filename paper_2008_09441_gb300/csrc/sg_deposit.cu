@@ -243,34 +243,40 @@ __global__ void __launch_bounds__(DEP_THREADS) k_deposit(PArrays<real, D> p, siz
       bhi[m] = s_box[par][D + m];
       any &= blo[m] <= bhi[m];
     }
-    if (any) {  // the touched box, one warp per row, lanes along x: add and clear
+    if (any) {  // the touched box: add to the grid and clear
+      // The box's (row, x) items are spread over all the block's threads,
+      // consecutive threads along x, so that narrow boxes (3D, or right
+      // after a sort) keep every lane busy.  FP32: an item is four nodes
+      // (one 16-byte shared load, one vector add); FP64: one node.
       const int ny = bhi[1 % D] - blo[1 % D] + 1;
       const int nrows = D == 2 ? ny : ny * (bhi[D - 1] - blo[D - 1] + 1);
-      for (int r = threadIdx.x >> 5; r < nrows; r += DEP_THREADS / 32) {
+      constexpr int PER = W::fixed ? 4 : 1;
+      const int x0 = W::fixed ? (blo[0] & ~3) : blo[0];
+      const int nx = (bhi[0] - x0) / PER + 1;
+      const int total = nrows * nx;
+      for (int f = threadIdx.x; f < total; f += DEP_THREADS) {
+        const int r = f / nx;
+        const int x = x0 + (f - r * nx) * PER;
         const int ly = blo[1 % D] + (D == 2 ? r : r % ny);
         const int lz = D == 2 ? 0 : blo[D - 1] + r / ny;
         const size_t gy = (size_t)((origin[1 % D] + ly) & mask);
         const size_t grow = D == 2 ? gy * N : ((size_t)((origin[D - 1] + lz) & mask) * N + gy) * N;
         T* wrow = win + ((size_t)lz * side + ly) * side;
-        if constexpr (W::fixed) {  // four nodes per lane: one 16-byte shared load, one vector add
-          for (int x = (blo[0] & ~3) + 4 * lane; x <= bhi[0]; x += 128) {
-            const int4 v = *reinterpret_cast<const int4*>(wrow + x);
-            if ((v.x | v.y | v.z | v.w) != 0) {
-              float* dst = rho + grow + ((origin[0] + x) & mask);
-              asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst),
-                           "f"(W::value(v.x, inv_scale)), "f"(W::value(v.y, inv_scale)),
-                           "f"(W::value(v.z, inv_scale)), "f"(W::value(v.w, inv_scale))
-                           : "memory");
-              *reinterpret_cast<int4*>(wrow + x) = make_int4(0, 0, 0, 0);
-            }
+        if constexpr (W::fixed) {
+          const int4 v = *reinterpret_cast<const int4*>(wrow + x);
+          if ((v.x | v.y | v.z | v.w) != 0) {
+            float* dst = rho + grow + ((origin[0] + x) & mask);
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst),
+                         "f"(W::value(v.x, inv_scale)), "f"(W::value(v.y, inv_scale)),
+                         "f"(W::value(v.z, inv_scale)), "f"(W::value(v.w, inv_scale))
+                         : "memory");
+            *reinterpret_cast<int4*>(wrow + x) = make_int4(0, 0, 0, 0);
           }
         } else {
-          for (int x = blo[0] + lane; x <= bhi[0]; x += 32) {
-            const T v = wrow[x];
-            if (v != (T)0) {
-              atomicAdd(&rho[grow + ((origin[0] + x) & mask)], W::value(v, inv_scale));
-              wrow[x] = (T)0;
-            }
+          const T v = wrow[x];
+          if (v != (T)0) {
+            atomicAdd(&rho[grow + ((origin[0] + x) & mask)], W::value(v, inv_scale));
+            wrow[x] = (T)0;
           }
         }
       }
