@@ -61,3 +61,45 @@ def test_window_deposit_equals_oracle(d, n, side, shift):
     got = window_deposit(u, q, n, L, side, shift)
     ref = O.deposit_cic(u, q, (n,) * d, L, "cell" if shift else "node")
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-10 * np.max(np.abs(ref)))
+
+
+def flush_items(blo, bhi, threads, fixed):
+    """The flush's enumeration of a touched box [blo, bhi] (window
+    coordinates, x first): flat items f = thread, thread + threads, ...; item
+    f is row r = f // nx and x = x0 + (f mod nx) * per, with x0 = blo_x
+    rounded down to 4 and per = 4 nodes (fixed point) or x0 = blo_x and
+    per = 1.  Returns the window nodes each item covers."""
+    d = len(blo)
+    per = 4 if fixed else 1
+    x0 = (blo[0] & ~3) if fixed else blo[0]
+    nx = (bhi[0] - x0) // per + 1
+    ny = bhi[1] - blo[1] + 1
+    nrows = ny if d == 2 else ny * (bhi[2] - blo[2] + 1)
+    out = []
+    for t in range(threads):
+        for f in range(t, nrows * nx, threads):
+            r, xi = divmod(f, nx)
+            x = x0 + xi * per
+            ly = blo[1] + (r if d == 2 else r % ny)
+            lz = 0 if d == 2 else blo[2] + r // ny
+            out.append([(x + k, ly, lz) for k in range(per)])
+    return out
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("fixed", [True, False])
+def test_flush_items_cover_the_box_once(d, fixed):
+    rng = np.random.default_rng(5 + d + 7 * fixed)
+    side = 128 if d == 2 else 24
+    for _ in range(50):
+        lo = rng.integers(0, side - 1, d)
+        hi = np.array([rng.integers(lo[m], side) for m in range(d)])  # hi <= side - 1: the fast path's bound
+        items = flush_items(list(lo), list(hi), 512, fixed)
+        nodes = [n for it in items for n in it]
+        assert len(nodes) == len(set(nodes))  # no node twice
+        want = {(x, y, z) for x in range(lo[0], hi[0] + 1) for y in range(lo[1], hi[1] + 1)
+                for z in (range(lo[2], hi[2] + 1) if d == 3 else [0])}
+        assert want <= set(nodes)  # every touched node flushed
+        assert all(0 <= x < side for x, _, _ in nodes)  # 16-byte reads stay in the window row
+        # the extra nodes are the quad padding along x of rows in the box
+        assert all(lo[1] <= y <= hi[1] and (d == 2 or lo[2] <= z <= hi[2]) for _, y, z in nodes)
