@@ -540,7 +540,7 @@ def main():
     u = torch.from_numpy(wl.u.astype(np.float32)).to(dev)
     v = torch.from_numpy(wl.v.astype(np.float32)).to(dev)
     q = torch.from_numpy(wl.q.astype(np.float32)).to(dev)
-    sort_every = args.sort_every if args.sort_every > 0 else 4  # the library default
+    sort_every = args.sort_every if args.sort_every > 0 else (6 if d == 3 else 4)  # the library default
     run = Run(wl.L, n, u, v, q, wl.dt, tau=wl.tau, qm=wl.qm, B=wl.B, eext_lin=wl.eext_lin, precision="fp32",
               sort_every=sort_every, stream=stream.cuda_stream, mode=args.mode, centring=args.centring,
               combine=args.combine)

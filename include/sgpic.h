@@ -106,7 +106,7 @@ typedef struct {
   double alpha;       /* denoising threshold fraction (Section 4.3.3) */
   double pc_ref;      /* reference particles per cell (P_c)_ref (Section 4.3.3) */
   int tau_constants;  /* SG_TAU_CONST_PAPER or SG_TAU_CONST_EMPIRICAL */
-  int sort_every;     /* cell-key sort period in steps; 0 = library default (4) */
+  int sort_every;     /* cell-key sort period in steps; 0 = library default (4 in 2D, 6 in 3D) */
   void* stream;       /* cudaStream_t for all work of the run; NULL = own stream */
   int mode;           /* SG_MODE_COMBINE (0): sparse PIC, a spectral solve on every
                          component grid and the signed combination of their fields

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
 
 
-LIB_DEFAULT_SORT_EVERY = 4  # sg_params.sort_every = 0
+LIB_DEFAULT_SORT_EVERY = {2: 4, 3: 6}  # sg_params.sort_every = 0, by dimension
 
 
 def nrmse(a, ref):
@@ -196,7 +196,7 @@ def trajectory_check(wl, prec, torch, steps, tol_scale=1.0, **kw):
     run, (u64, v64, q64) = make_run(wl, prec, torch, **kw)
     ref = O.OracleRun(wl.L, wl.n, u64, v64, q64, wl.dt, qm=wl.qm, tau=wl.tau, B=wl.B, eext_lin=wl.eext_lin)
     tol = TOL[prec] * tol_scale
-    period = kw.get("sort_every") or LIB_DEFAULT_SORT_EVERY
+    period = kw.get("sort_every") or LIB_DEFAULT_SORT_EVERY[ref.d]
     # the oracle's checksum after every step (the GPU's is the one of its last
     # sort: init, then every `period` steps)
     k0 = O.cell_keys(O.wrap_unit(u64), ref.n)
