@@ -292,7 +292,9 @@ int sg_pic_stage_times(sg_pic* h, double* ms, int cap);
  * variant stays through later grid-set changes.  Returns SG_ERR_INVALID for
  * another value and SG_ERR_UNSUPPORTED for SG_SOLVE_ONE_BLOCK when a
  * component grid exceeds the one-block size; synchronises the run's
- * stream.  No effect on the filter mode's regular-grid solve. */
+ * stream.  No effect on the filter mode's regular-grid solve, nor on the
+ * cross-run solve of batched serving, which always takes one block per
+ * (run, grid). */
 #define SG_SOLVE_AUTO (-1)
 #define SG_SOLVE_PASSES 0
 #define SG_SOLVE_ONE_BLOCK 1
